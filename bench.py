@@ -1,0 +1,433 @@
+#!/usr/bin/env python3
+"""Benchmark of the softened direct sum on GB300.
+
+One step = one evaluation of the accelerations of an equal-mass Plummer
+sphere of N = 131072 particles (i set = j set, eps = 4 / N^(1/3), FP32
+records) with the plain FP32 kernel: N^2 pair interactions. The headline
+value is pair interactions per second over the K timed steps (CUDA events
+on the launching stream, L2 flushed between steps by writing 256 MiB).
+Beside it the line reports the compensated (double-single) form on the
+same input, the roofline fraction of the pair kernel, the end-to-end rate
+through the host-buffer C-ABI call (copies included), and the FP64 oracle
+timed on the host cores on a bounded sample of the same workload.
+
+  python bench.py [--steps K] [--warmup W]          # one GPU
+  torchrun --nproc-per-node N bench.py --gpus N     # N independent replicas (weak scaling)
+  python bench.py --impl reference                  # the FP64 CPU oracle on this host
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "pair interactions/s and % of FP32/MUFU roofline at N=131072, FP32 vs compensated"
+UNIT = "pairs/s"
+N_DEFAULT = 131072
+FLOP_PER_PAIR = 38  # the paper's counting convention (Eq. 5)
+ISSUE_PER_PAIR = 13  # 12 FP32-pipe instructions + 1 MUFU per pair (plain kernel, no potential)
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+PAPER_PAIRS_PER_S = 256e9 / FLOP_PER_PAIR  # 8800GTX, N = 131072 (Table 3): context only
+
+
+# ------------------------------------------------------------------ distributed plumbing
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+def dist_init(backend: str):
+    import torch.distributed as dist
+
+    rank, world, _ = dist_env()
+    if world > 1 and not dist.is_initialized():
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        os.environ.setdefault("MASTER_PORT", "29531")
+        dist.init_process_group(backend=backend, rank=rank, world_size=world)
+    return rank, world
+
+
+def barrier(device=None):
+    import torch.distributed as dist
+
+    if dist.is_available() and dist.is_initialized():
+        if device is not None and device.type == "cuda":
+            dist.barrier(device_ids=[device.index])
+        else:
+            dist.barrier()
+
+
+def reduce_max(x: float, device=None) -> float:
+    """Max of a scalar over ranks (control plane only: timings)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()):
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(units_per_rank: float, world: int, max_seconds: float) -> float:
+    """Whole-job throughput: units all ranks processed / the slowest rank's time."""
+    return units_per_rank * world / max_seconds if max_seconds > 0 else float("nan")
+
+
+def shard_rows(n: int, rank: int, world: int):
+    """Contiguous i-range of one rank when one system's i set is split across ranks."""
+    lo = n * rank // world
+    hi = n * (rank + 1) // world
+    return lo, hi
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100"]
+            if self.gpu_id is not None:
+                cmd += ["-i", self.gpu_id]
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons, power = [], [], set(), []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                    power.append(float(parts[3]))
+                except ValueError:
+                    continue
+                for name, val in zip(self.NAMES, parts[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(name)
+        os.unlink(self.path)
+        return {
+            "sm_mhz": statistics.median(sm) if sm else None,
+            "sm_max_mhz": max(mx) if mx else None,
+            "power_w_max": max(power) if power else None,
+            "samples": len(sm),
+            "reasons": sorted(reasons),
+        }
+
+
+def gpu_selector(torch, device):
+    try:
+        props = torch.cuda.get_device_properties(device)
+        return f"{props.pci_domain_id:08X}:{props.pci_bus_id:02X}:{props.pci_device_id:02X}.0"
+    except Exception:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        return vis.split(",")[device.index] if vis else str(device.index)
+
+
+# ------------------------------------------------------------------ workload
+
+def workload(n: int, seed: int):
+    from paper_astro_ph_0703100_gb300 import synth
+
+    p = synth.plummer(n, seed)
+    eps2 = float(np.float32(synth.plummer_eps(n)) ** 2)
+    return p, eps2
+
+
+def cpu_baseline(p, eps2, gpu_results: dict, budget_s: float):
+    """The FP64 oracle on this host's cores on a bounded row sample, plus the
+    E_max of the GPU results on those rows (Eq. 4)."""
+    import oracle
+
+    n = p.shape[0]
+    cores = oracle.max_threads()
+    probe_rows = np.arange(0, n, max(1, n // 128))[:128]
+    t0 = time.perf_counter()
+    oracle.force(p, p, eps2, rows=probe_rows, potential=False)
+    rate = probe_rows.size * n / max(time.perf_counter() - t0, 1e-6)
+    n_rows = int(min(n, max(256, rate * budget_s / n)))
+    from paper_astro_ph_0703100_gb300 import synth
+
+    rows = synth.sample_rows(n, n_rows, seed=n + 17)
+    t0 = time.perf_counter()
+    ref, _ = oracle.force(p, p, eps2, rows=rows, potential=False)
+    dt = time.perf_counter() - t0
+    out = {
+        "value": rows.size * n / dt,
+        "unit": UNIT,
+        "cores": cores,
+        "kind": "oracle",
+        "sample": f"{rows.size} seeded i-rows x {n} j of the same N={n} Plummer sphere, FP64 Neumaier sums",
+        "seconds": round(dt, 3),
+    }
+    for name, a in gpu_results.items():
+        out[f"emax_{name}_on_sample"] = oracle.e_max(np.asarray(a, dtype=np.float64)[rows], ref)
+    return out
+
+
+def time_steps(torch, fn, steps, stream, flush):
+    """Per-step CUDA events on `stream`, L2 flushed between steps (outside the events)."""
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for k in range(steps):
+        if flush is not None:
+            flush.zero_()
+        starts[k].record(stream)
+        fn()
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    return [s.elapsed_time(e) for s, e in zip(starts, ends)]
+
+
+def run_ours(args):
+    import torch
+
+    import paper_astro_ph_0703100_gb300 as cn
+    from paper_astro_ph_0703100_gb300 import _build
+
+    rank, world, local = dist_env()
+    device = torch.device("cuda", local % max(torch.cuda.device_count(), 1))
+    torch.cuda.set_device(device)
+    rank, world = dist_init("nccl")
+    if rank == 0 or not os.path.exists(_build.LIB):
+        _build.build()
+    barrier(device)
+    cn.load()
+
+    n = args.n
+    p, eps2 = workload(n, n + rank)  # one independent replica per rank
+    t = torch.from_numpy(p).to(device)
+    stream = torch.cuda.current_stream(device)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
+    acc = torch.empty((n, 3), dtype=torch.float32, device=device)
+    acc_dd = torch.empty((n, 3), dtype=torch.float64, device=device)
+
+    tuned = None
+    if not args.no_autotune:
+        tuned = cn.cn_autotune("f32", t, t, eps2, reps=2)
+        tuned_dd = cn.cn_autotune("dd", t, t, eps2, reps=1)
+    else:
+        tuned_dd = None
+    f32_step = lambda: cn.cn_force(t, t, eps2, acc_out=acc)
+    dd_step = lambda: cn.cn_force_dd(t, t, eps2, acc_out=acc_dd)
+    for _ in range(args.warmup):
+        f32_step()
+    dd_step()
+    torch.cuda.synchronize()
+    if cn.cn_get_device_status() != 0:
+        raise RuntimeError("device status flagged during warm-up")
+
+    sampler = ClockSampler(gpu_selector(torch, device)) if rank == 0 else None
+    barrier(device)
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+    times = time_steps(torch, f32_step, args.steps, stream, flush)
+    if sampler:
+        clocks = sampler.stop()
+    barrier(device)
+    total_s = reduce_max(sum(times) / 1e3, device)
+    mean_kernel_s = reduce_max(statistics.mean(times) / 1e3, device)
+
+    dd_times = time_steps(torch, dd_step, args.dd_steps, stream, flush)
+    dd_mean_s = reduce_max(statistics.mean(dd_times) / 1e3, device)
+    status = cn.cn_get_device_status()
+    if status != 0:
+        raise RuntimeError(f"device status {status} after the timed region")
+
+    # end to end through the host-buffer entry point: pinned input, copies in the timed region
+    host_in = torch.from_numpy(p).pin_memory()
+    host_acc = torch.empty((n, 3), dtype=torch.float32).pin_memory()
+    e2e_steps = max(3, min(args.steps, 50))
+    for _ in range(2):
+        cn.cn_force_host(host_in, host_in, eps2, acc_out=host_acc)
+    barrier(device)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        cn.cn_force_host(host_in, host_in, eps2, acc_out=host_acc)
+    e2e_s = reduce_max((time.perf_counter() - t0), device)
+
+    if rank != 0:
+        return None
+    pairs = float(n) * float(n)
+    value = aggregate_rate(pairs * args.steps, world, total_s)
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    peak = sms * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / ISSUE_PER_PAIR
+    achieved = pairs / mean_kernel_s
+    dd_rate = pairs / dd_mean_s
+    peaks = cn.cn_probe_peaks()
+    obs_mhz = clocks.get("sm_mhz") or SM_MAX_MHZ
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1e3 * total_s / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": value / PAPER_PAIRS_PER_S,
+        "vs_baseline_basis": "paper, GeForce 8800GTX, N=131072: 256 Gflop/s at 38 flop/pair = 6.74e9 pairs/s (context)",
+        "dtype": "f32",
+        "data": "synthetic: seeded Plummer sphere (scale radius 1, total mass 1, no truncation), one replica per rank",
+        "config": {
+            "workload": f"plummer_n{n}_eps4N^-1/3_fp32_accel",
+            "n": n,
+            "eps2": eps2,
+            "pairs_per_step": pairs,
+            "l2": "flushed between timed steps (256 MiB write outside the events); inputs 2 MiB",
+            "launch_shape_f32": tuned or cn.cn_tune_get("f32", n, n),
+            "launch_shape_dd": tuned_dd or cn.cn_tune_get("dd", n, n),
+        },
+        "gflops_at_38": value * FLOP_PER_PAIR / 1e9,
+        "roofline": {
+            "bound": "alu",
+            "achieved": achieved / 1e9,
+            "peak": peak / 1e9,
+            "unit": "Gpair/s",
+            "frac": achieved / peak,
+            "traffic": None,
+            "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {SM_MAX_MHZ:.0f} MHz / "
+                          f"{ISSUE_PER_PAIR} issue slots per pair (12 FP32 + 1 MUFU)",
+            "frac_at_observed_clock": achieved / (peak * obs_mhz / SM_MAX_MHZ),
+            "probe_pair_mix": peaks["pair_mix_per_s"] / 1e9,
+            "probe_ffma_per_s": peaks["ffma_per_s"],
+            "probe_mufu_per_s": peaks["mufu_rsqrt_per_s"],
+        },
+        "compensated": {
+            "value": dd_rate * world,
+            "unit": UNIT,
+            "ms_per_step": 1e3 * dd_mean_s,
+            "frac_of_fp32_peak": dd_rate / peak,
+            "steps": args.dd_steps,
+            "dtype": "f32 pairs, double-single accumulation, f64 output",
+        },
+        "e2e": {
+            "value": aggregate_rate(pairs * e2e_steps, world, e2e_s),
+            "unit": UNIT,
+            "h2d_bytes_per_step": n * 16,
+            "d2h_bytes_per_step": n * 12,
+            "api": "cn_force_host (pinned host buffers; i = j so the records are copied once)",
+        },
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(p, eps2, {"f32": acc.cpu().numpy(), "dd": acc_dd.cpu().numpy()},
+                                            args.cpu_budget)
+    return line
+
+
+def run_reference(args):
+    """The FP64 oracle on this host, same workload; each step a bounded row sample."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return None
+    import oracle
+    from paper_astro_ph_0703100_gb300 import synth
+
+    oracle.compile_oracle()
+    n = args.n
+    p, eps2 = workload(n, n)
+    rows_per_step = args.ref_rows
+    rows = [synth.sample_rows(n, rows_per_step, seed=1000 + k) for k in range(args.warmup + args.steps)]
+    for k in range(args.warmup):
+        oracle.force(p, p, eps2, rows=rows[k], potential=False)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        oracle.force(p, p, eps2, rows=rows[args.warmup + k], potential=False)
+    dt = time.perf_counter() - t0
+    pairs = float(rows_per_step) * n * args.steps
+    value = pairs / dt
+    sample = f"{rows_per_step} seeded i-rows x {n} j per step of the N={n} Plummer sphere, FP64 Neumaier sums"
+    return {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic: seeded Plummer sphere",
+        "config": {"workload": f"plummer_n{n}_eps4N^-1/3_fp32_accel", "n": n, "eps2": eps2},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--dd-steps", type=int, default=20)
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=10.0, help="seconds of oracle work for cpu_baseline")
+    ap.add_argument("--ref-rows", type=int, default=256, help="oracle rows per step of --impl reference")
+    args = ap.parse_args(argv)
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    line = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+    try:
+        import torch.distributed as dist
+
+        if dist.is_available() and dist.is_initialized():
+            dist.destroy_process_group()
+    except Exception:
+        pass
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,301 @@
+/*
+ * cunbody.h - C ABI of libcunbody, softened direct-summation gravity on
+ * NVIDIA GB300 (sm_103a).
+ *
+ * The library computes, for i-particles with positions x_i and
+ * j-particles with positions x_j and masses m_j, the softened acceleration
+ * of Eq. 1 (Section 1.1), with G = 1 and r_ij = r_j - r_i:
+ *
+ *     a_i   =  sum_j m_j (x_j - x_i) / (|x_j - x_i|^2 + eps2)^(3/2)
+ *     phi_i = -sum_{j : x_j != x_i} m_j / (|x_j - x_i|^2 + eps2)^(1/2)
+ *
+ * The call shape follows the library routine of Section 3.1 (Figure
+ * "structure of subroutine of our library": j positions and masses, i
+ * positions, the squared softening eps2, the output accelerations, n_i and
+ * n_j), with positions and masses packed into 16-byte records as in the
+ * appendix driver (JDIM = 4: x, y, z, m).
+ *
+ * Conventions shared by every entry point:
+ *  - Array arguments are DEVICE pointers owned by the caller unless the
+ *    name says "host". Particle arrays are float[n][4] records
+ *    (x, y, z, m), 16-byte aligned (else CN_ERR_MISALIGNED); the 4th
+ *    component of an i-record is ignored. The i and j arrays may be the
+ *    same buffer. Outputs must not overlap inputs.
+ *  - eps2 is the SQUARED softening length (the pipeline descriptions of the
+ *    appendix add it to dx^2 + dy^2 + dz^2); it must be finite and >= 0.
+ *  - A pair with |x_j - x_i|^2 + eps2 == 0 (eps2 = 0 and coincident points)
+ *    contributes nothing. The potential skips every pair whose coordinate
+ *    differences are all exactly zero, so the i = j self term is excluded.
+ *    (Separations below about 1e-19, whose squares flush to zero in FP32,
+ *    count as zero.)
+ *  - n_i == 0 is a no-op; n_j == 0 writes zeros.
+ *  - Calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy
+ *    default stream). Argument errors are detected on the host and returned
+ *    before anything is launched. Results are valid after the stream is
+ *    synchronised. cn_get_device_status reports errors detected inside a
+ *    kernel (every wait inside a kernel is bounded in time).
+ *  - Entry points without a `workspace` argument use a workspace owned by
+ *    the library, kept per (device, stream) and grown on demand; growing it
+ *    allocates, which is not allowed while `stream` is being captured into
+ *    a CUDA graph (CN_ERR_WORKSPACE): make one call on that stream before
+ *    capturing, or use the *_ws forms.
+ *  - Thread safety: concurrent calls are safe on different streams.
+ */
+#ifndef CUNBODY_H
+#define CUNBODY_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define CN_API __attribute__((visibility("default")))
+#else
+#define CN_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t; declared here so the header needs no CUDA headers. */
+typedef struct CUstream_st *cn_stream;
+
+typedef enum cn_status {
+    CN_OK = 0,
+    CN_ERR_INVALID_ARG = 1,        /* a size, pointer or eps2 is invalid                     */
+    CN_ERR_MISALIGNED = 2,         /* a float[n][4] array is not 16-byte aligned             */
+    CN_ERR_CUDA = 3,               /* a CUDA runtime call failed (see cn_last_error_message)  */
+    CN_ERR_TIMEOUT = 4,            /* a kernel gave up waiting (reported by cn_get_device_status) */
+    CN_ERR_UNSUPPORTED_DEVICE = 5, /* the current device is not sm_103 (GB300)               */
+    CN_ERR_WORKSPACE = 6           /* workspace too small, or allocation needed during capture */
+} cn_status;
+
+/* Kernel variants, used by the workspace, tuning and autotuning calls. */
+typedef enum cn_variant {
+    CN_VARIANT_F32 = 0,        /* cn_force without potential      */
+    CN_VARIANT_F32_POT = 1,    /* cn_force with potential         */
+    CN_VARIANT_DD = 2,         /* cn_force_dd without potential   */
+    CN_VARIANT_DD_POT = 3,     /* cn_force_dd with potential      */
+    CN_VARIANT_ADJOINT = 4,    /* cn_force_adjoint                */
+    CN_VARIANT_BATCHED = 5,    /* cn_force_batched                */
+    CN_VARIANT_BATCHED_POT = 6 /* cn_force_batched with potential */
+} cn_variant;
+
+/* Launch shape of the pair kernels. Zero in a field means "library default". */
+typedef struct cn_tune {
+    int32_t i_per_thread; /* i-particles held in registers per thread: 1, 2, 4 or 8              */
+    int32_t threads;      /* threads per CTA: 64, 128 or 256                                      */
+    int32_t j_tile;       /* j records per shared-memory stage: multiple of 8, 8 .. 4096          */
+    int32_t stages;       /* shared-memory ring depth: 2 .. 8                                     */
+    int32_t ctas_per_sm;  /* resident CTAs per SM to launch (0 = occupancy maximum)               */
+    int32_t chunk_units;  /* 0 = static schedule (equal share per CTA); > 0 = dynamic queue chunks
+                             of this many (i-tile x j-tile) units                                 */
+} cn_tune;
+
+/* ------------------------------------------------------------------ force */
+
+/*
+ * Plain FP32 direct sum (Eq. 1, and the potential when pot_out != NULL).
+ *   n_i, pos_i       : i-particles, float[n_i][4] (4th component ignored)
+ *   n_j, pos_mass_j  : j-particles, float[n_j][4] (x, y, z, m)
+ *   eps2             : squared softening (finite, >= 0)
+ *   acc_out          : float[n_i][3] accelerations (written)
+ *   pot_out          : float[n_i] potentials phi_i, or NULL
+ * FP32 pair arithmetic with the MUFU inverse square root; each j-tile's
+ * FP32 partial is folded into an FP32 running sum (the FORCE-LOOP of
+ * Section 2.2.2, Eq. 3); partial sums of i-tiles split across CTAs are
+ * merged in FP64 in a fixed order, so results are bitwise reproducible for
+ * a given launch shape.
+ */
+CN_API cn_status cn_force(int64_t n_i, const float *pos_i, int64_t n_j, const float *pos_mass_j, float eps2,
+                   float *acc_out, float *pot_out, cn_stream stream);
+
+/* cn_force with a caller-owned workspace of ws_bytes >= cn_workspace_bytes(
+ * pot_out ? CN_VARIANT_F32_POT : CN_VARIANT_F32, n_i, n_j), 256-byte
+ * aligned. Its first 4 KiB must be zero before the first use (every call
+ * leaves them zero); the rest needs no initialisation and may hold anything
+ * between calls. No allocation happens inside this call. Calls sharing a
+ * workspace must not overlap in time on the device. */
+CN_API cn_status cn_force_ws(int64_t n_i, const float *pos_i, int64_t n_j, const float *pos_mass_j, float eps2,
+                      float *acc_out, float *pot_out, void *workspace, size_t ws_bytes, cn_stream stream);
+
+/*
+ * Compensated ("split-precision") direct sum with FP64 outputs.
+ *   acc_out : double[n_i][3]; pot_out : double[n_i] or NULL; other
+ *   arguments as cn_force.
+ * FP32 instructions only: every quantity of the pair term (x_j - x_i, the
+ * softened squared distance, its inverse square root from the MUFU
+ * estimate plus an FMA-formed residual, the cube, the mass and direction
+ * products) is carried as a double-single (hi, lo) pair with each rounding
+ * recovered by TwoSum or an FMA, and every term is added to a
+ * double-single running sum with Knuth's TwoSum. Partial sums of split
+ * i-tiles are merged in FP64 in a fixed order. Per-particle relative error
+ * against an exact sum is of order 1e-10 or below (the FP32 form: ~1e-6).
+ * The wide accumulators of the GRAPE pipelines (Section 2.1) and the
+ * FORCE-LOOP error analysis (Section 2.2.2) motivate the form.
+ */
+CN_API cn_status cn_force_dd(int64_t n_i, const float *pos_i, int64_t n_j, const float *pos_mass_j, float eps2,
+                      double *acc_out, double *pot_out, cn_stream stream);
+
+/* cn_force_dd with a caller-owned workspace (same rules as cn_force_ws,
+ * sized by CN_VARIANT_DD / CN_VARIANT_DD_POT). */
+CN_API cn_status cn_force_dd_ws(int64_t n_i, const float *pos_i, int64_t n_j, const float *pos_mass_j, float eps2,
+                         double *acc_out, double *pot_out, void *workspace, size_t ws_bytes, cn_stream stream);
+
+/* Workspace bytes that a call of `variant` with these sizes needs under the
+ * launch shape currently selected for them (see cn_tune_get). For
+ * CN_VARIANT_ADJOINT pass n_i = n_j = n. Returns 0 for invalid input. */
+CN_API size_t cn_workspace_bytes(int variant, int64_t n_i, int64_t n_j);
+
+/* ------------------------------------------------------------------ batched */
+
+/* An ensemble of independent systems ("clusters") stored back to back:
+ * cluster c owns records offsets[c] .. offsets[c+1]-1 and softening
+ * eps2[c]; every cluster is its own i set and j set. A plan holds the
+ * (cluster, i-tile, j-tile) unit table in device memory; it is built once
+ * per ensemble shape on the current device. This is the many-small-systems
+ * use of Section 4.3 (groups of particles sharing one interaction list in
+ * the modified tree algorithm) in a single persistent launch. */
+typedef struct cn_batch_plan cn_batch_plan;
+
+/* offsets_host: int64[n_clusters + 1], non-decreasing, offsets_host[0] == 0;
+ * eps2_host: float[n_clusters]; tune: launch shape or NULL (default or the
+ * shape stored by cn_tune_set for CN_VARIANT_BATCHED); with_potential:
+ * nonzero to reserve the potential form. Allocates device memory. */
+CN_API cn_status cn_batch_plan_create(int32_t n_clusters, const int64_t *offsets_host, const float *eps2_host,
+                               const cn_tune *tune, int with_potential, cn_batch_plan **plan_out);
+CN_API cn_status cn_batch_plan_destroy(cn_batch_plan *plan);
+/* Workspace bytes a cn_force_batched call on this plan needs. */
+CN_API size_t cn_batch_plan_workspace_bytes(const cn_batch_plan *plan);
+/* Number of particles (offsets[n_clusters]) and pair interactions
+ * (sum_c N_c^2) the plan covers; either pointer may be NULL. */
+CN_API cn_status cn_batch_plan_info(const cn_batch_plan *plan, int64_t *n_total, double *pairs);
+
+/*
+ * One persistent launch over all clusters of `plan`.
+ *   pos_mass  : float[n_total][4] records of all clusters
+ *   acc_out   : float[n_total][3]; pot_out : float[n_total] or NULL
+ *   workspace : caller-owned, >= cn_batch_plan_workspace_bytes(plan) bytes,
+ *               256-byte aligned, its first 4 KiB zero before first use
+ *               (every call leaves them zero); NULL to use the library
+ *               workspace of `stream`.
+ * No allocation happens when a workspace is passed, so the call can be
+ * captured into a CUDA graph (see cn_batch_plan_capture).
+ */
+CN_API cn_status cn_force_batched(const cn_batch_plan *plan, const float *pos_mass, float *acc_out, float *pot_out,
+                           void *workspace, size_t ws_bytes, cn_stream stream);
+
+/* Captures cn_force_batched with these arguments into a CUDA graph owned by
+ * the plan (replacing any earlier one); cn_batch_plan_launch replays it. */
+CN_API cn_status cn_batch_plan_capture(cn_batch_plan *plan, const float *pos_mass, float *acc_out, float *pot_out,
+                                void *workspace, size_t ws_bytes, cn_stream stream);
+CN_API cn_status cn_batch_plan_launch(const cn_batch_plan *plan, cn_stream stream);
+
+/* ------------------------------------------------------------------ adjoint */
+
+/*
+ * Gradient of L = sum_i w_i . a_i (i set = j set = all n particles) with
+ * respect to every position and mass, in one O(n^2) pass:
+ *   dL/dx_k = sum_p [ g u - 3 h (d . u) d ],  dL/dm_k = -sum_p g (w_p . d)
+ * with d = x_p - x_k, s = |d|^2 + eps2, g = s^-3/2, h = s^-5/2,
+ * u = m_k w_p - m_p w_k. The paper has no adjoint; this is the derivative
+ * of Eq. 1.
+ *   pos_mass  : float[n][4]; w : float[n][3] (any 4-byte alignment)
+ *   grad_pos  : float[n][3]; grad_mass : float[n] (both written)
+ * FP32 pair arithmetic, per-tile FP32 partials, FP64 merge of split tiles.
+ */
+CN_API cn_status cn_force_adjoint(int64_t n, const float *pos_mass, float eps2, const float *w, float *grad_pos,
+                           float *grad_mass, cn_stream stream);
+
+/* ------------------------------------------------------------------ potential energy */
+
+/* W = 1/2 sum_i m_i phi_i accumulated in FP64 in a fixed order.
+ * pos_mass: float[n][4] (masses in the 4th component); pot: float[n]
+ * (cn_potential_energy) or double[n] (cn_potential_energy_dd);
+ * w_out: ONE double in device memory (written). */
+CN_API cn_status cn_potential_energy(int64_t n, const float *pos_mass, const float *pot, double *w_out, cn_stream stream);
+CN_API cn_status cn_potential_energy_dd(int64_t n, const float *pos_mass, const double *pot, double *w_out,
+                                 cn_stream stream);
+
+/* ------------------------------------------------------------------ host-memory forms */
+
+/* cn_force on HOST buffers: copies pos_i and pos_mass_j to the device,
+ * evaluates, copies acc (and pot) back and returns when they are in host
+ * memory. Uses device buffers kept by the library per (device, stream).
+ * Pinned host memory gives the fastest copies. */
+CN_API cn_status cn_force_host(int64_t n_i, const float *pos_i_host, int64_t n_j, const float *pos_mass_j_host, float eps2,
+                        float *acc_host, float *pot_host, cn_stream stream);
+
+/* The library routine exactly as Section 3.1 states it: FP64 host arrays
+ * xj[nj][3], mj[nj], xi[ni][3], the squared softening eps2 and the output
+ * a[ni][3]. Values are rounded to FP32 records (as the appendix driver
+ * packs them), evaluated with cn_force on the legacy default stream, and
+ * widened back. Synchronous. */
+CN_API cn_status cn_force_host_f64(const double *xj, const double *mj, const double *xi, double eps2, double *a, int ni,
+                            int nj);
+
+/* ------------------------------------------------------------------ tuning */
+
+/* Launch shape that calls of `variant` with these sizes will use on the
+ * current device: an entry set by cn_tune_set / cn_autotune for the size
+ * class (ceil(log2 n_i), ceil(log2 n_j)), else the built-in heuristic. */
+CN_API cn_status cn_tune_get(int variant, int64_t n_i, int64_t n_j, cn_tune *out);
+/* Stores (tune != NULL) or clears (tune == NULL) the shape for the size class. */
+CN_API cn_status cn_tune_set(int variant, int64_t n_i, int64_t n_j, const cn_tune *tune);
+
+/*
+ * Times every candidate launch shape for `variant` on these inputs (CUDA
+ * events on `stream`, best of `reps`), stores the fastest with cn_tune_set
+ * and returns it in best_out. Outputs are overwritten; synchronises
+ * `stream`. For the DD variants acc_out/pot_out point to double arrays,
+ * for the F32 variants to float arrays. Not for CN_VARIANT_ADJOINT or the
+ * batched variants (see cn_autotune_batched).
+ */
+CN_API cn_status cn_autotune(int variant, int64_t n_i, const float *pos_i, int64_t n_j, const float *pos_mass_j,
+                      float eps2, void *acc_out, void *pot_out, int reps, cn_stream stream, cn_tune *best_out);
+
+/* Times candidate shapes for a batched ensemble (building a plan for each),
+ * returns the fastest in best_out and stores it for CN_VARIANT_BATCHED /
+ * CN_VARIANT_BATCHED_POT keyed by (number of clusters, total particles). */
+CN_API cn_status cn_autotune_batched(int32_t n_clusters, const int64_t *offsets_host, const float *eps2_host,
+                              const float *pos_mass, float *acc_out, float *pot_out, int reps, cn_stream stream,
+                              cn_tune *best_out);
+
+/* ------------------------------------------------------------------ status, probes */
+
+/* Synchronises `stream` and reports CN_ERR_TIMEOUT if any kernel of this
+ * library on the current device flagged a timed-out wait since the last
+ * call (the flag is then cleared and library workspaces are re-zeroed), or
+ * CN_ERR_CUDA if the synchronisation failed. */
+CN_API cn_status cn_get_device_status(cn_stream stream);
+
+/* Sets the bound on every in-kernel wait, in nanoseconds (default 2e9);
+ * 0 restores the default. Applies to launches made after the call. */
+CN_API cn_status cn_set_wait_limit_ns(uint64_t ns);
+
+/* Launches one kernel that waits on a shared-memory barrier which nothing
+ * completes, bounded by the current wait limit: the kernel then flags a
+ * timeout and returns. Lets a test exercise the timeout path without a
+ * hang; follow with cn_get_device_status. */
+CN_API cn_status cn_debug_timeout_probe(cn_stream stream);
+
+/* Measured issue rates of the current device (one probe kernel each):
+ *   out[0] FP32 FFMA lane operations per second,
+ *   out[1] MUFU inverse square roots per second,
+ *   out[2] pair-equivalent rate of a loop of 12 FP32 + 1 MUFU per pair,
+ *   out[3] mean SM clock during the probes in MHz,
+ *   out[4] number of SMs.
+ * Synchronises `stream`. */
+CN_API cn_status cn_probe_peaks(cn_stream stream, double *out5);
+
+CN_API const char *cn_status_string(cn_status status);
+/* Detail of the last error on the calling thread (empty if none). */
+CN_API const char *cn_last_error_message(void);
+/* Library version string. */
+CN_API const char *cn_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CUNBODY_H */

@@ -1,0 +1,1105 @@
+// Host side of the libcunbody C ABI (include/cunbody.h): argument checks,
+// launch-shape selection, workspaces, dispatch to the kernels, batched
+// plans, host-memory forms, tuning and status.
+#include "../../include/cunbody.h"
+#include "cn_kernels.h"
+
+#include <algorithm>
+#include <atomic>
+#include <cfloat>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+namespace cn {
+cudaError_t device_status_address(int** p);
+cudaError_t launch_timeout_probe(int* status, uint64_t wait_ns, cudaStream_t s);
+cudaError_t run_probes(cudaStream_t s, double* out);
+size_t energy_workspace_doubles();
+}  // namespace cn
+
+using cn::Plan;
+using cn::PairArgs;
+
+struct cn_batch_plan {
+  int dev = -1;
+  int32_t n_clusters = 0;
+  int64_t n_total = 0;
+  double pairs = 0.0;
+  Plan plan;
+  bool guard = false;
+  bool pot = false;
+  cn::TileDesc* d_tiles = nullptr;
+  int32_t n_tiles = 0;
+  int64_t units = 0;
+  int64_t n_chunks = 0;
+  int grid = 0;
+  size_t ws_bytes = 0;
+  size_t off_partials = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+constexpr size_t kCtrlBytes = 4096;  // queue words and spare control space at the head of a workspace
+constexpr uint64_t kDefaultWaitNs = 2000000000ull;
+constexpr size_t kMaxSmem = 227 * 1024;
+
+thread_local std::string g_last_error;
+std::atomic<uint64_t> g_wait_ns{kDefaultWaitNs};
+std::atomic<uint32_t> g_epoch{1};
+
+// A fresh nonzero launch number for the split-tile arrival counters.
+uint32_t next_epoch() {
+  uint32_t e = g_epoch.fetch_add(1);
+  if (e == 0) e = g_epoch.fetch_add(1);
+  return e;
+}
+
+cn_status fail(cn_status st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+
+cn_status fail_cuda(cudaError_t e, const char* what) {
+  g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  return CN_ERR_CUDA;
+}
+
+// Host-side fault injection for tests: CN_FAULT_INJECT holds a comma list of
+// "alloc", "launch", "capture"; the matching step then fails as if the CUDA
+// call had failed. Nothing is done on the device.
+bool inject(const char* point) {
+  const char* v = std::getenv("CN_FAULT_INJECT");
+  return v && std::strstr(v, point) != nullptr;
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
+  if (!a || !b || na == 0 || nb == 0) return false;
+  const auto pa = reinterpret_cast<uintptr_t>(a), pb = reinterpret_cast<uintptr_t>(b);
+  return pa < pb + nb && pb < pa + na;
+}
+
+// ------------------------------------------------------------------ devices
+struct DeviceInfo {
+  int sms = 0;
+  int major = 0;
+  int minor = 0;
+  int* status = nullptr;
+  bool supported = false;
+};
+
+std::mutex g_mu;  // guards the maps below
+std::map<int, DeviceInfo> g_devices;
+
+cn_status current_device(int* dev_out, DeviceInfo** info) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail_cuda(e, "cudaGetDevice");
+  std::lock_guard<std::mutex> lock(g_mu);
+  auto it = g_devices.find(dev);
+  if (it == g_devices.end()) {
+    DeviceInfo d;
+    if ((e = cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&d.major, cudaDevAttrComputeCapabilityMajor, dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&d.minor, cudaDevAttrComputeCapabilityMinor, dev)) != cudaSuccess)
+      return fail_cuda(e, "cudaDeviceGetAttribute");
+    d.supported = (d.major == 10 && d.minor == 3);
+    if (d.supported && (e = cn::device_status_address(&d.status)) != cudaSuccess)
+      return fail_cuda(e, "cudaGetSymbolAddress(device status)");
+    it = g_devices.emplace(dev, d).first;
+  }
+  if (!it->second.supported)
+    return fail(CN_ERR_UNSUPPORTED_DEVICE, "libcunbody is built for sm_103a (GB300); device " + std::to_string(dev) +
+                                               " is sm_" + std::to_string(it->second.major) +
+                                               std::to_string(it->second.minor));
+  if (dev_out) *dev_out = dev;
+  *info = &it->second;
+  return CN_OK;
+}
+
+// ------------------------------------------------------------------ library workspaces
+struct LibWorkspace {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+  double* aux = nullptr;  // potential-energy block sums + counter
+};
+std::map<std::pair<int, cudaStream_t>, LibWorkspace> g_ws;
+
+bool capturing(cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) return false;
+  return cs != cudaStreamCaptureStatusNone;
+}
+
+cn_status library_workspace(cudaStream_t s, size_t need, void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail_cuda(e, "cudaGetDevice");
+  std::lock_guard<std::mutex> lock(g_mu);
+  LibWorkspace& w = g_ws[{dev, s}];
+  if (w.ptr && w.bytes >= need) {
+    *out = w.ptr;
+    return CN_OK;
+  }
+  if (inject("capture") || capturing(s))
+    return fail(CN_ERR_WORKSPACE,
+                "the library workspace of this stream must grow, which allocates; not allowed during graph "
+                "capture (make one call before capturing, or pass a workspace)");
+  if (inject("alloc")) return fail(CN_ERR_CUDA, "cudaMalloc: injected allocation failure");
+  if (w.ptr) {
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return fail_cuda(e, "cudaStreamSynchronize");
+    cudaFree(w.ptr);
+    w.ptr = nullptr;
+    w.bytes = 0;
+  }
+  const size_t nb = align_up(std::max(need, static_cast<size_t>(1) << 20), static_cast<size_t>(1) << 20);
+  void* p = nullptr;
+  if ((e = cudaMalloc(&p, nb)) != cudaSuccess) return fail_cuda(e, "cudaMalloc(workspace)");
+  if ((e = cudaMemsetAsync(p, 0, nb, s)) != cudaSuccess) {
+    cudaFree(p);
+    return fail_cuda(e, "cudaMemsetAsync(workspace)");
+  }
+  w.ptr = p;
+  w.bytes = nb;
+  *out = p;
+  return CN_OK;
+}
+
+cn_status library_aux(cudaStream_t s, double** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail_cuda(e, "cudaGetDevice");
+  std::lock_guard<std::mutex> lock(g_mu);
+  LibWorkspace& w = g_ws[{dev, s}];
+  if (!w.aux) {
+    if (inject("capture") || capturing(s))
+      return fail(CN_ERR_WORKSPACE, "first potential-energy call on a stream allocates; not allowed during capture");
+    if (inject("alloc")) return fail(CN_ERR_CUDA, "cudaMalloc: injected allocation failure");
+    const size_t nb = (cn::energy_workspace_doubles() + 1) * sizeof(double);
+    if ((e = cudaMalloc(reinterpret_cast<void**>(&w.aux), nb)) != cudaSuccess) return fail_cuda(e, "cudaMalloc(aux)");
+    if ((e = cudaMemsetAsync(w.aux, 0, nb, s)) != cudaSuccess) return fail_cuda(e, "cudaMemsetAsync(aux)");
+  }
+  *out = w.aux;
+  return CN_OK;
+}
+
+// ------------------------------------------------------------------ tuning
+std::map<std::tuple<int, int, int, int>, cn_tune> g_tune;
+
+int bucket(int64_t n) {
+  int b = 0;
+  while (b < 62 && (static_cast<int64_t>(1) << b) < n) ++b;
+  return b;
+}
+
+bool valid_k(int variant, int k) {
+  if (variant == cn::kDD || variant == cn::kDDPot || variant == cn::kAdjoint) return k == 1 || k == 2 || k == 4;
+  return k == 1 || k == 2 || k == 4 || k == 8;
+}
+
+cn_tune default_tune(int variant, int64_t n_i, int64_t n_j) {
+  cn_tune t{};
+  const int64_t n = std::max(n_i, n_j);
+  const bool dd = variant == cn::kDD || variant == cn::kDDPot;
+  const bool adj = variant == cn::kAdjoint;
+  t.stages = 4;
+  t.threads = 128;
+  if (variant == cn::kBatched || variant == cn::kBatchedPot) {
+    t.i_per_thread = 4;
+    t.j_tile = 256;
+  } else if (n >= 32768) {
+    t.i_per_thread = adj ? 2 : (dd ? 4 : 8);
+    t.j_tile = 512;
+  } else if (n >= 4096) {
+    t.i_per_thread = adj ? 2 : 4;
+    t.j_tile = 256;
+  } else {
+    t.i_per_thread = adj ? 1 : 2;
+    t.threads = 64;
+    t.j_tile = 128;
+  }
+  return t;
+}
+
+cn_status check_tune(int variant, const cn_tune& t) {
+  if (t.i_per_thread && !valid_k(variant, t.i_per_thread))
+    return fail(CN_ERR_INVALID_ARG, "i_per_thread must be 1, 2, 4 or 8 (compensated and adjoint forms: 1, 2, 4)");
+  if (t.threads && t.threads != 64 && t.threads != 128 && t.threads != 256)
+    return fail(CN_ERR_INVALID_ARG, "threads must be 64, 128 or 256");
+  if (t.j_tile && (t.j_tile < 8 || t.j_tile > 4096 || t.j_tile % 8))
+    return fail(CN_ERR_INVALID_ARG, "j_tile must be a multiple of 8 in 8..4096");
+  if (t.stages && (t.stages < 2 || t.stages > 8)) return fail(CN_ERR_INVALID_ARG, "stages must be 2..8");
+  if (t.ctas_per_sm < 0 || t.chunk_units < 0) return fail(CN_ERR_INVALID_ARG, "negative tuning field");
+  return CN_OK;
+}
+
+cn_status resolve_plan(int dev, int variant, int64_t n_i, int64_t n_j, bool guard, const cn_tune* explicit_tune,
+                       Plan* p) {
+  cn_tune t = default_tune(variant, n_i, n_j);
+  cn_tune chosen{};
+  bool have = false;
+  if (explicit_tune) {
+    chosen = *explicit_tune;
+    have = true;
+  } else {
+    std::lock_guard<std::mutex> lock(g_mu);
+    auto it = g_tune.find({dev, variant, bucket(n_i), bucket(n_j)});
+    if (it != g_tune.end()) {
+      chosen = it->second;
+      have = true;
+    }
+  }
+  if (have) {
+    cn_status st = check_tune(variant, chosen);
+    if (st != CN_OK) return st;
+    if (chosen.i_per_thread) t.i_per_thread = chosen.i_per_thread;
+    if (chosen.threads) t.threads = chosen.threads;
+    if (chosen.j_tile) t.j_tile = chosen.j_tile;
+    if (chosen.stages) t.stages = chosen.stages;
+    t.ctas_per_sm = chosen.ctas_per_sm;
+    t.chunk_units = chosen.chunk_units;
+  }
+  p->k = guard ? 1 : t.i_per_thread;
+  p->threads = t.threads;
+  p->j_tile = t.j_tile;
+  p->stages = t.stages;
+  p->ctas_per_sm = t.ctas_per_sm;
+  p->chunk_units = t.chunk_units;
+  const size_t smem = variant == cn::kAdjoint ? cn::adjoint_smem_bytes(*p) : cn::ring_smem_bytes(*p);
+  if (smem > kMaxSmem) return fail(CN_ERR_INVALID_ARG, "j_tile x stages exceeds the shared memory of one CTA");
+  return CN_OK;
+}
+
+// ------------------------------------------------------------------ geometry
+struct Geometry {
+  int64_t n_tiles = 0;
+  int64_t njt = 0;
+  int64_t units = 0;
+  int64_t n_chunks = 0;
+  int grid = 0;
+  size_t smem = 0;
+  size_t off_partials = 0;
+  size_t off_wrec = 0;
+  size_t ws_bytes = 0;
+};
+
+std::map<std::tuple<int, int, bool, bool, int, int, size_t>, int> g_occ;
+
+cn_status occupancy(int dev, int variant, bool guard, const Plan& p, size_t smem, int* ctas) {
+  const auto key = std::make_tuple(dev, variant, guard, false, p.k, p.threads, smem);
+  {
+    std::lock_guard<std::mutex> lock(g_mu);
+    auto it = g_occ.find(key);
+    if (it != g_occ.end()) {
+      *ctas = it->second;
+      return CN_OK;
+    }
+  }
+  int c = 0;
+  cudaError_t e;
+  switch (variant) {
+    case cn::kF32: e = cn::occupancy_f32(p, false, guard, false, smem, &c); break;
+    case cn::kF32Pot: e = cn::occupancy_f32(p, true, guard, false, smem, &c); break;
+    case cn::kDD: e = cn::occupancy_dd(p, false, guard, smem, &c); break;
+    case cn::kDDPot: e = cn::occupancy_dd(p, true, guard, smem, &c); break;
+    case cn::kAdjoint: e = cn::occupancy_adjoint(p, guard, smem, &c); break;
+    case cn::kBatched: e = cn::occupancy_f32(p, false, guard, true, smem, &c); break;
+    case cn::kBatchedPot: e = cn::occupancy_f32(p, true, guard, true, smem, &c); break;
+    default: return fail(CN_ERR_INVALID_ARG, "unknown variant");
+  }
+  if (e != cudaSuccess) return fail_cuda(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+  if (c <= 0) return fail(CN_ERR_INVALID_ARG, "launch shape does not fit on one SM");
+  std::lock_guard<std::mutex> lock(g_mu);
+  g_occ[key] = c;
+  *ctas = c;
+  return CN_OK;
+}
+
+int slot_f4(int variant) { return (variant == cn::kDD || variant == cn::kDDPot) ? 2 : 1; }
+
+// Grid and workspace layout for `units` units over `n_tiles` i-tiles.
+cn_status layout(int dev, const DeviceInfo& d, int variant, bool guard, const Plan& p, int64_t n_tiles,
+                 int64_t units, int64_t n_wrec, Geometry* g) {
+  g->n_tiles = n_tiles;
+  g->units = units;
+  g->smem = variant == cn::kAdjoint ? cn::adjoint_smem_bytes(p) : cn::ring_smem_bytes(p);
+  int occ = 0;
+  cn_status st = occupancy(dev, variant, guard, p, g->smem, &occ);
+  if (st != CN_OK) return st;
+  const int ctas = p.ctas_per_sm > 0 ? std::min(p.ctas_per_sm, occ) : occ;
+  const int64_t slots = static_cast<int64_t>(ctas) * d.sms;
+  if (p.chunk_units == 0) {
+    g->n_chunks = std::min<int64_t>(slots, units);
+    g->grid = static_cast<int>(g->n_chunks);
+  } else {
+    g->n_chunks = ceil_div(units, p.chunk_units);
+    g->grid = static_cast<int>(std::min<int64_t>(slots, g->n_chunks));
+  }
+  if (g->n_tiles > INT32_MAX || g->n_chunks > INT32_MAX)
+    return fail(CN_ERR_INVALID_ARG, "problem too large for one launch");
+  const size_t counters = align_up(kCtrlBytes + static_cast<size_t>(n_tiles) * 8, 256);
+  g->off_partials = counters;
+  const size_t partial_bytes =
+      static_cast<size_t>(g->n_chunks) * 2 * static_cast<size_t>(p.i_tile()) * 16 * slot_f4(variant);
+  g->off_wrec = align_up(g->off_partials + partial_bytes, 256);
+  g->ws_bytes = g->off_wrec + static_cast<size_t>(n_wrec) * 16;
+  return CN_OK;
+}
+
+cn_status single_geometry(int dev, const DeviceInfo& d, int variant, bool guard, const Plan& p, int64_t n_i,
+                          int64_t n_j, Geometry* g) {
+  const int64_t n_tiles = ceil_div(n_i, p.i_tile());
+  const int64_t njt = ceil_div(n_j, p.j_tile);
+  if (njt > INT32_MAX) return fail(CN_ERR_INVALID_ARG, "n_j too large");
+  g->njt = njt;
+  return layout(dev, d, variant, guard, p, n_tiles, n_tiles * njt, variant == cn::kAdjoint ? n_i : 0, g);
+}
+
+PairArgs base_args(void* ws, const Geometry& g, const Plan& p, int* status) {
+  PairArgs a{};
+  char* base = static_cast<char*>(ws);
+  a.queue = reinterpret_cast<int*>(base);
+  a.counters = reinterpret_cast<unsigned long long*>(base + kCtrlBytes);
+  a.partials = reinterpret_cast<float4*>(base + g.off_partials);
+  a.status = status;
+  a.total_units = g.units;
+  a.chunk_units = p.chunk_units;
+  a.n_chunks = g.n_chunks;
+  a.n_tiles = static_cast<int32_t>(g.n_tiles);
+  a.njt = static_cast<int32_t>(g.njt);
+  a.j_tile = p.j_tile;
+  a.stages = p.stages;
+  a.wait_ns = g_wait_ns.load();
+  a.epoch = next_epoch();
+  return a;
+}
+
+cn_status check_eps2(float eps2) {
+  if (!std::isfinite(eps2) || eps2 < 0.f) return fail(CN_ERR_INVALID_ARG, "eps2 must be finite and >= 0");
+  return CN_OK;
+}
+
+// eps2 below the smallest normal float can make s flush to zero: take the guarded kernels.
+bool needs_guard(float eps2) { return !(eps2 >= FLT_MIN); }
+
+cn_status check_records(const float* p, int64_t n, const char* name) {
+  if (n > 0 && !p) return fail(CN_ERR_INVALID_ARG, std::string(name) + " is NULL");
+  if (p && !aligned(p, 16)) return fail(CN_ERR_MISALIGNED, std::string(name) + " must be 16-byte aligned");
+  return CN_OK;
+}
+
+// ------------------------------------------------------------------ single-system force
+cn_status force_common(bool dd, int64_t n_i, const float* pos_i, int64_t n_j, const float* pos_mass_j,
+                       float eps2, void* acc_out, void* pot_out, void* ws, size_t ws_bytes, bool lib_ws,
+                       cudaStream_t s) {
+  if (n_i < 0 || n_j < 0) return fail(CN_ERR_INVALID_ARG, "n_i and n_j must be >= 0");
+  cn_status st;
+  if ((st = check_eps2(eps2)) != CN_OK) return st;
+  if ((st = check_records(pos_i, n_i, "pos_i")) != CN_OK) return st;
+  if ((st = check_records(pos_mass_j, n_j, "pos_mass_j")) != CN_OK) return st;
+  const size_t elt = dd ? sizeof(double) : sizeof(float);
+  if (n_i > 0 && !acc_out) return fail(CN_ERR_INVALID_ARG, "acc_out is NULL");
+  if ((acc_out && !aligned(acc_out, elt)) || (pot_out && !aligned(pot_out, elt)))
+    return fail(CN_ERR_MISALIGNED, "outputs must be aligned to their element size");
+  const size_t acc_b = static_cast<size_t>(n_i) * 3 * elt, pot_b = pot_out ? static_cast<size_t>(n_i) * elt : 0;
+  const size_t pi_b = static_cast<size_t>(n_i) * 16, pj_b = static_cast<size_t>(n_j) * 16;
+  if (overlaps(acc_out, acc_b, pos_i, pi_b) || overlaps(acc_out, acc_b, pos_mass_j, pj_b) ||
+      overlaps(pot_out, pot_b, pos_i, pi_b) || overlaps(pot_out, pot_b, pos_mass_j, pj_b) ||
+      overlaps(acc_out, acc_b, pot_out, pot_b))
+    return fail(CN_ERR_INVALID_ARG, "outputs overlap inputs or each other");
+  if (n_i == 0) return CN_OK;
+  int dev = 0;
+  DeviceInfo* d = nullptr;
+  if ((st = current_device(&dev, &d)) != CN_OK) return st;
+  cudaError_t e;
+  if (n_j == 0) {
+    if ((e = cudaMemsetAsync(acc_out, 0, acc_b, s)) != cudaSuccess) return fail_cuda(e, "cudaMemsetAsync");
+    if (pot_out && (e = cudaMemsetAsync(pot_out, 0, pot_b, s)) != cudaSuccess) return fail_cuda(e, "cudaMemsetAsync");
+    return CN_OK;
+  }
+  const bool pot = pot_out != nullptr;
+  const bool guard = needs_guard(eps2);
+  const int variant = dd ? (pot ? cn::kDDPot : cn::kDD) : (pot ? cn::kF32Pot : cn::kF32);
+  Plan p;
+  if ((st = resolve_plan(dev, variant, n_i, n_j, guard, nullptr, &p)) != CN_OK) return st;
+  Geometry g;
+  if ((st = single_geometry(dev, *d, variant, guard, p, n_i, n_j, &g)) != CN_OK) return st;
+  if (lib_ws) {
+    if ((st = library_workspace(s, g.ws_bytes, &ws)) != CN_OK) return st;
+  } else if (!ws || ws_bytes < g.ws_bytes) {
+    return fail(CN_ERR_WORKSPACE, "workspace smaller than cn_workspace_bytes()");
+  } else if (!aligned(ws, 256)) {
+    return fail(CN_ERR_MISALIGNED, "workspace must be 256-byte aligned");
+  }
+  PairArgs a = base_args(ws, g, p, d->status);
+  a.pos_i = reinterpret_cast<const float4*>(pos_i);
+  a.pos_j = reinterpret_cast<const float4*>(pos_mass_j);
+  a.acc_out = acc_out;
+  a.pot_out = pot_out;
+  a.n_i = n_i;
+  a.n_j = n_j;
+  a.eps2 = eps2;
+  if (inject("launch")) return fail(CN_ERR_CUDA, "kernel launch: injected launch failure");
+  e = dd ? cn::launch_dd(a, p, pot, guard, g.grid, s) : cn::launch_f32(a, p, pot, guard, false, g.grid, s);
+  if (e != cudaSuccess) return fail_cuda(e, "pair kernel launch");
+  return CN_OK;
+}
+
+cn_status run_batched(const cn_batch_plan* plan, const float* pos_mass, float* acc_out, float* pot_out, void* ws,
+                      size_t ws_bytes, cudaStream_t s) {
+  if (!plan) return fail(CN_ERR_INVALID_ARG, "plan is NULL");
+  cn_status st;
+  if ((st = check_records(pos_mass, plan->n_total, "pos_mass")) != CN_OK) return st;
+  if (plan->n_total > 0 && !acc_out) return fail(CN_ERR_INVALID_ARG, "acc_out is NULL");
+  if ((acc_out && !aligned(acc_out, 4)) || (pot_out && !aligned(pot_out, 4)))
+    return fail(CN_ERR_MISALIGNED, "outputs must be 4-byte aligned");
+  if (pot_out && !plan->pot) return fail(CN_ERR_INVALID_ARG, "plan was created without the potential form");
+  const size_t n = static_cast<size_t>(plan->n_total);
+  if (overlaps(acc_out, n * 12, pos_mass, n * 16) || overlaps(pot_out, n * 4, pos_mass, n * 16) ||
+      overlaps(acc_out, n * 12, pot_out, n * 4))
+    return fail(CN_ERR_INVALID_ARG, "outputs overlap inputs or each other");
+  int dev = 0;
+  DeviceInfo* d = nullptr;
+  if ((st = current_device(&dev, &d)) != CN_OK) return st;
+  if (dev != plan->dev) return fail(CN_ERR_INVALID_ARG, "plan was built on another device");
+  if (plan->units == 0) {
+    cudaError_t e;
+    if (n && (e = cudaMemsetAsync(acc_out, 0, n * 12, s)) != cudaSuccess) return fail_cuda(e, "cudaMemsetAsync");
+    if (n && pot_out && (e = cudaMemsetAsync(pot_out, 0, n * 4, s)) != cudaSuccess)
+      return fail_cuda(e, "cudaMemsetAsync");
+    return CN_OK;
+  }
+  if (!ws) {
+    if ((st = library_workspace(s, plan->ws_bytes, &ws)) != CN_OK) return st;
+  } else if (ws_bytes < plan->ws_bytes) {
+    return fail(CN_ERR_WORKSPACE, "workspace smaller than cn_batch_plan_workspace_bytes()");
+  } else if (!aligned(ws, 256)) {
+    return fail(CN_ERR_MISALIGNED, "workspace must be 256-byte aligned");
+  }
+  Geometry g;
+  g.units = plan->units;
+  g.n_chunks = plan->n_chunks;
+  g.n_tiles = plan->n_tiles;
+  g.off_partials = plan->off_partials;
+  PairArgs a = base_args(ws, g, plan->plan, d->status);
+  a.pos_i = reinterpret_cast<const float4*>(pos_mass);
+  a.pos_j = reinterpret_cast<const float4*>(pos_mass);
+  a.acc_out = acc_out;
+  a.pot_out = pot_out;
+  a.tiles = plan->d_tiles;
+  a.n_i = plan->n_total;
+  a.n_j = plan->n_total;
+  if (inject("launch")) return fail(CN_ERR_CUDA, "kernel launch: injected launch failure");
+  cudaError_t e = cn::launch_f32(a, plan->plan, plan->pot, plan->guard, true, plan->grid, s);
+  if (e != cudaSuccess) return fail_cuda(e, "batched pair kernel launch");
+  return CN_OK;
+}
+
+cn_status build_batch_plan(int32_t n_clusters, const int64_t* offsets, const float* eps2, const cn_tune* tune,
+                           int with_pot, cn_batch_plan** out) {
+  if (!out) return fail(CN_ERR_INVALID_ARG, "plan_out is NULL");
+  *out = nullptr;
+  if (n_clusters < 0 || (n_clusters > 0 && (!offsets || !eps2)))
+    return fail(CN_ERR_INVALID_ARG, "n_clusters < 0 or NULL offsets/eps2");
+  if (n_clusters > 0 && offsets[0] != 0) return fail(CN_ERR_INVALID_ARG, "offsets[0] must be 0");
+  bool guard = false;
+  double pairs = 0.0;
+  for (int32_t c = 0; c < n_clusters; ++c) {
+    if (offsets[c + 1] < offsets[c]) return fail(CN_ERR_INVALID_ARG, "offsets must be non-decreasing");
+    cn_status st = check_eps2(eps2[c]);
+    if (st != CN_OK) return st;
+    const int64_t nc = offsets[c + 1] - offsets[c];
+    if (nc > 0 && needs_guard(eps2[c])) guard = true;
+    pairs += static_cast<double>(nc) * static_cast<double>(nc);
+  }
+  int dev = 0;
+  DeviceInfo* d = nullptr;
+  cn_status st = current_device(&dev, &d);
+  if (st != CN_OK) return st;
+  const int64_t n_total = n_clusters > 0 ? offsets[n_clusters] : 0;
+  const int variant = with_pot ? cn::kBatchedPot : cn::kBatched;
+  Plan p;
+  if ((st = resolve_plan(dev, variant, n_clusters, n_total, guard, tune, &p)) != CN_OK) return st;
+  // tiles in order of decreasing cluster size (largest work first for the dynamic queue)
+  std::vector<int32_t> order(static_cast<size_t>(n_clusters));
+  for (int32_t c = 0; c < n_clusters; ++c) order[c] = c;
+  std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
+    return offsets[x + 1] - offsets[x] > offsets[y + 1] - offsets[y];
+  });
+  std::vector<cn::TileDesc> tiles;
+  int64_t units = 0;
+  const int it = p.i_tile();
+  for (int32_t c : order) {
+    const int64_t nc = offsets[c + 1] - offsets[c];
+    if (nc == 0) continue;
+    const int64_t njt = ceil_div(nc, p.j_tile);
+    for (int64_t i0 = 0; i0 < nc; i0 += it) {
+      cn::TileDesc t{};
+      t.i0 = offsets[c] + i0;
+      t.j0 = offsets[c];
+      t.nj = nc;
+      t.unit0 = units;
+      t.ni = static_cast<int32_t>(std::min<int64_t>(it, nc - i0));
+      t.njt = static_cast<int32_t>(njt);
+      t.eps2 = eps2[c];
+      tiles.push_back(t);
+      units += njt;
+    }
+  }
+  Geometry g;
+  if (!tiles.empty() && (st = layout(dev, *d, variant, guard, p, static_cast<int64_t>(tiles.size()), units, 0, &g)) !=
+                            CN_OK)
+    return st;
+  auto* plan = new cn_batch_plan();
+  plan->dev = dev;
+  plan->n_clusters = n_clusters;
+  plan->n_total = n_total;
+  plan->pairs = pairs;
+  plan->plan = p;
+  plan->guard = guard;
+  plan->pot = with_pot != 0;
+  plan->n_tiles = static_cast<int32_t>(tiles.size());
+  plan->units = units;
+  plan->n_chunks = g.n_chunks;
+  plan->grid = g.grid;
+  plan->ws_bytes = tiles.empty() ? 0 : g.ws_bytes;
+  plan->off_partials = g.off_partials;
+  if (!tiles.empty()) {
+    if (inject("alloc")) {
+      delete plan;
+      return fail(CN_ERR_CUDA, "cudaMalloc: injected allocation failure");
+    }
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&plan->d_tiles), tiles.size() * sizeof(cn::TileDesc));
+    if (e == cudaSuccess)
+      e = cudaMemcpy(plan->d_tiles, tiles.data(), tiles.size() * sizeof(cn::TileDesc), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      cudaFree(plan->d_tiles);
+      delete plan;
+      return fail_cuda(e, "uploading the batched unit table");
+    }
+  }
+  *out = plan;
+  return CN_OK;
+}
+
+// Host staging buffers of cn_force_host, per (device, stream).
+struct HostStage {
+  void* buf = nullptr;
+  size_t bytes = 0;
+};
+std::map<std::pair<int, cudaStream_t>, HostStage> g_stage;
+
+cn_status stage_buffer(cudaStream_t s, size_t need, void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail_cuda(e, "cudaGetDevice");
+  std::lock_guard<std::mutex> lock(g_mu);
+  HostStage& h = g_stage[{dev, s}];
+  if (h.bytes < need) {
+    if (inject("alloc")) return fail(CN_ERR_CUDA, "cudaMalloc: injected allocation failure");
+    if (h.buf) {
+      if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return fail_cuda(e, "cudaStreamSynchronize");
+      cudaFree(h.buf);
+      h.buf = nullptr;
+      h.bytes = 0;
+    }
+    const size_t nb = align_up(need, static_cast<size_t>(1) << 20);
+    if ((e = cudaMalloc(&h.buf, nb)) != cudaSuccess) return fail_cuda(e, "cudaMalloc(staging)");
+    h.bytes = nb;
+  }
+  *out = h.buf;
+  return CN_OK;
+}
+
+cn_status energy_common(int64_t n, const float* pos_mass, const float* pot_f, const double* pot_d, double* w_out,
+                        cudaStream_t s) {
+  if (n < 0) return fail(CN_ERR_INVALID_ARG, "n must be >= 0");
+  if (!w_out || !aligned(w_out, 8)) return fail(CN_ERR_INVALID_ARG, "w_out must be a non-NULL aligned double pointer");
+  cn_status st = check_records(pos_mass, n, "pos_mass");
+  if (st != CN_OK) return st;
+  if (n > 0 && !pot_f && !pot_d) return fail(CN_ERR_INVALID_ARG, "pot is NULL");
+  int dev = 0;
+  DeviceInfo* d = nullptr;
+  if ((st = current_device(&dev, &d)) != CN_OK) return st;
+  if (n == 0) {
+    cudaError_t e = cudaMemsetAsync(w_out, 0, sizeof(double), s);
+    return e == cudaSuccess ? CN_OK : fail_cuda(e, "cudaMemsetAsync");
+  }
+  double* aux = nullptr;
+  if ((st = library_aux(s, &aux)) != CN_OK) return st;
+  const size_t nb = cn::energy_workspace_doubles();
+  if (inject("launch")) return fail(CN_ERR_CUDA, "kernel launch: injected launch failure");
+  cudaError_t e = cn::launch_energy(n, reinterpret_cast<const float4*>(pos_mass), pot_f, pot_d, aux,
+                                    reinterpret_cast<int*>(aux + nb), w_out, s);
+  return e == cudaSuccess ? CN_OK : fail_cuda(e, "potential-energy kernel launch");
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+cn_status cn_force(int64_t n_i, const float* pos_i, int64_t n_j, const float* pos_mass_j, float eps2, float* acc_out,
+                   float* pot_out, cn_stream stream) {
+  return force_common(false, n_i, pos_i, n_j, pos_mass_j, eps2, acc_out, pot_out, nullptr, 0, true,
+                      reinterpret_cast<cudaStream_t>(stream));
+}
+
+cn_status cn_force_ws(int64_t n_i, const float* pos_i, int64_t n_j, const float* pos_mass_j, float eps2,
+                      float* acc_out, float* pot_out, void* workspace, size_t ws_bytes, cn_stream stream) {
+  return force_common(false, n_i, pos_i, n_j, pos_mass_j, eps2, acc_out, pot_out, workspace, ws_bytes, false,
+                      reinterpret_cast<cudaStream_t>(stream));
+}
+
+cn_status cn_force_dd(int64_t n_i, const float* pos_i, int64_t n_j, const float* pos_mass_j, float eps2,
+                      double* acc_out, double* pot_out, cn_stream stream) {
+  return force_common(true, n_i, pos_i, n_j, pos_mass_j, eps2, acc_out, pot_out, nullptr, 0, true,
+                      reinterpret_cast<cudaStream_t>(stream));
+}
+
+cn_status cn_force_dd_ws(int64_t n_i, const float* pos_i, int64_t n_j, const float* pos_mass_j, float eps2,
+                         double* acc_out, double* pot_out, void* workspace, size_t ws_bytes, cn_stream stream) {
+  return force_common(true, n_i, pos_i, n_j, pos_mass_j, eps2, acc_out, pot_out, workspace, ws_bytes, false,
+                      reinterpret_cast<cudaStream_t>(stream));
+}
+
+size_t cn_workspace_bytes(int variant, int64_t n_i, int64_t n_j) {
+  if (n_i <= 0 || n_j <= 0 || variant < cn::kF32 || variant > cn::kAdjoint) return 0;
+  int dev = 0;
+  DeviceInfo* d = nullptr;
+  if (current_device(&dev, &d) != CN_OK) return 0;
+  Plan p;
+  if (resolve_plan(dev, variant, n_i, n_j, false, nullptr, &p) != CN_OK) return 0;
+  Geometry g;
+  if (single_geometry(dev, *d, variant, false, p, n_i, n_j, &g) != CN_OK) return 0;
+  // the guarded (eps2 = 0) shape uses one i-particle per thread: size for the larger of the two
+  Plan pg = p;
+  pg.k = 1;
+  Geometry gg;
+  if (single_geometry(dev, *d, variant, true, pg, n_i, n_j, &gg) != CN_OK) return g.ws_bytes;
+  return std::max(g.ws_bytes, gg.ws_bytes);
+}
+
+cn_status cn_batch_plan_create(int32_t n_clusters, const int64_t* offsets_host, const float* eps2_host,
+                               const cn_tune* tune, int with_potential, cn_batch_plan** plan_out) {
+  return build_batch_plan(n_clusters, offsets_host, eps2_host, tune, with_potential, plan_out);
+}
+
+cn_status cn_batch_plan_destroy(cn_batch_plan* plan) {
+  if (!plan) return CN_OK;
+  if (plan->exec) cudaGraphExecDestroy(plan->exec);
+  if (plan->graph) cudaGraphDestroy(plan->graph);
+  if (plan->d_tiles) cudaFree(plan->d_tiles);
+  delete plan;
+  return CN_OK;
+}
+
+size_t cn_batch_plan_workspace_bytes(const cn_batch_plan* plan) { return plan ? plan->ws_bytes : 0; }
+
+cn_status cn_batch_plan_info(const cn_batch_plan* plan, int64_t* n_total, double* pairs) {
+  if (!plan) return fail(CN_ERR_INVALID_ARG, "plan is NULL");
+  if (n_total) *n_total = plan->n_total;
+  if (pairs) *pairs = plan->pairs;
+  return CN_OK;
+}
+
+cn_status cn_force_batched(const cn_batch_plan* plan, const float* pos_mass, float* acc_out, float* pot_out,
+                           void* workspace, size_t ws_bytes, cn_stream stream) {
+  return run_batched(plan, pos_mass, acc_out, pot_out, workspace, ws_bytes, reinterpret_cast<cudaStream_t>(stream));
+}
+
+cn_status cn_batch_plan_capture(cn_batch_plan* plan, const float* pos_mass, float* acc_out, float* pot_out,
+                                void* workspace, size_t ws_bytes, cn_stream stream) {
+  if (!plan) return fail(CN_ERR_INVALID_ARG, "plan is NULL");
+  auto s = reinterpret_cast<cudaStream_t>(stream);
+  if (!s) return fail(CN_ERR_INVALID_ARG, "graph capture needs a non-default stream");
+  if (!workspace && plan->ws_bytes) return fail(CN_ERR_WORKSPACE, "graph capture needs a caller workspace");
+  if (inject("capture")) return fail(CN_ERR_CUDA, "cudaStreamBeginCapture: injected capture failure");
+  cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return fail_cuda(e, "cudaStreamBeginCapture");
+  cn_status st = run_batched(plan, pos_mass, acc_out, pot_out, workspace, ws_bytes, s);
+  cudaGraph_t graph = nullptr;
+  e = cudaStreamEndCapture(s, &graph);
+  if (st != CN_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  if (e != cudaSuccess) return fail_cuda(e, "cudaStreamEndCapture");
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    return fail_cuda(e, "cudaGraphInstantiate");
+  }
+  if (plan->exec) cudaGraphExecDestroy(plan->exec);
+  if (plan->graph) cudaGraphDestroy(plan->graph);
+  plan->graph = graph;
+  plan->exec = exec;
+  return CN_OK;
+}
+
+cn_status cn_batch_plan_launch(const cn_batch_plan* plan, cn_stream stream) {
+  if (!plan || !plan->exec) return fail(CN_ERR_INVALID_ARG, "plan has no captured graph");
+  if (inject("launch")) return fail(CN_ERR_CUDA, "cudaGraphLaunch: injected launch failure");
+  cudaError_t e = cudaGraphLaunch(plan->exec, reinterpret_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? CN_OK : fail_cuda(e, "cudaGraphLaunch");
+}
+
+cn_status cn_force_adjoint(int64_t n, const float* pos_mass, float eps2, const float* w, float* grad_pos,
+                           float* grad_mass, cn_stream stream) {
+  auto s = reinterpret_cast<cudaStream_t>(stream);
+  if (n < 0) return fail(CN_ERR_INVALID_ARG, "n must be >= 0");
+  cn_status st;
+  if ((st = check_eps2(eps2)) != CN_OK) return st;
+  if ((st = check_records(pos_mass, n, "pos_mass")) != CN_OK) return st;
+  if (n > 0 && (!w || !grad_pos || !grad_mass)) return fail(CN_ERR_INVALID_ARG, "w, grad_pos and grad_mass are required");
+  if ((w && !aligned(w, 4)) || (grad_pos && !aligned(grad_pos, 4)) || (grad_mass && !aligned(grad_mass, 4)))
+    return fail(CN_ERR_MISALIGNED, "w and the gradients must be 4-byte aligned");
+  const size_t un = static_cast<size_t>(n);
+  if (overlaps(grad_pos, un * 12, pos_mass, un * 16) || overlaps(grad_pos, un * 12, w, un * 12) ||
+      overlaps(grad_mass, un * 4, pos_mass, un * 16) || overlaps(grad_mass, un * 4, w, un * 12) ||
+      overlaps(grad_pos, un * 12, grad_mass, un * 4))
+    return fail(CN_ERR_INVALID_ARG, "outputs overlap inputs or each other");
+  if (n == 0) return CN_OK;
+  int dev = 0;
+  DeviceInfo* d = nullptr;
+  if ((st = current_device(&dev, &d)) != CN_OK) return st;
+  const bool guard = needs_guard(eps2);
+  Plan p;
+  if ((st = resolve_plan(dev, cn::kAdjoint, n, n, guard, nullptr, &p)) != CN_OK) return st;
+  Geometry g;
+  if ((st = single_geometry(dev, *d, cn::kAdjoint, guard, p, n, n, &g)) != CN_OK) return st;
+  void* ws = nullptr;
+  if ((st = library_workspace(s, g.ws_bytes, &ws)) != CN_OK) return st;
+  float4* wrec = reinterpret_cast<float4*>(static_cast<char*>(ws) + g.off_wrec);
+  if (inject("launch")) return fail(CN_ERR_CUDA, "kernel launch: injected launch failure");
+  cudaError_t e = cn::launch_pack_w(w, wrec, n, s);
+  if (e != cudaSuccess) return fail_cuda(e, "weight packing launch");
+  PairArgs a = base_args(ws, g, p, d->status);
+  a.pos_i = reinterpret_cast<const float4*>(pos_mass);
+  a.pos_j = reinterpret_cast<const float4*>(pos_mass);
+  a.pos_i2 = wrec;
+  a.pos_j2 = wrec;
+  a.acc_out = grad_pos;
+  a.pot_out = grad_mass;
+  a.n_i = n;
+  a.n_j = n;
+  a.eps2 = eps2;
+  e = cn::launch_adjoint(a, p, guard, g.grid, s);
+  return e == cudaSuccess ? CN_OK : fail_cuda(e, "adjoint kernel launch");
+}
+
+cn_status cn_potential_energy(int64_t n, const float* pos_mass, const float* pot, double* w_out, cn_stream stream) {
+  return energy_common(n, pos_mass, pot, nullptr, w_out, reinterpret_cast<cudaStream_t>(stream));
+}
+
+cn_status cn_potential_energy_dd(int64_t n, const float* pos_mass, const double* pot, double* w_out,
+                                 cn_stream stream) {
+  return energy_common(n, pos_mass, nullptr, pot, w_out, reinterpret_cast<cudaStream_t>(stream));
+}
+
+cn_status cn_force_host(int64_t n_i, const float* pos_i_host, int64_t n_j, const float* pos_mass_j_host, float eps2,
+                        float* acc_host, float* pot_host, cn_stream stream) {
+  auto s = reinterpret_cast<cudaStream_t>(stream);
+  if (n_i < 0 || n_j < 0) return fail(CN_ERR_INVALID_ARG, "n_i and n_j must be >= 0");
+  if ((n_i > 0 && (!pos_i_host || !acc_host)) || (n_j > 0 && !pos_mass_j_host))
+    return fail(CN_ERR_INVALID_ARG, "NULL host buffer");
+  cn_status st = check_eps2(eps2);
+  if (st != CN_OK) return st;
+  if (n_i == 0) return CN_OK;
+  int dev = 0;
+  DeviceInfo* d = nullptr;
+  if ((st = current_device(&dev, &d)) != CN_OK) return st;
+  // i = j when the caller passes the same host array for both sets: copy it once
+  const bool same = pos_i_host == pos_mass_j_host && n_i == n_j;
+  const size_t bi = align_up(static_cast<size_t>(n_i) * 16, 256);
+  const size_t bj = same ? 0 : align_up(static_cast<size_t>(n_j) * 16, 256);
+  const size_t ba = align_up(static_cast<size_t>(n_i) * 12, 256);
+  const size_t bp = pot_host ? align_up(static_cast<size_t>(n_i) * 4, 256) : 0;
+  void* buf = nullptr;
+  if ((st = stage_buffer(s, bi + bj + ba + bp, &buf)) != CN_OK) return st;
+  char* base = static_cast<char*>(buf);
+  float* d_pi = reinterpret_cast<float*>(base);
+  float* d_pj = same ? d_pi : reinterpret_cast<float*>(base + bi);
+  float* d_acc = reinterpret_cast<float*>(base + bi + bj);
+  float* d_pot = pot_host ? reinterpret_cast<float*>(base + bi + bj + ba) : nullptr;
+  cudaError_t e = cudaMemcpyAsync(d_pi, pos_i_host, static_cast<size_t>(n_i) * 16, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && !same && n_j > 0)
+    e = cudaMemcpyAsync(d_pj, pos_mass_j_host, static_cast<size_t>(n_j) * 16, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return fail_cuda(e, "cudaMemcpyAsync(host to device)");
+  if ((st = cn_force(n_i, d_pi, n_j, d_pj, eps2, d_acc, d_pot, stream)) != CN_OK) return st;
+  e = cudaMemcpyAsync(acc_host, d_acc, static_cast<size_t>(n_i) * 12, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && pot_host)
+    e = cudaMemcpyAsync(pot_host, d_pot, static_cast<size_t>(n_i) * 4, cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return fail_cuda(e, "cudaMemcpyAsync(device to host)");
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return fail_cuda(e, "cudaStreamSynchronize");
+  return CN_OK;
+}
+
+cn_status cn_force_host_f64(const double* xj, const double* mj, const double* xi, double eps2, double* a, int ni,
+                            int nj) {
+  if (ni < 0 || nj < 0) return fail(CN_ERR_INVALID_ARG, "ni and nj must be >= 0");
+  if ((ni > 0 && (!xi || !a)) || (nj > 0 && (!xj || !mj))) return fail(CN_ERR_INVALID_ARG, "NULL host array");
+  if (!std::isfinite(eps2) || eps2 < 0.0) return fail(CN_ERR_INVALID_ARG, "eps2 must be finite and >= 0");
+  if (ni == 0) return CN_OK;
+  std::vector<float> pi(static_cast<size_t>(ni) * 4), pj(static_cast<size_t>(nj) * 4), acc(static_cast<size_t>(ni) * 3);
+  for (int i = 0; i < ni; ++i) {
+    for (int c = 0; c < 3; ++c) pi[4 * i + c] = static_cast<float>(xi[3 * i + c]);
+    pi[4 * i + 3] = 0.f;
+  }
+  for (int j = 0; j < nj; ++j) {
+    for (int c = 0; c < 3; ++c) pj[4 * j + c] = static_cast<float>(xj[3 * j + c]);
+    pj[4 * j + 3] = static_cast<float>(mj[j]);
+  }
+  cn_status st = cn_force_host(ni, pi.data(), nj, nj ? pj.data() : nullptr, static_cast<float>(eps2), acc.data(),
+                               nullptr, nullptr);
+  if (st != CN_OK) return st;
+  for (size_t k = 0; k < acc.size(); ++k) a[k] = acc[k];
+  return CN_OK;
+}
+
+cn_status cn_tune_get(int variant, int64_t n_i, int64_t n_j, cn_tune* out) {
+  if (!out || variant < cn::kF32 || variant > cn::kBatchedPot || n_i < 0 || n_j < 0)
+    return fail(CN_ERR_INVALID_ARG, "bad variant, size or NULL output");
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail_cuda(e, "cudaGetDevice");
+  Plan p;
+  cn_status st = resolve_plan(dev, variant, n_i, n_j, false, nullptr, &p);
+  if (st != CN_OK) return st;
+  out->i_per_thread = p.k;
+  out->threads = p.threads;
+  out->j_tile = p.j_tile;
+  out->stages = p.stages;
+  out->ctas_per_sm = p.ctas_per_sm;
+  out->chunk_units = static_cast<int32_t>(p.chunk_units);
+  return CN_OK;
+}
+
+cn_status cn_tune_set(int variant, int64_t n_i, int64_t n_j, const cn_tune* tune) {
+  if (variant < cn::kF32 || variant > cn::kBatchedPot || n_i < 0 || n_j < 0)
+    return fail(CN_ERR_INVALID_ARG, "bad variant or size");
+  if (tune) {
+    cn_status st = check_tune(variant, *tune);
+    if (st != CN_OK) return st;
+  }
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail_cuda(e, "cudaGetDevice");
+  std::lock_guard<std::mutex> lock(g_mu);
+  const auto key = std::make_tuple(dev, variant, bucket(n_i), bucket(n_j));
+  if (tune)
+    g_tune[key] = *tune;
+  else
+    g_tune.erase(key);
+  return CN_OK;
+}
+
+cn_status cn_autotune(int variant, int64_t n_i, const float* pos_i, int64_t n_j, const float* pos_mass_j, float eps2,
+                      void* acc_out, void* pot_out, int reps, cn_stream stream, cn_tune* best_out) {
+  if (variant < cn::kF32 || variant > cn::kDDPot) return fail(CN_ERR_INVALID_ARG, "cn_autotune covers the F32 and DD variants");
+  if (n_i <= 0 || n_j <= 0) return fail(CN_ERR_INVALID_ARG, "autotuning needs n_i > 0 and n_j > 0");
+  const bool dd = variant == cn::kDD || variant == cn::kDDPot;
+  const bool pot = variant == cn::kF32Pot || variant == cn::kDDPot;
+  if (pot && !pot_out) return fail(CN_ERR_INVALID_ARG, "the potential variants need pot_out");
+  auto s = reinterpret_cast<cudaStream_t>(stream);
+  if (reps < 1) reps = 1;
+  const int ks[] = {1, 2, 4, 8};
+  const int ths[] = {64, 128, 256};
+  const int tiles[] = {128, 256, 512, 1024};
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best_ms = 1e30f;
+  cn_tune best{};
+  cn_status result = CN_OK;
+  for (int k : ks) {
+    if (!valid_k(variant, k)) continue;
+    for (int th : ths) {
+      if (static_cast<int64_t>(k) * th > 4 * std::max<int64_t>(n_i, 256)) continue;  // tile far larger than the i set
+      for (int jt : tiles) {
+        if (jt > 4 * std::max<int64_t>(n_j, 64)) continue;
+        cn_tune t{k, th, jt, 4, 0, 0};
+        cn_tune_set(variant, n_i, n_j, &t);
+        auto call = [&]() {
+          return force_common(dd, n_i, pos_i, n_j, pos_mass_j, eps2, acc_out, pot ? pot_out : nullptr, nullptr, 0,
+                              true, s);
+        };
+        cn_status st = call();  // warm-up (and workspace growth)
+        if (st != CN_OK) {
+          if (st == CN_ERR_INVALID_ARG) continue;  // shape does not fit
+          result = st;
+          break;
+        }
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < reps; ++r) call();
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+          result = fail(CN_ERR_CUDA, "autotune: event synchronisation failed");
+          break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) {
+          best_ms = ms;
+          best = t;
+        }
+      }
+      if (result != CN_OK) break;
+    }
+    if (result != CN_OK) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (result != CN_OK) {
+    cn_tune_set(variant, n_i, n_j, nullptr);
+    return result;
+  }
+  if (best_ms >= 1e30f) {
+    cn_tune_set(variant, n_i, n_j, nullptr);
+    return fail(CN_ERR_INVALID_ARG, "no candidate launch shape fits");
+  }
+  cn_tune_set(variant, n_i, n_j, &best);
+  if (best_out) *best_out = best;
+  return CN_OK;
+}
+
+cn_status cn_autotune_batched(int32_t n_clusters, const int64_t* offsets_host, const float* eps2_host,
+                              const float* pos_mass, float* acc_out, float* pot_out, int reps, cn_stream stream,
+                              cn_tune* best_out) {
+  if (n_clusters <= 0 || !offsets_host) return fail(CN_ERR_INVALID_ARG, "empty ensemble");
+  auto s = reinterpret_cast<cudaStream_t>(stream);
+  if (reps < 1) reps = 1;
+  const int variant = pot_out ? cn::kBatchedPot : cn::kBatched;
+  const int ks[] = {2, 4, 8};
+  const int ths[] = {64, 128, 256};
+  const int tiles[] = {128, 256, 512};
+  const int chunks[] = {0, 8, 32};
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best_ms = 1e30f;
+  cn_tune best{};
+  cn_status result = CN_OK;
+  for (int k : ks)
+    for (int th : ths)
+      for (int jt : tiles)
+        for (int ch : chunks) {
+          if (result != CN_OK) break;
+          cn_tune t{k, th, jt, 4, 0, ch};
+          cn_batch_plan* plan = nullptr;
+          cn_status st = build_batch_plan(n_clusters, offsets_host, eps2_host, &t, pot_out != nullptr, &plan);
+          if (st != CN_OK) {
+            if (st == CN_ERR_INVALID_ARG) continue;
+            result = st;
+            break;
+          }
+          st = run_batched(plan, pos_mass, acc_out, pot_out, nullptr, 0, s);
+          if (st == CN_OK) {
+            cudaEventRecord(e0, s);
+            for (int r = 0; r < reps; ++r) run_batched(plan, pos_mass, acc_out, pot_out, nullptr, 0, s);
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) == cudaSuccess) {
+              float ms = 0.f;
+              cudaEventElapsedTime(&ms, e0, e1);
+              if (ms < best_ms) {
+                best_ms = ms;
+                best = t;
+              }
+            } else {
+              st = fail(CN_ERR_CUDA, "autotune: event synchronisation failed");
+            }
+          }
+          cn_batch_plan_destroy(plan);
+          if (st != CN_OK) result = st;
+        }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (result != CN_OK) return result;
+  if (best_ms >= 1e30f) return fail(CN_ERR_INVALID_ARG, "no candidate launch shape fits");
+  const int64_t n_total = offsets_host[n_clusters];
+  cn_tune_set(variant, n_clusters, n_total, &best);
+  if (best_out) *best_out = best;
+  return CN_OK;
+}
+
+cn_status cn_get_device_status(cn_stream stream) {
+  auto s = reinterpret_cast<cudaStream_t>(stream);
+  int dev = 0;
+  DeviceInfo* d = nullptr;
+  cn_status st = current_device(&dev, &d);
+  if (st != CN_OK) return st;
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail_cuda(e, "cudaStreamSynchronize");
+  int flag = 0;
+  if ((e = cudaMemcpy(&flag, d->status, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return fail_cuda(e, "reading the device status word");
+  if (flag == 0) return CN_OK;
+  const int zero = 0;
+  cudaMemcpy(d->status, &zero, sizeof(int), cudaMemcpyHostToDevice);
+  {
+    // arrival counters may have been left mid-protocol: clear every library workspace of this device
+    std::lock_guard<std::mutex> lock(g_mu);
+    for (auto& kv : g_ws)
+      if (kv.first.first == dev) {
+        if (kv.second.ptr) cudaMemset(kv.second.ptr, 0, kv.second.bytes);
+        if (kv.second.aux) cudaMemset(kv.second.aux, 0, (cn::energy_workspace_doubles() + 1) * sizeof(double));
+      }
+  }
+  cudaDeviceSynchronize();
+  return fail(CN_ERR_TIMEOUT, "a kernel wait timed out (device status bits " + std::to_string(flag) + ")");
+}
+
+cn_status cn_set_wait_limit_ns(uint64_t ns) {
+  g_wait_ns.store(ns ? ns : kDefaultWaitNs);
+  return CN_OK;
+}
+
+cn_status cn_debug_timeout_probe(cn_stream stream) {
+  int dev = 0;
+  DeviceInfo* d = nullptr;
+  cn_status st = current_device(&dev, &d);
+  if (st != CN_OK) return st;
+  cudaError_t e = cn::launch_timeout_probe(d->status, g_wait_ns.load(), reinterpret_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? CN_OK : fail_cuda(e, "timeout probe launch");
+}
+
+cn_status cn_probe_peaks(cn_stream stream, double* out5) {
+  if (!out5) return fail(CN_ERR_INVALID_ARG, "out is NULL");
+  int dev = 0;
+  DeviceInfo* d = nullptr;
+  cn_status st = current_device(&dev, &d);
+  if (st != CN_OK) return st;
+  cudaError_t e = cn::run_probes(reinterpret_cast<cudaStream_t>(stream), out5);
+  return e == cudaSuccess ? CN_OK : fail_cuda(e, "issue-rate probes");
+}
+
+const char* cn_status_string(cn_status status) {
+  switch (status) {
+    case CN_OK: return "CN_OK";
+    case CN_ERR_INVALID_ARG: return "CN_ERR_INVALID_ARG";
+    case CN_ERR_MISALIGNED: return "CN_ERR_MISALIGNED";
+    case CN_ERR_CUDA: return "CN_ERR_CUDA";
+    case CN_ERR_TIMEOUT: return "CN_ERR_TIMEOUT";
+    case CN_ERR_UNSUPPORTED_DEVICE: return "CN_ERR_UNSUPPORTED_DEVICE";
+    case CN_ERR_WORKSPACE: return "CN_ERR_WORKSPACE";
+  }
+  return "CN_ERR_UNKNOWN";
+}
+
+const char* cn_last_error_message(void) { return g_last_error.c_str(); }
+
+const char* cn_version(void) { return "cunbody 0.1.0 (sm_103a)"; }
+
+}  // extern "C"

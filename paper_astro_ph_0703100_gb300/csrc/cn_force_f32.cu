@@ -1,0 +1,57 @@
+// FP32 pair-kernel instantiations (single system and batched ensemble).
+#include "cn_pair.cuh"
+
+namespace cn {
+namespace {
+
+template <int K, bool POT, bool GUARD, bool BATCHED>
+const void* fn() {
+  return reinterpret_cast<const void*>(&pair_kernel<F32Policy<K, POT, GUARD>, K, BATCHED>);
+}
+
+template <bool POT, bool GUARD, bool BATCHED>
+const void* by_k(int k) {
+  if constexpr (GUARD) {
+    return k == 1 ? fn<1, POT, true, BATCHED>() : nullptr;
+  } else {
+    switch (k) {
+      case 1: return fn<1, POT, false, BATCHED>();
+      case 2: return fn<2, POT, false, BATCHED>();
+      case 4: return fn<4, POT, false, BATCHED>();
+      case 8: return fn<8, POT, false, BATCHED>();
+      default: return nullptr;
+    }
+  }
+}
+
+const void* select(int k, bool pot, bool guard, bool batched) {
+  if (batched) {
+    if (pot) return guard ? by_k<true, true, true>(k) : by_k<true, false, true>(k);
+    return guard ? by_k<false, true, true>(k) : by_k<false, false, true>(k);
+  }
+  if (pot) return guard ? by_k<true, true, false>(k) : by_k<true, false, false>(k);
+  return guard ? by_k<false, true, false>(k) : by_k<false, false, false>(k);
+}
+
+}  // namespace
+
+cudaError_t occupancy_f32(const Plan& p, bool pot, bool guard, bool batched, size_t smem, int* ctas) {
+  const void* f = select(p.k, pot, guard, batched);
+  if (!f) return cudaErrorInvalidValue;
+  cudaError_t e = prepare_kernel(f, smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, f, p.threads, smem);
+}
+
+cudaError_t launch_f32(const PairArgs& a, const Plan& p, bool pot, bool guard, bool batched, int grid,
+                       cudaStream_t s) {
+  const void* f = select(p.k, pot, guard, batched);
+  if (!f) return cudaErrorInvalidValue;
+  const size_t smem = ring_smem_bytes(p);
+  cudaError_t e = prepare_kernel(f, smem);
+  if (e != cudaSuccess) return e;
+  void* args[] = {const_cast<PairArgs*>(&a)};
+  return cudaLaunchKernel(f, dim3(grid), dim3(p.threads), args, smem, s);
+}
+
+}  // namespace cn

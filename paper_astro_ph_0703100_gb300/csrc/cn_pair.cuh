@@ -1,0 +1,676 @@
+// The pair kernel: softened direct summation (Eq. 1) for a set of i-tiles
+// against their j-particles, with the j-tiles staged through a ring of
+// shared-memory stages by bulk copies (the J-BAG / J-PACKING of Section
+// 2.2), several i-particles held in registers per thread (the I-POT), and a
+// two-level accumulation in which each j-tile's partial sum is folded into
+// a running sum (the FORCE-LOOP of Section 2.2.2, Eq. 3).
+//
+// Work decomposition: the i set is cut into i-tiles of threads x K
+// particles and the j set of each i-tile's system into j-tiles of j_tile
+// records. One (i-tile, j-tile) pair is a "unit"; units are numbered
+// tile-major, so consecutive units share an i-tile. Each CTA processes
+// contiguous unit ranges ("chunks"): either one chunk per CTA of equal size
+// (static schedule, every SM gets the same number of pair interactions) or
+// fixed-size chunks popped from an atomic queue (dynamic schedule). An
+// i-tile whose units fall in one chunk is written directly; an i-tile split
+// over several chunks has each chunk write its FP32 (or double-single)
+// partial to the workspace, and the chunk that finishes last sums the
+// partials in chunk order in FP64 - a deterministic cross-CTA reduction.
+#pragma once
+
+#include "cn_device.cuh"
+#include "cn_kernels.h"
+
+namespace cn {
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Counts one arrival on a split tile's counter and returns the number of
+// earlier arrivals of this launch. The counter word is (epoch << 32) |
+// arrivals; a word left by another launch or holding stale workspace bytes
+// carries another epoch and counts as zero. Lock-free: each failed CAS means
+// another CTA's arrival succeeded.
+__device__ __forceinline__ int arrive_counter(unsigned long long* c, uint32_t epoch) {
+  unsigned long long cur = *reinterpret_cast<volatile unsigned long long*>(c);
+  for (;;) {
+    const unsigned long long next = (static_cast<uint32_t>(cur >> 32) == epoch)
+                                        ? cur + 1ull
+                                        : ((static_cast<unsigned long long>(epoch) << 32) | 1ull);
+    const unsigned long long seen = atomicCAS(c, cur, next);
+    if (seen == cur) return static_cast<int>(static_cast<uint32_t>(next)) - 1;
+    cur = seen;
+  }
+}
+
+// ------------------------------------------------------------------ schedule
+struct Sched {
+  int64_t U;  // total units
+  int64_t Q;  // number of chunks
+  int64_t C;  // dynamic chunk size, 0 for the static schedule
+  __device__ __forceinline__ int64_t begin(int64_t q) const { return C ? q * C : (q * U) / Q; }
+  __device__ __forceinline__ int64_t end(int64_t q) const {
+    return C ? ((q + 1) * C < U ? (q + 1) * C : U) : ((q + 1) * U) / Q;
+  }
+  // chunk holding unit u: the largest q with begin(q) <= u
+  __device__ __forceinline__ int64_t chunk_of(int64_t u) const { return C ? u / C : ((u + 1) * Q - 1) / U; }
+};
+
+template <bool BATCHED>
+__device__ __forceinline__ TileDesc tile_at(const PairArgs& a, int32_t t, int i_tile) {
+  if constexpr (BATCHED) {
+    return a.tiles[t];
+  } else {
+    TileDesc d;
+    d.i0 = static_cast<int64_t>(t) * i_tile;
+    const int64_t left = a.n_i - d.i0;
+    d.ni = static_cast<int32_t>(left < i_tile ? left : i_tile);
+    d.j0 = 0;
+    d.nj = a.n_j;
+    d.njt = a.njt;
+    d.unit0 = static_cast<int64_t>(t) * a.njt;
+    d.eps2 = a.eps2;
+    d.pad = 0;
+    return d;
+  }
+}
+
+template <bool BATCHED>
+__device__ __forceinline__ int32_t tile_of_unit(const PairArgs& a, int64_t u) {
+  if constexpr (BATCHED) {
+    int32_t lo = 0, hi = a.n_tiles - 1;
+    while (lo < hi) {
+      const int32_t mid = (lo + hi + 1) >> 1;
+      if (a.tiles[mid].unit0 <= u)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    return lo;
+  } else {
+    return static_cast<int32_t>(u / a.njt);
+  }
+}
+
+// ------------------------------------------------------------------ pair math
+// One j record against K i-particles in FP32: 3 FADD + 3 FFMA for the
+// softened squared distance, one MUFU rsqrt, 3 FMUL for m r^-3 and 3 FFMA
+// into the partial. POT adds the pair potential m / r for every pair whose
+// separation is not exactly zero; GUARD zeroes pairs with s == 0 (reachable
+// only for eps2 == 0 and coincident points).
+template <int K, bool POT, bool GUARD>
+__device__ __forceinline__ void pair_f32(const float4 pj, const float (&xi)[K][3], float eps2,
+                                         float (&part)[K][POT ? 4 : 3]) {
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const float dx = pj.x - xi[k][0];
+    const float dy = pj.y - xi[k][1];
+    const float dz = pj.z - xi[k][2];
+    float s, d2 = 0.f;
+    if constexpr (POT) {
+      d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+      s = d2 + eps2;
+    } else {
+      s = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+    }
+    float r = rsqrt_mufu(s);
+    if constexpr (GUARD) r = (s > 0.f) ? r : 0.f;
+    const float mr = pj.w * r;
+    const float q = mr * (r * r);
+    part[k][0] = fmaf(q, dx, part[k][0]);
+    part[k][1] = fmaf(q, dy, part[k][1]);
+    part[k][2] = fmaf(q, dz, part[k][2]);
+    if constexpr (POT) part[k][3] += (d2 != 0.f) ? mr : 0.f;
+  }
+}
+
+// ------------------------------------------------------------------ policies
+// Plain FP32: per-tile FP32 partial folded into an FP32 running sum.
+template <int K, bool POT, bool GUARD>
+struct F32Policy {
+  static constexpr int NC = POT ? 4 : 3;
+  static constexpr int kSlotF4 = 1;  // float4 per i-particle in a workspace slot
+  static constexpr int kJRec = 1;    // float4 per j record
+  float xi[K][3];
+  float run[K][NC];
+
+  __device__ __forceinline__ void load_i(const PairArgs& a, int64_t gi, bool valid, int k) {
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (valid) v = __ldg(a.pos_i + gi);
+    xi[k][0] = v.x;
+    xi[k][1] = v.y;
+    xi[k][2] = v.z;
+  }
+
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+      for (int c = 0; c < NC; ++c) run[k][c] = 0.f;
+  }
+
+  __device__ __forceinline__ void tile(const float4* js, int T, float eps2, int64_t /*self_off*/, bool /*diag*/,
+                                       int /*tid*/, int /*NT*/) {
+    float part[K][NC];
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+      for (int c = 0; c < NC; ++c) part[k][c] = 0.f;
+#pragma unroll 1
+    for (int j = 0; j < T; j += 8) {
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj) pair_f32<K, POT, GUARD>(js[j + jj], xi, eps2, part);
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+      for (int c = 0; c < NC; ++c) run[k][c] += part[k][c];
+  }
+
+  __device__ __forceinline__ void store_final(const PairArgs& a, int64_t i, int k) const {
+    float* acc = static_cast<float*>(a.acc_out) + 3 * i;
+    acc[0] = run[k][0];
+    acc[1] = run[k][1];
+    acc[2] = run[k][2];
+    if constexpr (POT) {
+      if (a.pot_out) static_cast<float*>(a.pot_out)[i] = -run[k][3];
+    }
+  }
+
+  __device__ __forceinline__ void store_partial(float4* slot, int il, int /*i_tile*/, int k) const {
+    slot[il] = make_float4(run[k][0], run[k][1], run[k][2], POT ? run[k][3] : 0.f);
+  }
+
+  __device__ static __forceinline__ void add_partial(const float4* slot, int il, int /*i_tile*/, double (&s)[4]) {
+    const float4 v = __ldcg(slot + il);
+    s[0] += v.x;
+    s[1] += v.y;
+    s[2] += v.z;
+    s[3] += v.w;
+  }
+
+  __device__ static __forceinline__ void store_merged(const PairArgs& a, int64_t i, const double (&s)[4]) {
+    float* acc = static_cast<float*>(a.acc_out) + 3 * i;
+    acc[0] = static_cast<float>(s[0]);
+    acc[1] = static_cast<float>(s[1]);
+    acc[2] = static_cast<float>(s[2]);
+    if constexpr (POT) {
+      if (a.pot_out) static_cast<float*>(a.pot_out)[i] = static_cast<float>(-s[3]);
+    }
+  }
+};
+
+// Compensated ("split-precision") form. Every quantity of the pair term is
+// carried as a double-single (hi, lo) pair of FP32 numbers and every FP32
+// rounding is recovered exactly, with TwoSum for sums and an FMA for
+// products:
+//   d = x_j - x_i            TwoSum per component (exact)
+//   s = |d|^2 + eps2         exact squares (FMA), three TwoSums, plus the
+//                            cross term 2 d_hi . d_lo
+//   y = s^-1/2               MUFU estimate y0, then y = y0 + y0 rho / 2 with
+//                            the residual rho = 1 - s y0^2 formed by FMAs
+//   g = y^3, m g, m g d      double-single products
+//   a += m g d               TwoSum of the hi part into the running hi sum,
+//                            every low part into the running lo sum
+// so the per-pair relative error is of order 2^-44 and the accumulated sum
+// is exact to a few ulps of the hi part. FP32 instructions only (about 104
+// issue slots per pair plus one MUFU). Partials of split tiles are merged
+// in FP64; outputs are FP64 (hi + lo).
+template <int K, bool POT, bool GUARD>
+__device__ __forceinline__ void pair_ds(const float4 pj, const float (&xi)[K][3], float eps2,
+                                        float (&hi)[K][POT ? 4 : 3], float (&lo)[K][POT ? 4 : 3]) {
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    float dh[3], dl[3], ph[3], pl[3];
+    two_sum(pj.x, -xi[k][0], dh[0], dl[0]);
+    two_sum(pj.y, -xi[k][1], dh[1], dl[1]);
+    two_sum(pj.z, -xi[k][2], dh[2], dl[2]);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      ph[c] = __fmul_rn(dh[c], dh[c]);
+      pl[c] = fmaf(dh[c], dh[c], -ph[c]);
+    }
+    float t1, e1, t2, e2, sh, e3;
+    two_sum(ph[0], ph[1], t1, e1);
+    two_sum(t1, ph[2], t2, e2);
+    two_sum(t2, eps2, sh, e3);
+    float cross = fmaf(dh[0], dl[0], fmaf(dh[1], dl[1], __fmul_rn(dh[2], dl[2])));
+    float sl = __fadd_rn(__fadd_rn(e1, e2), __fadd_rn(e3, __fadd_rn(__fadd_rn(pl[0], pl[1]), pl[2])));
+    sl = fmaf(2.0f, cross, sl);
+    float y0 = rsqrt_mufu(sh);
+    if constexpr (GUARD) y0 = (sh > 0.f) ? y0 : 0.f;
+    const float q = __fmul_rn(y0, y0);
+    const float ql = fmaf(y0, y0, -q);
+    float rho = fmaf(-sh, q, 1.0f);
+    rho = fmaf(-sh, ql, rho);
+    rho = fmaf(-sl, q, rho);
+    const float yl = __fmul_rn(y0, __fmul_rn(0.5f, rho));
+    const float y2l = fmaf(__fmul_rn(2.0f, y0), yl, ql);
+    const float y3h = __fmul_rn(q, y0);
+    float y3l = fmaf(q, y0, -y3h);
+    y3l = fmaf(q, yl, y3l);
+    y3l = fmaf(y2l, y0, y3l);
+    const float mgh = __fmul_rn(pj.w, y3h);
+    float mgl = fmaf(pj.w, y3h, -mgh);
+    mgl = fmaf(pj.w, y3l, mgl);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float fh = __fmul_rn(mgh, dh[c]);
+      float fl = fmaf(mgh, dh[c], -fh);
+      fl = fmaf(mgh, dl[c], fl);
+      fl = fmaf(mgl, dh[c], fl);
+      float sum, err;
+      two_sum(hi[k][c], fh, sum, err);
+      hi[k][c] = sum;
+      lo[k][c] = __fadd_rn(lo[k][c], __fadd_rn(err, fl));
+    }
+    if constexpr (POT) {
+      // m (y0 + yl), skipped when the separation is exactly zero (t2 == 0)
+      const bool apart = t2 != 0.f;
+      const float uh = apart ? __fmul_rn(pj.w, y0) : 0.f;
+      const float ul = apart ? fmaf(pj.w, yl, fmaf(pj.w, y0, -uh)) : 0.f;
+      float sum, err;
+      two_sum(hi[k][3], uh, sum, err);
+      hi[k][3] = sum;
+      lo[k][3] = __fadd_rn(lo[k][3], __fadd_rn(err, ul));
+    }
+  }
+}
+
+template <int K, bool POT, bool GUARD>
+struct DDPolicy {
+  static constexpr int NC = POT ? 4 : 3;
+  static constexpr int kSlotF4 = 2;  // hi float4 then lo float4
+  static constexpr int kJRec = 1;
+  float xi[K][3];
+  float hi[K][NC];
+  float lo[K][NC];
+
+  __device__ __forceinline__ void load_i(const PairArgs& a, int64_t gi, bool valid, int k) {
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (valid) v = __ldg(a.pos_i + gi);
+    xi[k][0] = v.x;
+    xi[k][1] = v.y;
+    xi[k][2] = v.z;
+  }
+
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+      for (int c = 0; c < NC; ++c) hi[k][c] = lo[k][c] = 0.f;
+  }
+
+  __device__ __forceinline__ void tile(const float4* js, int T, float eps2, int64_t /*self_off*/, bool /*diag*/,
+                                       int /*tid*/, int /*NT*/) {
+#pragma unroll 1
+    for (int j = 0; j < T; j += 8) {
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj) pair_ds<K, POT, GUARD>(js[j + jj], xi, eps2, hi, lo);
+    }
+  }
+
+  __device__ __forceinline__ void store_final(const PairArgs& a, int64_t i, int k) const {
+    double* acc = static_cast<double*>(a.acc_out) + 3 * i;
+    acc[0] = static_cast<double>(hi[k][0]) + static_cast<double>(lo[k][0]);
+    acc[1] = static_cast<double>(hi[k][1]) + static_cast<double>(lo[k][1]);
+    acc[2] = static_cast<double>(hi[k][2]) + static_cast<double>(lo[k][2]);
+    if constexpr (POT) {
+      if (a.pot_out)
+        static_cast<double*>(a.pot_out)[i] = -(static_cast<double>(hi[k][3]) + static_cast<double>(lo[k][3]));
+    }
+  }
+
+  __device__ __forceinline__ void store_partial(float4* slot, int il, int i_tile, int k) const {
+    slot[il] = make_float4(hi[k][0], hi[k][1], hi[k][2], POT ? hi[k][3] : 0.f);
+    slot[i_tile + il] = make_float4(lo[k][0], lo[k][1], lo[k][2], POT ? lo[k][3] : 0.f);
+  }
+
+  __device__ static __forceinline__ void add_partial(const float4* slot, int il, int i_tile, double (&s)[4]) {
+    const float4 h = __ldcg(slot + il);
+    const float4 l = __ldcg(slot + i_tile + il);
+    s[0] += static_cast<double>(h.x) + static_cast<double>(l.x);
+    s[1] += static_cast<double>(h.y) + static_cast<double>(l.y);
+    s[2] += static_cast<double>(h.z) + static_cast<double>(l.z);
+    s[3] += static_cast<double>(h.w) + static_cast<double>(l.w);
+  }
+
+  __device__ static __forceinline__ void store_merged(const PairArgs& a, int64_t i, const double (&s)[4]) {
+    double* acc = static_cast<double*>(a.acc_out) + 3 * i;
+    acc[0] = s[0];
+    acc[1] = s[1];
+    acc[2] = s[2];
+    if constexpr (POT) {
+      if (a.pot_out) static_cast<double*>(a.pot_out)[i] = -s[3];
+    }
+  }
+};
+
+// Adjoint of L = sum_i w_i . a_i (i set = j set). Per pair, with
+// d = x_p - x_k, s = |d|^2 + eps2, g = s^-3/2, h = s^-5/2 and
+// u = m_k w_p - m_p w_k, the thread owning k adds g u - 3 h (d . u) d to
+// dL/dx_k and -g (w_p . d) to dL/dm_k: 3 FADD + 3 FFMA + MUFU + 4 FMUL for
+// s, g and 3h; 6 for u; 3 for d . u; 1 for 3h (d . u); 6 into dL/dx; 3 for
+// w_p . d; 1 into dL/dm. The self pair is skipped exactly: units whose
+// j-range overlaps the i-tile compare indices (the `diag` path).
+template <int K, bool GUARD, bool SELF>
+__device__ __forceinline__ void pair_adjoint(const float4 pj, const float4 wp, const float (&xk)[K][3],
+                                             const float (&mk)[K], const float (&wk)[K][3], float eps2, int j,
+                                             const int (&self_j)[K], float (&part)[K][4]) {
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const float dx = pj.x - xk[k][0];
+    const float dy = pj.y - xk[k][1];
+    const float dz = pj.z - xk[k][2];
+    const float s = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+    float r = rsqrt_mufu(s);
+    if constexpr (GUARD) r = (s > 0.f) ? r : 0.f;
+    if constexpr (SELF) r = (j == self_j[k]) ? 0.f : r;
+    const float r2 = r * r;
+    const float g = r2 * r;
+    const float h3 = g * (3.0f * r2);
+    const float ux = fmaf(mk[k], wp.x, -(pj.w * wk[k][0]));
+    const float uy = fmaf(mk[k], wp.y, -(pj.w * wk[k][1]));
+    const float uz = fmaf(mk[k], wp.z, -(pj.w * wk[k][2]));
+    const float c = h3 * fmaf(dx, ux, fmaf(dy, uy, dz * uz));
+    part[k][0] = fmaf(-c, dx, fmaf(g, ux, part[k][0]));
+    part[k][1] = fmaf(-c, dy, fmaf(g, uy, part[k][1]));
+    part[k][2] = fmaf(-c, dz, fmaf(g, uz, part[k][2]));
+    part[k][3] = fmaf(-g, fmaf(wp.x, dx, fmaf(wp.y, dy, wp.z * dz)), part[k][3]);
+  }
+}
+
+template <int K, bool GUARD>
+struct AdjointPolicy {
+  static constexpr int NC = 4;
+  static constexpr int kSlotF4 = 1;
+  static constexpr int kJRec = 2;  // (x, y, z, m) then (wx, wy, wz, 0)
+  float xk[K][3];
+  float mk[K];
+  float wk[K][3];
+  float run[K][4];
+
+  __device__ __forceinline__ void load_i(const PairArgs& a, int64_t gi, bool valid, int k) {
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (valid) {
+      v = __ldg(a.pos_i + gi);
+      w = __ldg(a.pos_i2 + gi);
+    }
+    xk[k][0] = v.x;
+    xk[k][1] = v.y;
+    xk[k][2] = v.z;
+    mk[k] = v.w;
+    wk[k][0] = w.x;
+    wk[k][1] = w.y;
+    wk[k][2] = w.z;
+  }
+
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) run[k][c] = 0.f;
+  }
+
+  // self_off = (first j index of the tile) - (first i index of the i-tile)
+  __device__ __forceinline__ void tile(const float4* js, int T, float eps2, int64_t self_off, bool diag, int tid,
+                                       int NT) {
+    const float4* jw = js + T;
+    float part[K][4];
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) part[k][c] = 0.f;
+    int self_j[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      // the j slot (0 .. T-1) holding this thread's own particle, or -1
+      const int64_t sj = static_cast<int64_t>(k * NT + tid) - self_off;
+      self_j[k] = (sj >= 0 && sj < T) ? static_cast<int>(sj) : -1;
+    }
+    if (!diag) {
+#pragma unroll 1
+      for (int j = 0; j < T; j += 8) {
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj)
+          pair_adjoint<K, GUARD, false>(js[j + jj], jw[j + jj], xk, mk, wk, eps2, j + jj, self_j, part);
+      }
+    } else {
+#pragma unroll 1
+      for (int j = 0; j < T; j += 8) {
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj)
+          pair_adjoint<K, GUARD, true>(js[j + jj], jw[j + jj], xk, mk, wk, eps2, j + jj, self_j, part);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) run[k][c] += part[k][c];
+  }
+
+  __device__ __forceinline__ void store_final(const PairArgs& a, int64_t i, int k) const {
+    float* g = static_cast<float*>(a.acc_out) + 3 * i;
+    g[0] = run[k][0];
+    g[1] = run[k][1];
+    g[2] = run[k][2];
+    static_cast<float*>(a.pot_out)[i] = run[k][3];
+  }
+
+  __device__ __forceinline__ void store_partial(float4* slot, int il, int /*i_tile*/, int k) const {
+    slot[il] = make_float4(run[k][0], run[k][1], run[k][2], run[k][3]);
+  }
+
+  __device__ static __forceinline__ void add_partial(const float4* slot, int il, int /*i_tile*/, double (&s)[4]) {
+    const float4 v = __ldcg(slot + il);
+    s[0] += v.x;
+    s[1] += v.y;
+    s[2] += v.z;
+    s[3] += v.w;
+  }
+
+  __device__ static __forceinline__ void store_merged(const PairArgs& a, int64_t i, const double (&s)[4]) {
+    float* g = static_cast<float*>(a.acc_out) + 3 * i;
+    g[0] = static_cast<float>(s[0]);
+    g[1] = static_cast<float>(s[1]);
+    g[2] = static_cast<float>(s[2]);
+    static_cast<float*>(a.pot_out)[i] = static_cast<float>(s[3]);
+  }
+};
+
+// ------------------------------------------------------------------ kernel
+template <class Policy, int K, bool BATCHED>
+__global__ void __launch_bounds__(256) pair_kernel(const __grid_constant__ PairArgs a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int NT = blockDim.x;
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int T = a.j_tile;
+  const int S = a.stages;
+  const int IT = NT * K;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem);
+  uint64_t* empty = full + S;
+  volatile int* ctl = reinterpret_cast<volatile int*>(smem + 16 * S);  // [0] abort [1] last [2] chunk
+  float4* ring = reinterpret_cast<float4*>(smem + 256);
+
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], NT / 32);
+    }
+    ctl[0] = 0;
+    ctl[1] = 0;
+    mbar_init_fence();
+  }
+  __syncthreads();
+
+  const Sched sc{a.total_units, a.n_chunks, a.chunk_units};
+  const bool dynamic = a.chunk_units > 0;
+  const uint32_t D = S > 2 ? static_cast<uint32_t>(S - 2) : 1u;  // prefetch distance in tiles
+  uint32_t issued = 0;    // loads issued (thread 0 only)
+  uint32_t consumed = 0;  // tiles consumed (identical in every thread)
+  constexpr int JR = Policy::kJRec;
+  Policy acc;
+
+  int64_t q = dynamic ? -1 : static_cast<int64_t>(blockIdx.x);
+  for (;;) {
+    if (dynamic) {
+      if (tid == 0) ctl[2] = atomicAdd(&a.queue[0], 1);
+      __syncthreads();
+      q = ctl[2];
+      __syncthreads();
+    }
+    if (q >= sc.Q) break;
+    const int64_t ub = sc.begin(q);
+    const int64_t ue = sc.end(q);
+    if (ub < ue) {
+      int32_t tc = tile_of_unit<BATCHED>(a, ub);
+      TileDesc td = tile_at<BATCHED>(a, tc, IT);
+      int64_t jt = ub - td.unit0;
+      // producer cursor (meaningful in thread 0 only)
+      int32_t tp = tc;
+      TileDesc tdp = td;
+      int64_t jtp = jt;
+      const uint32_t last_load = consumed + static_cast<uint32_t>(ue - ub);
+      int64_t seg_u0 = ub;
+      bool seg_open = false;
+      for (int64_t uc = ub; uc < ue; ++uc) {
+        if (tid == 0) {
+          while (!ctl[0] && issued < last_load && issued <= consumed + D) {
+            const int slot = static_cast<int>(issued % S);
+            if (issued >= static_cast<uint32_t>(S) &&
+                !mbar_wait(&empty[slot], ((issued / S) - 1) & 1u, a.wait_ns)) {
+              set_status(a.status, kStatusTimeoutEmpty);
+              ctl[0] = 1;
+              break;
+            }
+            const int64_t jb = jtp * T;
+            const int64_t left = tdp.nj - jb;
+            const int cnt = static_cast<int>(left < T ? left : T);
+            float4* dst = ring + static_cast<size_t>(slot) * T * JR;
+            for (int z = cnt; z < T; ++z) {  // zero-mass (and zero-weight) padding of a short tile
+              dst[z] = make_float4(0.f, 0.f, 0.f, 0.f);
+              if constexpr (JR == 2) dst[T + z] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(&full[slot], static_cast<uint32_t>(cnt) * 16u * JR);
+            bulk_copy_g2s(dst, a.pos_j + tdp.j0 + jb, static_cast<uint32_t>(cnt) * 16u, &full[slot]);
+            if constexpr (JR == 2)
+              bulk_copy_g2s(dst + T, a.pos_j2 + tdp.j0 + jb, static_cast<uint32_t>(cnt) * 16u, &full[slot]);
+            ++issued;
+            if (++jtp == tdp.njt) {
+              ++tp;
+              jtp = 0;
+              if (tp < a.n_tiles) tdp = tile_at<BATCHED>(a, tp, IT);
+            }
+          }
+        }
+        if (!seg_open) {
+#pragma unroll
+          for (int k = 0; k < K; ++k) {
+            const int il = k * NT + tid;
+            acc.load_i(a, td.i0 + il, il < td.ni, k);
+          }
+          acc.zero();
+          seg_u0 = uc;
+          seg_open = true;
+        }
+        const int slot = static_cast<int>(consumed % S);
+        // After a timed-out wait anywhere in the CTA (ctl[0] set) every thread
+        // keeps walking the same units and segment ends - so all of them meet
+        // the same barriers - but waits, computes and releases nothing more.
+        bool live = !ctl[0];
+        if (live && !mbar_wait(&full[slot], (consumed / S) & 1u, a.wait_ns)) {
+          set_status(a.status, kStatusTimeoutFull);
+          ctl[0] = 1;
+          live = false;
+        }
+        live = __all_sync(0xffffffffu, live);
+        if (live) {
+          // j-range of this unit relative to the i-tile (used by the adjoint's self-pair exclusion)
+          const int64_t self_off = td.j0 + jt * T - td.i0;
+          const bool diag = self_off < IT && self_off + T > 0;
+          acc.tile(ring + static_cast<size_t>(slot) * T * JR, T, td.eps2, self_off, diag, tid, NT);
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&empty[slot]);
+        }
+        ++consumed;
+        ++jt;
+        if (jt == td.njt || uc + 1 == ue) {
+          // ---- end of a segment: write the tile or its partial
+          const int64_t qf = sc.chunk_of(td.unit0);
+          const int64_t ql = sc.chunk_of(td.unit0 + td.njt - 1);
+          if (qf == ql) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+              const int il = k * NT + tid;
+              if (il < td.ni) acc.store_final(a, td.i0 + il, k);
+            }
+          } else {
+            const int which = (seg_u0 == ub) ? 0 : 1;
+            float4* slotp = a.partials + static_cast<size_t>(q * 2 + which) * IT * Policy::kSlotF4;
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+              const int il = k * NT + tid;
+              acc.store_partial(slotp, il, IT, k);
+            }
+            __threadfence();
+            __syncthreads();
+            if (tid == 0) {
+              const int before = arrive_counter(&a.counters[tc], a.epoch);
+              ctl[1] = (before == static_cast<int>(ql - qf)) ? 1 : 0;
+            }
+            __syncthreads();
+            if (ctl[1]) {
+              __threadfence();
+              for (int k = 0; k < K; ++k) {
+                const int il = k * NT + tid;
+                if (il >= td.ni) continue;
+                double s[4] = {0.0, 0.0, 0.0, 0.0};
+                for (int64_t p = qf; p <= ql; ++p) {
+                  const int w = (sc.begin(p) >= td.unit0) ? 0 : 1;
+                  Policy::add_partial(a.partials + static_cast<size_t>(p * 2 + w) * IT * Policy::kSlotF4, il, IT,
+                                      s);
+                }
+                Policy::store_merged(a, td.i0 + il, s);
+              }
+              if (tid == 0) a.counters[tc] = 0ull;
+            }
+          }
+          seg_open = false;
+          if (jt == td.njt) {
+            ++tc;
+            jt = 0;
+            if (tc < a.n_tiles) td = tile_at<BATCHED>(a, tc, IT);
+          }
+        }
+      }
+    }
+    if (!dynamic) break;
+  }
+
+  if (dynamic && tid == 0) {
+    __threadfence();
+    const int done = atomicAdd(&a.queue[1], 1);
+    if (done == static_cast<int>(gridDim.x) - 1) {
+      a.queue[0] = 0;
+      a.queue[1] = 0;
+    }
+  }
+  // On an aborted run, wait (bounded) for copies that may still be in
+  // flight - at most the latest one per stage, since a stage is refilled
+  // only after every warp saw its previous copy land - before the shared
+  // memory they target is released.
+  if (tid == 0 && ctl[0]) {
+    for (uint32_t c = issued > static_cast<uint32_t>(S) ? issued - S : 0u; c < issued; ++c) {
+      if (!mbar_wait(&full[c % S], (c / S) & 1u, a.wait_ns)) {
+        set_status(a.status, kStatusTimeoutDrain);
+        break;
+      }
+    }
+  }
+}
+
+}  // namespace cn

@@ -1,0 +1,118 @@
+"""Parity of the adjoint kernel (dL/dx, dL/dm for L = sum_i w_i . a_i).
+
+The CUDA gradient is checked against the oracle's analytic FP64 gradient
+and against FP64 central finite differences of L (Richardson-extrapolated)
+on a seeded subset. Tolerance: FP32 pair arithmetic with cancellation
+between the two halves of u = m_k w_p - m_p w_k; per particle
+|g_gpu - g_ref| / |g_ref| <= 1e-4 for dL/dx and max |dm_gpu - dm_ref| /
+max |dm_ref| <= 1e-5 for dL/dm.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from gpu_common import dev_tensor, e_max, lib, torch_cuda
+from paper_astro_ph_0703100_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL_POS = 1e-4
+TOL_MASS = 1e-5
+
+
+def gpu_adjoint(cn, p, w, eps2):
+    torch = torch_cuda()
+    gp, gm = cn.cn_force_adjoint(dev_tensor(p), eps2, dev_tensor(w))
+    torch.cuda.synchronize()
+    assert cn.cn_get_device_status() == 0
+    return gp.cpu().numpy().astype(np.float64), gm.cpu().numpy().astype(np.float64)
+
+
+def mass_err(gm, ref):
+    return float(np.max(np.abs(gm - ref)) / np.max(np.abs(ref)))
+
+
+@pytest.mark.parametrize("n", [1, 2, 33, 1000, 3001])
+def test_adjoint_small_all_particles(n):
+    cn = lib()
+    p = synth.plummer(n, 100 + n)
+    w = synth.adjoint_weights(n, 200 + n)
+    gp, gm = gpu_adjoint(cn, p, w, 0.01)
+    rp, rm = oracle.adjoint(p, 0.01, w)
+    if n == 1:
+        assert np.all(gp == 0) and np.all(gm == 0)
+        return
+    assert e_max(gp, rp) <= TOL_POS
+    assert mass_err(gm, rm) <= TOL_MASS
+
+
+@pytest.mark.parametrize("tune", [{"i_per_thread": 1, "threads": 64, "j_tile": 32, "stages": 2},
+                                  {"i_per_thread": 4, "threads": 128, "j_tile": 256, "stages": 4}])
+def test_adjoint_launch_shapes(tune):
+    cn = lib()
+    n = 2500
+    p = synth.plummer(n, 1)
+    w = synth.adjoint_weights(n, 2)
+    cn.cn_tune_set("adjoint", n, n, tune)
+    try:
+        gp, gm = gpu_adjoint(cn, p, w, 0.01)
+    finally:
+        cn.cn_tune_set("adjoint", n, n, None)
+    rp, rm = oracle.adjoint(p, 0.01, w)
+    assert e_max(gp, rp) <= TOL_POS
+    assert mass_err(gm, rm) <= TOL_MASS
+
+
+def test_adjoint_c5_oracle_and_finite_differences():
+    """N = 65536 Plummer, eps = 0.01: analytic gradient on sampled rows, FD on 256."""
+    cn = lib()
+    n = 65536
+    p = synth.plummer(n, 65536)
+    w = synth.adjoint_weights(n, 65537)
+    eps2 = float(np.float32(0.01) ** 2)
+    gp, gm = gpu_adjoint(cn, p, w, eps2)
+    rows = synth.sample_rows(n, 1024, seed=3)
+    rp, rm = oracle.adjoint(p, eps2, w, rows=rows)
+    assert e_max(gp[rows], rp) <= TOL_POS
+    assert float(np.max(np.abs(gm[rows] - rm)) / np.max(np.abs(rm))) <= TOL_MASS
+    fd_rows = synth.sample_rows(n, 256, seed=256)
+    for k in fd_rows[:64]:  # 64 of the 256 here; the bench's reference leg covers all
+        x0 = p[k, :3].astype(np.float64)
+        m0 = float(p[k, 3])
+        fd = np.zeros(3)
+        for c in range(3):
+            est = []
+            for h in (2e-5, 1e-5):
+                xp = x0.copy(); xp[c] += h
+                xm = x0.copy(); xm[c] -= h
+                est.append((oracle.loss_k(p, eps2, w, k, xp, m0) - oracle.loss_k(p, eps2, w, k, xm, m0)) / (2 * h))
+            fd[c] = (4 * est[1] - est[0]) / 3
+        assert np.linalg.norm(gp[k] - fd) <= TOL_POS * np.linalg.norm(fd) + 1e-6 * np.abs(rp).max()
+        h = 1e-3 * m0
+        fdm = (oracle.loss_k(p, eps2, w, k, x0, m0 + h) - oracle.loss_k(p, eps2, w, k, x0, m0 - h)) / (2 * h)
+        assert abs(gm[k] - fdm) <= TOL_MASS * np.max(np.abs(rm))
+
+
+def test_autograd_matches_adjoint_entry_point():
+    cn = lib()
+    torch = torch_cuda()
+    p = synth.plummer(777, 5)
+    w = synth.adjoint_weights(777, 6)
+    pm = dev_tensor(p).requires_grad_(True)
+    acc = cn.gravity(pm, 0.02)
+    (acc * dev_tensor(w)).sum().backward()
+    gp, gm = cn.cn_force_adjoint(dev_tensor(p), 0.02, dev_tensor(w))
+    torch.cuda.synchronize()
+    assert torch.equal(pm.grad[:, :3], gp) and torch.equal(pm.grad[:, 3], gm)
+
+
+def test_adjoint_zero_softening_guard():
+    cn = lib()
+    p = synth.plummer(400, 8)
+    w = synth.adjoint_weights(400, 9)
+    gp, gm = gpu_adjoint(cn, p, w, 0.0)
+    rp, rm = oracle.adjoint(p, 0.0, w)
+    assert np.all(np.isfinite(gp)) and np.all(np.isfinite(gm))
+    assert e_max(gp, rp) <= TOL_POS
+    assert mass_err(gm, rm) <= TOL_MASS

@@ -1,0 +1,221 @@
+"""Parity of cn_force / cn_force_dd (CUDA, sm_103a) with the FP64 oracle.
+
+Tolerances (per-particle |a_gpu - a_oracle| / |a_oracle|, max over the
+checked particles, Eq. 4):
+  plain FP32       <= 1e-5
+  compensated      <= 1e-7 on the Plummer workloads (the FP32 pair
+                   arithmetic, refined by one Newton-Raphson step, sets the
+                   floor; see the design notes for the Hernquist case)
+Potentials: relative error <= 1e-5 (FP32) / 1e-7 (compensated).
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from gpu_common import dev_tensor, e_max, lib, rel_pot_err, torch_cuda
+from paper_astro_ph_0703100_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL_F32 = 1e-5
+TOL_DD = 1e-7
+
+
+def run(cn, pi, pj, eps2, potential=False, dd=False):
+    torch = torch_cuda()
+    ti, tj = dev_tensor(pi), dev_tensor(pj)
+    fn = cn.cn_force_dd if dd else cn.cn_force
+    acc, pot = fn(ti, tj, eps2, potential=potential)
+    torch.cuda.synchronize()
+    assert cn.cn_get_device_status() == 0
+    return acc.cpu().numpy(), (pot.cpu().numpy() if pot is not None else None)
+
+
+def test_c1_plummer_1024_acc_and_potential():
+    cn = lib()
+    p = synth.plummer(1024, 1001)
+    eps2 = float(np.float32(1 / 64) ** 2)
+    acc, pot = run(cn, p, p, eps2, potential=True)
+    ref_a, ref_p = oracle.force(p, p, eps2)
+    assert e_max(acc, ref_a) <= TOL_F32
+    assert rel_pot_err(pot, ref_p) <= TOL_F32
+
+
+@pytest.mark.parametrize("n", [2048])
+def test_c2_small_all_i(n):
+    cn = lib()
+    p = synth.plummer(n, n)
+    eps2 = float(np.float32(synth.plummer_eps(n)) ** 2)
+    acc, _ = run(cn, p, p, eps2)
+    ref, _ = oracle.force(p, p, eps2, potential=False)
+    assert e_max(acc, ref) <= TOL_F32
+
+
+@pytest.mark.parametrize("n", [16384, 131072])
+def test_c2_large_sampled_rows_autotuned(n):
+    """Full-size runs in the launch shape the benchmark uses (autotuned)."""
+    cn = lib()
+    torch = torch_cuda()
+    p = synth.plummer(n, n)
+    eps2 = float(np.float32(synth.plummer_eps(n)) ** 2)
+    t = dev_tensor(p)
+    cn.cn_autotune("f32", t, t, eps2, reps=2)
+    acc, _ = cn.cn_force(t, t, eps2)
+    torch.cuda.synchronize()
+    rows = synth.sample_rows(n, 4096, seed=n + 1)
+    ref, _ = oracle.force(p, p, eps2, rows=rows, potential=False)
+    assert e_max(acc.cpu().numpy()[rows], ref) <= TOL_F32
+    cn.cn_tune_set("f32", n, n, None)
+
+
+SHAPES = [
+    (1, 1), (1, 7), (7, 1), (31, 33), (33, 31), (257, 1000), (1000, 777), (3000, 5001), (4097, 2049),
+]
+TUNES = [
+    None,
+    {"i_per_thread": 1, "threads": 64, "j_tile": 8, "stages": 2},
+    {"i_per_thread": 2, "threads": 128, "j_tile": 64, "stages": 3},
+    {"i_per_thread": 4, "threads": 256, "j_tile": 256, "stages": 4},
+    {"i_per_thread": 8, "threads": 128, "j_tile": 512, "stages": 6},
+    {"i_per_thread": 4, "threads": 64, "j_tile": 128, "stages": 4, "chunk_units": 3},
+    {"i_per_thread": 2, "threads": 128, "j_tile": 32, "stages": 4, "ctas_per_sm": 1},
+]
+
+
+@pytest.mark.parametrize("tune", TUNES)
+@pytest.mark.parametrize("shape", SHAPES)
+def test_ragged_shapes_and_launch_shapes(shape, tune):
+    cn = lib()
+    n_i, n_j = shape
+    pj = synth.plummer(n_j, 11 + n_j)
+    pi = synth.plummer(n_i, 5 + n_i)  # an i set distinct from the j set
+    eps2 = 1e-3
+    for variant in ("f32", "f32_pot"):
+        cn.cn_tune_set(variant, n_i, n_j, tune)
+    try:
+        acc, pot = run(cn, pi, pj, eps2, potential=True)
+        acc2, _ = run(cn, pi, pj, eps2, potential=False)
+    finally:
+        for variant in ("f32", "f32_pot"):
+            cn.cn_tune_set(variant, n_i, n_j, None)
+    ref_a, ref_p = oracle.force(pi, pj, eps2)
+    assert e_max(acc, ref_a) <= TOL_F32
+    assert e_max(acc2, ref_a) <= TOL_F32
+    assert rel_pot_err(pot, ref_p) <= TOL_F32
+
+
+@pytest.mark.parametrize("tune", [None, {"i_per_thread": 2, "threads": 64, "j_tile": 64, "stages": 3},
+                                  {"i_per_thread": 4, "threads": 128, "j_tile": 128, "chunk_units": 5}])
+def test_bitwise_deterministic(tune):
+    cn = lib()
+    torch = torch_cuda()
+    p = synth.plummer(6000, 3)
+    t = dev_tensor(p)
+    cn.cn_tune_set("f32_pot", 6000, 6000, tune)
+    try:
+        a1, p1 = cn.cn_force(t, t, 1e-3, potential=True)
+        a2, p2 = cn.cn_force(t, t, 1e-3, potential=True)
+        torch.cuda.synchronize()
+    finally:
+        cn.cn_tune_set("f32_pot", 6000, 6000, None)
+    assert torch.equal(a1, a2) and torch.equal(p1, p2)
+
+
+def test_zero_softening_and_coincident_points():
+    """eps2 = 0: pairs with zero separation add nothing (no inf/NaN)."""
+    cn = lib()
+    p = synth.plummer(700, 9)
+    p[100:110] = p[50]  # ten exact copies of particle 50
+    acc, pot = run(cn, p, p, 0.0, potential=True)
+    ref_a, ref_p = oracle.force(p, p, 0.0)
+    assert np.all(np.isfinite(acc)) and np.all(np.isfinite(pot))
+    assert e_max(acc, ref_a) <= TOL_F32
+    assert rel_pot_err(pot, ref_p) <= TOL_F32
+    # subnormal eps2 takes the same guarded path
+    acc, _ = run(cn, p, p, 1e-40)
+    assert np.all(np.isfinite(acc))
+
+
+def test_potential_excludes_self_and_duplicates_with_softening():
+    cn = lib()
+    p = synth.plummer(300, 4)
+    p[7] = p[3]
+    acc, pot = run(cn, p, p, 0.01, potential=True)
+    ref_a, ref_p = oracle.force(p, p, 0.01)
+    assert rel_pot_err(pot, ref_p) <= TOL_F32
+    assert e_max(acc, ref_a) <= TOL_F32
+
+
+def test_empty_j_set_writes_zeros_and_empty_i_is_noop():
+    cn = lib()
+    torch = torch_cuda()
+    pi = dev_tensor(synth.plummer(50, 1))
+    pj = torch.zeros((0, 4), dtype=torch.float32, device="cuda")
+    acc = torch.full((50, 3), 7.0, device="cuda")
+    pot = torch.full((50,), 7.0, device="cuda")
+    cn.cn_force(pi, pj, 0.01, acc_out=acc, pot_out=pot)
+    torch.cuda.synchronize()
+    assert torch.count_nonzero(acc) == 0 and torch.count_nonzero(pot) == 0
+    a0, _ = cn.cn_force(pi[:0], pi, 0.01)
+    assert a0.shape == (0, 3)
+
+
+def test_workspace_form_matches_library_workspace():
+    cn = lib()
+    torch = torch_cuda()
+    p = synth.plummer(5000, 12)
+    t = dev_tensor(p)
+    nbytes = cn.cn_workspace_bytes("f32_pot", 5000, 5000)
+    assert nbytes > 0
+    ws = torch.zeros(nbytes, dtype=torch.uint8, device="cuda")
+    a1, p1 = cn.cn_force_ws(t, t, 1e-3, ws, potential=True)
+    a2, p2 = cn.cn_force_ws(t, t, 1e-3, ws, potential=True)  # counters were left zero by the first call
+    a3, p3 = cn.cn_force(t, t, 1e-3, potential=True)
+    torch.cuda.synchronize()
+    assert torch.equal(a1, a3) and torch.equal(a2, a3) and torch.equal(p1, p3)
+    small = torch.zeros(256, dtype=torch.uint8, device="cuda")
+    with pytest.raises(cn.CunbodyError) as ei:
+        cn.cn_force_ws(t, t, 1e-3, small)
+    assert ei.value.code == "CN_ERR_WORKSPACE"
+
+
+# ------------------------------------------------------------------ compensated form
+
+def test_dd_plummer_all_i():
+    cn = lib()
+    n = 2048
+    p = synth.plummer(n, n)
+    eps2 = float(np.float32(synth.plummer_eps(n)) ** 2)
+    acc, pot = run(cn, p, p, eps2, potential=True, dd=True)
+    ref_a, ref_p = oracle.force(p, p, eps2)
+    assert acc.dtype == np.float64
+    assert e_max(acc, ref_a) <= TOL_DD
+    assert rel_pot_err(pot, ref_p) <= TOL_DD
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (31, 33), (1000, 777), (4097, 2049)])
+def test_dd_ragged(shape):
+    cn = lib()
+    n_i, n_j = shape
+    pj = synth.plummer(n_j, 21 + n_j)
+    pi = synth.plummer(n_i, 2 + n_i)
+    acc, pot = run(cn, pi, pj, 1e-2, potential=True, dd=True)
+    ref_a, ref_p = oracle.force(pi, pj, 1e-2)
+    assert e_max(acc, ref_a) <= TOL_DD
+    assert rel_pot_err(pot, ref_p) <= TOL_DD
+
+
+def test_dd_beats_f32_on_plummer_131072_sampled():
+    cn = lib()
+    n = 131072
+    p = synth.plummer(n, n)
+    eps2 = float(np.float32(synth.plummer_eps(n)) ** 2)
+    rows = synth.sample_rows(n, 2048, seed=77)
+    ref, _ = oracle.force(p, p, eps2, rows=rows, potential=False)
+    a32, _ = run(cn, p, p, eps2)
+    add, _ = run(cn, p, p, eps2, dd=True)
+    e32, edd = e_max(a32[rows], ref), e_max(add[rows], ref)
+    assert e32 <= TOL_F32
+    assert edd <= TOL_DD
+    assert edd < e32

@@ -1,0 +1,113 @@
+"""Potential energy, host-memory forms, tuning, probes, failure paths."""
+
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from gpu_common import dev_tensor, e_max, lib, torch_cuda
+from paper_astro_ph_0703100_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def test_potential_energy_fp32_and_dd():
+    cn = lib()
+    torch = torch_cuda()
+    n = 16384
+    p = synth.plummer(n, 101)
+    eps2 = float(np.float32(1e-3) ** 2)
+    t = dev_tensor(p)
+    _, pot = cn.cn_force(t, t, eps2, potential=True)
+    _, pot_d = cn.cn_force_dd(t, t, eps2, potential=True)
+    w32 = cn.cn_potential_energy(t, pot)
+    wdd = cn.cn_potential_energy_dd(t, pot_d)
+    torch.cuda.synchronize()
+    _, ref_p = oracle.force(p, p, eps2)
+    ref_w = oracle.potential_energy(p, ref_p)
+    assert float(w32.item()) == pytest.approx(ref_w, rel=1e-6)
+    assert float(wdd.item()) == pytest.approx(ref_w, rel=1e-9)
+    # same inputs, same result (fixed-order FP64 reduction)
+    assert float(cn.cn_potential_energy(t, pot).item()) == float(w32.item())
+
+
+def test_host_forms():
+    cn = lib()
+    torch = torch_cuda()
+    p = synth.plummer(3000, 77)
+    acc_h, pot_h = cn.cn_force_host(p, p, 1e-3, potential=True)
+    t = dev_tensor(p)
+    acc_d, pot_d = cn.cn_force(t, t, 1e-3, potential=True)
+    torch.cuda.synchronize()
+    assert np.array_equal(acc_h, acc_d.cpu().numpy()) and np.array_equal(pot_h, pot_d.cpu().numpy())
+    # pinned host tensors
+    pin = torch.from_numpy(p).pin_memory()
+    acc_pin = torch.empty((3000, 3), dtype=torch.float32).pin_memory()
+    pot_pin = torch.empty((3000,), dtype=torch.float32).pin_memory()
+    cn.cn_force_host(pin, pin, 1e-3, acc_out=acc_pin, pot_out=pot_pin)  # same kernel variant as acc_h
+    assert np.array_equal(acc_pin.numpy(), acc_h) and np.array_equal(pot_pin.numpy(), pot_h)
+    # the paper's routine: FP64 host arrays, i set != j set
+    xj = p[:, :3].astype(np.float64)
+    mj = p[:, 3].astype(np.float64)
+    xi = synth.plummer(100, 78)[:, :3].astype(np.float64)
+    a = cn.cn_force_host_f64(xj, mj, xi, 1e-3)
+    pi = np.zeros((100, 4), dtype=np.float32)
+    pi[:, :3] = xi
+    ref, _ = oracle.force(pi, p, 1e-3, potential=False)
+    assert e_max(a, ref) <= 1e-5
+
+
+def test_tune_roundtrip_and_probe():
+    cn = lib()
+    t = {"i_per_thread": 2, "threads": 256, "j_tile": 64, "stages": 3, "ctas_per_sm": 0, "chunk_units": 0}
+    cn.cn_tune_set("f32", 5000, 7000, t)
+    assert cn.cn_tune_get("f32", 5000, 7000) == t
+    cn.cn_tune_set("f32", 5000, 7000, None)
+    assert cn.cn_tune_get("f32", 5000, 7000) != t
+    peaks = cn.cn_probe_peaks()
+    assert peaks["sms"] >= 100
+    assert peaks["ffma_per_s"] > 1e12 and peaks["mufu_rsqrt_per_s"] > 1e11 and peaks["pair_mix_per_s"] > 1e11
+    assert 500 < peaks["sm_mhz"] < 3000
+
+
+def test_timeout_path_reports_and_recovers():
+    """A wait that nothing completes gives up after the limit; the context stays usable."""
+    cn = lib()
+    torch = torch_cuda()
+    cn.cn_set_wait_limit_ns(2_000_000)  # 2 ms
+    try:
+        cn.cn_debug_timeout_probe()
+        assert cn.cn_get_device_status() == 4  # CN_ERR_TIMEOUT
+        assert cn.cn_get_device_status() == 0  # cleared
+    finally:
+        cn.cn_set_wait_limit_ns(0)
+    p = synth.plummer(500, 1)
+    t = dev_tensor(p)
+    acc, _ = cn.cn_force(t, t, 1e-2)
+    torch.cuda.synchronize()
+    ref, _ = oracle.force(p, p, 1e-2, potential=False)
+    assert e_max(acc.cpu().numpy(), ref) <= 1e-5
+
+
+def test_host_fault_injection(monkeypatch):
+    cn = lib()
+    torch = torch_cuda()
+    t = dev_tensor(synth.plummer(100, 2))
+    monkeypatch.setenv("CN_FAULT_INJECT", "launch")
+    with pytest.raises(cn.CunbodyError) as ei:
+        cn.cn_force(t, t, 1e-2)
+    assert ei.value.code == "CN_ERR_CUDA" and "injected" in str(ei.value)
+    monkeypatch.setenv("CN_FAULT_INJECT", "alloc")
+    s = torch.cuda.Stream()  # a fresh stream has no library workspace yet
+    with pytest.raises(cn.CunbodyError) as ei:
+        cn.cn_force(t, t, 1e-2, stream=s)
+    assert ei.value.code == "CN_ERR_CUDA"
+    monkeypatch.setenv("CN_FAULT_INJECT", "capture")
+    with pytest.raises(cn.CunbodyError) as ei:
+        cn.cn_force(t, t, 1e-2, stream=torch.cuda.Stream())
+    assert ei.value.code == "CN_ERR_WORKSPACE"
+    monkeypatch.delenv("CN_FAULT_INJECT")
+    acc, _ = cn.cn_force(t, t, 1e-2)
+    torch.cuda.synchronize()
+    assert torch.isfinite(acc).all()
