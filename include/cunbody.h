@@ -147,6 +147,30 @@ CN_API cn_status cn_force_dd_ws(int64_t n_i, const float *pos_i, int64_t n_j, co
  * CN_VARIANT_ADJOINT pass n_i = n_j = n. Returns 0 for invalid input. */
 CN_API size_t cn_workspace_bytes(int variant, int64_t n_i, int64_t n_j);
 
+/*
+ * cn_force for callers that cannot allocate device memory. The paper has no
+ * counterpart; it exists because some callers may not call cudaMalloc at
+ * all - a host application whose own memory manager owns every device
+ * allocation, or a latency-bound loop that cannot afford the device-wide
+ * synchronisation that cudaMalloc and cudaFree may imply - while cn_force
+ * grows a library workspace on demand and cn_force_ws needs a buffer from
+ * the caller.
+ *   Arguments, results and errors as cn_force; nothing is allocated.
+ *   Scratch: a fixed 32 MiB array in the library's device image (every GPU
+ *   that loads the library holds it until the process exits). A problem
+ *   whose launch shape needs more scratch than that (see
+ *   cn_workspace_bytes) is rejected with CN_ERR_WORKSPACE before anything
+ *   runs.
+ *   The first call on each device looks up the array's device address (a
+ *   one-time set-up with that device current); make that first call before
+ *   capturing any stream.
+ *   Every call uses the same array: calls that overlap on the GPU (other
+ *   streams, other host threads) race and corrupt each other's results, so
+ *   serialise them. Each call clears the part that must start at zero.
+ */
+CN_API cn_status cn_force_noalloc(int64_t n_i, const float *pos_i, int64_t n_j, const float *pos_mass_j, float eps2,
+                                  float *acc_out, float *pot_out, cn_stream stream);
+
 /* ------------------------------------------------------------------ batched */
 
 /* An ensemble of independent systems ("clusters") stored back to back:

@@ -647,6 +647,16 @@ cn_status energy_common(int64_t n, const float* pos_mass, const float* pot_f, co
 
 }  // namespace
 
+namespace cn {
+// cn_force on a workspace the caller supplies, without touching the
+// library-owned workspaces (used by the static-scratch entry point).
+cn_status force_f32_on_workspace(int64_t n_i, const float* pos_i, int64_t n_j, const float* pos_mass_j, float eps2,
+                                 float* acc_out, float* pot_out, void* ws, size_t ws_bytes, cudaStream_t s) {
+  return force_common(false, n_i, pos_i, n_j, pos_mass_j, eps2, acc_out, pot_out, ws, ws_bytes, false, s);
+}
+cn_status set_error(cn_status st, const std::string& msg) { return fail(st, msg); }
+}  // namespace cn
+
 // ====================================================================== C ABI
 extern "C" {
 
