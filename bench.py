@@ -37,7 +37,7 @@ if ROOT not in sys.path:
 METRIC = "pair interactions/s and % of FP32/MUFU roofline at N=131072, FP32 vs compensated"
 UNIT = "pairs/s"
 N_DEFAULT = 131072
-FLOP_PER_PAIR = 38  # the paper's counting convention (Eq. 5)
+FLOP_PER_PAIR = 38  # the paper's counting convention (Eq. 4)
 ISSUE_PER_PAIR = 13  # 12 FP32-pipe instructions + 1 MUFU per pair (plain kernel, no potential)
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
@@ -176,7 +176,7 @@ def workload(n: int, seed: int):
 
 def cpu_baseline(p, eps2, gpu_results: dict, budget_s: float):
     """The FP64 oracle on this host's cores on a bounded row sample, plus the
-    E_max of the GPU results on those rows (Eq. 4)."""
+    E_max of the GPU results on those rows (Eq. 3)."""
     import oracle
 
     n = p.shape[0]
@@ -359,6 +359,57 @@ def run_ours(args):
     return line
 
 
+def run_only(args):
+    """One kernel family on the benchmark workload with a pinned launch shape:
+    W warm-up launches then K timed launches (the command the ncu captures run)."""
+    import torch
+
+    import paper_astro_ph_0703100_gb300 as cn
+    from paper_astro_ph_0703100_gb300 import _build, synth
+
+    _build.build()
+    cn.load()
+    device = torch.device("cuda", 0)
+    torch.cuda.set_device(device)
+    n = args.n
+    tune = None
+    if args.tune:
+        k, th, jt, st = (int(x) for x in args.tune.split(","))
+        tune = {"i_per_thread": k, "threads": th, "j_tile": jt, "stages": st}
+    if args.only in ("f32", "dd"):
+        p, eps2 = workload(n, n)
+        t = torch.from_numpy(p).to(device)
+        if tune:
+            cn.cn_tune_set(args.only, n, n, tune)
+        fn = cn.cn_force if args.only == "f32" else cn.cn_force_dd
+        out = torch.empty((n, 3), dtype=torch.float32 if args.only == "f32" else torch.float64, device=device)
+        step = lambda: fn(t, t, eps2, acc_out=out)
+        pairs = float(n) * n
+    elif args.only == "adjoint":
+        p = synth.plummer(n, n)
+        eps2 = float(np.float32(0.01) ** 2)
+        w = torch.from_numpy(synth.adjoint_weights(n, n + 1)).to(device)
+        t = torch.from_numpy(p).to(device)
+        if tune:
+            cn.cn_tune_set("adjoint", n, n, tune)
+        step = lambda: cn.cn_force_adjoint(t, eps2, w)
+        pairs = float(n) * n
+    else:  # batched ensemble of 512 Plummer clusters
+        rec, offs, eps2s = synth.ensemble(512, 512)
+        t = torch.from_numpy(rec).to(device)
+        plan = cn.BatchPlan(offs, eps2s, tune=dict(tune, chunk_units=args.chunk) if tune else None)
+        acc = torch.empty((rec.shape[0], 3), dtype=torch.float32, device=device)
+        step = lambda: plan.run(t, acc_out=acc)
+        pairs = plan.pairs
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    times = time_steps(torch, step, args.steps, torch.cuda.current_stream(device), None)
+    status = cn.cn_get_device_status()
+    return {"only": args.only, "n": n, "tune": tune, "ms": times, "pairs_per_s": pairs / (statistics.mean(times) / 1e3),
+            "status": status}
+
+
 def run_reference(args):
     """The FP64 oracle on this host, same workload; each step a bounded row sample."""
     rank, world, _ = dist_env()
@@ -414,10 +465,17 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=10.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--ref-rows", type=int, default=256, help="oracle rows per step of --impl reference")
+    ap.add_argument("--only", choices=("f32", "dd", "adjoint", "batched"),
+                    help="time one kernel family alone (profiling mode; prints its own JSON)")
+    ap.add_argument("--tune", help="pinned launch shape for --only: i_per_thread,threads,j_tile,stages")
+    ap.add_argument("--chunk", type=int, default=0, help="dynamic chunk size for --only batched")
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
-    line = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if args.only:
+        line = run_only(args)
+    else:
+        line = run_reference(args) if args.impl == "reference" else run_ours(args)
     if line is not None:
         print(json.dumps(line), flush=True)
     try:

@@ -85,7 +85,7 @@ typedef enum cn_variant {
 typedef struct cn_tune {
     int32_t i_per_thread; /* i-particles held in registers per thread: 1, 2, 4 or 8              */
     int32_t threads;      /* threads per CTA: 64, 128 or 256                                      */
-    int32_t j_tile;       /* j records per shared-memory stage: multiple of 8, 8 .. 4096          */
+    int32_t j_tile;       /* j records per shared-memory stage: multiple of 16, 16 .. 4096        */
     int32_t stages;       /* shared-memory ring depth: 2 .. 8                                     */
     int32_t ctas_per_sm;  /* resident CTAs per SM to launch (0 = occupancy maximum)               */
     int32_t chunk_units;  /* 0 = static schedule (equal share per CTA); > 0 = dynamic queue chunks
@@ -103,7 +103,7 @@ typedef struct cn_tune {
  *   pot_out          : float[n_i] potentials phi_i, or NULL
  * FP32 pair arithmetic with the MUFU inverse square root; each j-tile's
  * FP32 partial is folded into an FP32 running sum (the FORCE-LOOP of
- * Section 2.2.2, Eq. 3); partial sums of i-tiles split across CTAs are
+ * Section 2.2.2, Eq. 2); partial sums of i-tiles split across CTAs are
  * merged in FP64 in a fixed order, so results are bitwise reproducible for
  * a given launch shape.
  */
@@ -131,7 +131,7 @@ CN_API cn_status cn_force_ws(int64_t n_i, const float *pos_i, int64_t n_j, const
  * double-single running sum with Knuth's TwoSum. Partial sums of split
  * i-tiles are merged in FP64 in a fixed order. Per-particle relative error
  * against an exact sum is of order 1e-10 or below (the FP32 form: ~1e-6).
- * The wide accumulators of the GRAPE pipelines (Section 2.1) and the
+ * The wide accumulators of the GRAPE pipelines (Section 1.6) and the
  * FORCE-LOOP error analysis (Section 2.2.2) motivate the form.
  */
 CN_API cn_status cn_force_dd(int64_t n_i, const float *pos_i, int64_t n_j, const float *pos_mass_j, float eps2,
@@ -178,7 +178,7 @@ CN_API cn_status cn_force_noalloc(int64_t n_i, const float *pos_i, int64_t n_j, 
  * eps2[c]; every cluster is its own i set and j set. A plan holds the
  * (cluster, i-tile, j-tile) unit table in device memory; it is built once
  * per ensemble shape on the current device. This is the many-small-systems
- * use of Section 4.3 (groups of particles sharing one interaction list in
+ * use of Section 4.4 (groups of particles sharing one interaction list in
  * the modified tree algorithm) in a single persistent launch. */
 typedef struct cn_batch_plan cn_batch_plan;
 

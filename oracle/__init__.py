@@ -172,7 +172,7 @@ def fp32_study(pos_i, pos_mass_j, eps2, mode: int, n_jb: int = 512, rows=None) -
 
 
 def rel_errors(a_test, a_ref) -> np.ndarray:
-    """Per-particle |a_test - a_ref| / |a_ref| (the quantity maximised in Eq. 4)."""
+    """Per-particle |a_test - a_ref| / |a_ref| (the quantity maximised in Eq. 3)."""
     a_test = np.asarray(a_test, dtype=np.float64)
     a_ref = np.asarray(a_ref, dtype=np.float64)
     num = np.linalg.norm(a_test - a_ref, axis=-1)
@@ -182,6 +182,6 @@ def rel_errors(a_test, a_ref) -> np.ndarray:
 
 
 def e_max(a_test, a_ref) -> float:
-    """E_max of Eq. 4: the largest per-particle relative error."""
+    """E_max of Eq. 3: the largest per-particle relative error."""
     e = rel_errors(a_test, a_ref)
     return float(e.max()) if e.size else 0.0

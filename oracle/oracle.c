@@ -236,10 +236,10 @@ double oracle_loss_k(int64_t n, const float *pos_mass, float eps2_f, const float
  * by the mass times the cubed inverse distance. The three modes differ
  * only in how the FP32 terms are summed:
  * mode 0: DIRECT style - one FP32 running sum over all j in order
- *         (Section 3.4, the second column of the cumulative-error table).
+ *         (Section 3.4, the DIRECT column of Table 2).
  * mode 1: FORCE-LOOP - an FP32 "current" sum over each J-BAG of n_jb
  *         j-particles, added into an FP32 "backup" sum after each bag
- *         (Section 2.2.2, Eq. 3).
+ *         (Section 2.2.2, Eq. 2).
  * mode 2: the same FP32 pair terms summed exactly (FP64 Neumaier), which
  *         isolates the rounding of the pair arithmetic itself.
  * This file is compiled with -ffp-contract=off, so no multiply-add is fused.

@@ -1,7 +1,7 @@
 // Host side of the libcunbody C ABI (include/cunbody.h): argument checks,
 // launch-shape selection, workspaces, dispatch to the kernels, batched
 // plans, host-memory forms, tuning and status.
-#include "../../include/cunbody.h"
+#include "cunbody.h"
 #include "cn_kernels.h"
 
 #include <algorithm>
@@ -237,8 +237,8 @@ cn_status check_tune(int variant, const cn_tune& t) {
     return fail(CN_ERR_INVALID_ARG, "i_per_thread must be 1, 2, 4 or 8 (compensated and adjoint forms: 1, 2, 4)");
   if (t.threads && t.threads != 64 && t.threads != 128 && t.threads != 256)
     return fail(CN_ERR_INVALID_ARG, "threads must be 64, 128 or 256");
-  if (t.j_tile && (t.j_tile < 8 || t.j_tile > 4096 || t.j_tile % 8))
-    return fail(CN_ERR_INVALID_ARG, "j_tile must be a multiple of 8 in 8..4096");
+  if (t.j_tile && (t.j_tile < 16 || t.j_tile > 4096 || t.j_tile % 16))
+    return fail(CN_ERR_INVALID_ARG, "j_tile must be a multiple of 16 in 16..4096");
   if (t.stages && (t.stages < 2 || t.stages > 8)) return fail(CN_ERR_INVALID_ARG, "stages must be 2..8");
   if (t.ctas_per_sm < 0 || t.chunk_units < 0) return fail(CN_ERR_INVALID_ARG, "negative tuning field");
   return CN_OK;

@@ -62,7 +62,7 @@ struct PairArgs {
 struct Plan {
   int k = 4;              // i-particles per thread
   int threads = 128;      // threads per CTA (64, 128 or 256)
-  int j_tile = 512;       // j records per shared-memory stage (multiple of 8)
+  int j_tile = 512;       // j records per shared-memory stage (multiple of 16)
   int stages = 4;         // ring depth
   int ctas_per_sm = 0;    // 0: occupancy maximum
   int64_t chunk_units = 0;  // 0: static schedule

@@ -7,7 +7,7 @@
 // CTAs, their arrival counters and the queue words) from a fixed-size
 // array that is part of the library's device image, so it allocates
 // nothing. The paper has no counterpart.
-#include "../../include/cunbody.h"
+#include "cunbody.h"
 #include "cn_kernels.h"
 
 #include <map>

@@ -3,7 +3,7 @@
 // shared-memory stages by bulk copies (the J-BAG / J-PACKING of Section
 // 2.2), several i-particles held in registers per thread (the I-POT), and a
 // two-level accumulation in which each j-tile's partial sum is folded into
-// a running sum (the FORCE-LOOP of Section 2.2.2, Eq. 3).
+// a running sum (the FORCE-LOOP of Section 2.2.2, Eq. 2).
 //
 // Work decomposition: the i set is cut into i-tiles of threads x K
 // particles and the j set of each i-tile's system into j-tiles of j_tile
@@ -157,10 +157,12 @@ struct F32Policy {
     for (int k = 0; k < K; ++k)
 #pragma unroll
       for (int c = 0; c < NC; ++c) part[k][c] = 0.f;
+    // 16 j records per loop trip (j_tile is a multiple of 16): enough
+    // independent pair terms in flight to cover the MUFU and FMA latencies.
 #pragma unroll 1
-    for (int j = 0; j < T; j += 8) {
+    for (int j = 0; j < T; j += 16) {
 #pragma unroll
-      for (int jj = 0; jj < 8; ++jj) pair_f32<K, POT, GUARD>(js[j + jj], xi, eps2, part);
+      for (int jj = 0; jj < 16; ++jj) pair_f32<K, POT, GUARD>(js[j + jj], xi, eps2, part);
     }
 #pragma unroll
     for (int k = 0; k < K; ++k)
@@ -481,8 +483,10 @@ struct AdjointPolicy {
 };
 
 // ------------------------------------------------------------------ kernel
+// Register budget: with K <= 4 two 256-thread CTAs must fit on an SM (up to
+// 128 registers per thread); K = 8 may use up to 255.
 template <class Policy, int K, bool BATCHED>
-__global__ void __launch_bounds__(256) pair_kernel(const __grid_constant__ PairArgs a) {
+__global__ void __launch_bounds__(256, (K >= 8 ? 1 : 2)) pair_kernel(const __grid_constant__ PairArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int NT = blockDim.x;
   const int tid = threadIdx.x;

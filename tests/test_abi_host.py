@@ -125,6 +125,8 @@ def test_batch_plan_validation(lib):
     assert lib.cn_tune_set(0, 1024, 1024, ctypes.byref(t)) == 1
     t = cn_tune(4, 128, 100, 4, 0, 0)
     assert lib.cn_tune_set(0, 1024, 1024, ctypes.byref(t)) == 1
+    t = cn_tune(4, 128, 8, 4, 0, 0)  # below the 16-record minimum
+    assert lib.cn_tune_set(0, 1024, 1024, ctypes.byref(t)) == 1
 
 
 def test_host_f64_form_validation(lib):

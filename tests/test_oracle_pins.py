@@ -286,7 +286,7 @@ def test_adjoint_rows_subset():
 def test_cumulative_error_trend_matches_table(n):
     """FP32 DIRECT vs FORCE-LOOP errors land in the paper's decade (Table 2).
 
-    The paper does not state its softening; the test program of Section 3.2
+    The paper does not state its softening; the test program of Section 3.1
     uses eps2 = 0.01, taken here. Inputs, hardware rounding and the sampled
     sphere differ, so the check is a factor-of-3 band, plus the ordering
     DIRECT > FORCE-LOOP > exact sum of FP32 terms.
