@@ -64,6 +64,9 @@ def _load():
         lib.oracle_fp32_study.argtypes = [ctypes.c_int64, _i64p, _f32p, ctypes.c_int64, _f32p,
                                           ctypes.c_float, ctypes.c_int, ctypes.c_int64, _f64p]
         lib.oracle_fp32_study.restype = None
+        lib.oracle_force_jerk_rows.argtypes = [ctypes.c_int64, _i64p, _f32p, _f32p, ctypes.c_int64, _f32p, _f32p,
+                                               ctypes.c_float, _f64p, _f64p, _f64p]
+        lib.oracle_force_jerk_rows.restype = None
         lib.oracle_max_threads.argtypes = []
         lib.oracle_max_threads.restype = ctypes.c_int
         lib.oracle_set_threads.argtypes = [ctypes.c_int]
@@ -111,6 +114,30 @@ def force(pos_i, pos_mass_j, eps2, rows=None, potential: bool = True):
     lib.oracle_force_rows(n_rows, _ptr(rp, _i64p), _ptr(pi, _f32p), pj.shape[0], _ptr(pj, _f32p),
                           float(np.float32(eps2)), _ptr(acc, _f64p), _ptr(pot, _f64p))
     return acc, pot
+
+
+def force_jerk(pos_i, vel_i, pos_mass_j, vel_j, eps2, rows=None, potential: bool = True):
+    """Acceleration, jerk (d a / dt along straight-line motion) and potential in FP64.
+
+    Returns ``(acc[n_rows, 3], jerk[n_rows, 3], pot[n_rows] or None)``.
+    """
+    lib = _load()
+    pi, vi = _rec(pos_i), _rec(vel_i)
+    pj, vj = _rec(pos_mass_j), _rec(vel_j)
+    if vi.shape[0] != pi.shape[0] or vj.shape[0] != pj.shape[0]:
+        raise ValueError("velocity records must match the position records")
+    if rows is None:
+        n_rows, rp = pi.shape[0], None
+    else:
+        rows = np.ascontiguousarray(rows, dtype=np.int64)
+        n_rows, rp = rows.shape[0], rows
+    acc = np.zeros((n_rows, 3), dtype=np.float64)
+    jerk = np.zeros((n_rows, 3), dtype=np.float64)
+    pot = np.zeros(n_rows, dtype=np.float64) if potential else None
+    lib.oracle_force_jerk_rows(n_rows, _ptr(rp, _i64p), _ptr(pi, _f32p), _ptr(vi, _f32p), pj.shape[0],
+                               _ptr(pj, _f32p), _ptr(vj, _f32p), float(np.float32(eps2)), _ptr(acc, _f64p),
+                               _ptr(jerk, _f64p), _ptr(pot, _f64p))
+    return acc, jerk, pot
 
 
 def potential_energy(pos_mass, pot) -> float:

@@ -123,6 +123,64 @@ void oracle_force_rows(int64_t n_rows, const int64_t *rows, const float *pos_i,
     }
 }
 
+/*
+ * Acceleration, its time derivative (jerk) and the potential - the outputs
+ * of the force-jerk-potential pipeline description of the appendix - for
+ * particles moving with velocities v:
+ *   a_i   =  sum_j m_j d / s^(3/2)
+ *   j_i   =  sum_j m_j [ w / s^(3/2) - 3 (d . w) d / s^(5/2) ]
+ *   phi_i = -sum_{j : d != 0} m_j / s^(1/2)
+ * with d = x_j - x_i, w = v_j - v_i, s = |d|^2 + eps2 (j_i is d a_i / dt
+ * for straight-line motion). vel_i, vel_j are FP32 [*, 4] records (the 4th
+ * component is ignored). Pairs with s = 0 are skipped.
+ */
+void oracle_force_jerk_rows(int64_t n_rows, const int64_t *rows, const float *pos_i, const float *vel_i,
+                            int64_t n_j, const float *pos_mass_j, const float *vel_j, float eps2_f,
+                            double *acc, double *jerk, double *pot)
+{
+    const double eps2 = (double)eps2_f;
+    int64_t r;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (r = 0; r < n_rows; ++r) {
+        const int64_t i = rows ? rows[r] : r;
+        const double xi = pos_i[4 * i + 0], yi = pos_i[4 * i + 1], zi = pos_i[4 * i + 2];
+        const double ui = vel_i[4 * i + 0], vi = vel_i[4 * i + 1], wi = vel_i[4 * i + 2];
+        nsum ax = {0, 0}, ay = {0, 0}, az = {0, 0};
+        nsum jx = {0, 0}, jy = {0, 0}, jz = {0, 0}, ph = {0, 0};
+        for (int64_t j = 0; j < n_j; ++j) {
+            const double dx = (double)pos_mass_j[4 * j + 0] - xi;
+            const double dy = (double)pos_mass_j[4 * j + 1] - yi;
+            const double dz = (double)pos_mass_j[4 * j + 2] - zi;
+            const double wx = (double)vel_j[4 * j + 0] - ui;
+            const double wy = (double)vel_j[4 * j + 1] - vi;
+            const double wz = (double)vel_j[4 * j + 2] - wi;
+            const double mj = pos_mass_j[4 * j + 3];
+            const double s = dx * dx + dy * dy + dz * dz + eps2;
+            if (s == 0.0)
+                continue;
+            const double root = sqrt(s);
+            const double g = mj / (s * root);           /* m / s^(3/2) */
+            const double h = 3.0 * (dx * wx + dy * wy + dz * wz) / s;
+            nsum_add(&ax, g * dx);
+            nsum_add(&ay, g * dy);
+            nsum_add(&az, g * dz);
+            nsum_add(&jx, g * (wx - h * dx));
+            nsum_add(&jy, g * (wy - h * dy));
+            nsum_add(&jz, g * (wz - h * dz));
+            if (pot && !(dx == 0.0 && dy == 0.0 && dz == 0.0))
+                nsum_add(&ph, -mj / root);
+        }
+        acc[3 * r + 0] = nsum_value(&ax);
+        acc[3 * r + 1] = nsum_value(&ay);
+        acc[3 * r + 2] = nsum_value(&az);
+        jerk[3 * r + 0] = nsum_value(&jx);
+        jerk[3 * r + 1] = nsum_value(&jy);
+        jerk[3 * r + 2] = nsum_value(&jz);
+        if (pot)
+            pot[r] = nsum_value(&ph);
+    }
+}
+
 /* Potential energy W = 1/2 sum_i m_i phi_i (FP64, Neumaier, i ascending). */
 double oracle_potential_energy(int64_t n, const float *pos_mass, const double *pot)
 {

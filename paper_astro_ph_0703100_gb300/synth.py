@@ -32,6 +32,7 @@ __all__ = [
     "adjoint_weights",
     "sample_rows",
     "plummer_eps",
+    "plummer_velocities",
 ]
 
 
@@ -149,3 +150,17 @@ def sample_rows(n: int, k: int, seed: int) -> np.ndarray:
     rng = _rng(seed)
     k = min(k, n)
     return np.sort(rng.choice(n, size=k, replace=False)).astype(np.int64)
+
+
+def plummer_velocities(n: int, seed: int, scale: float = 0.5) -> np.ndarray:
+    """Seeded isotropic Gaussian velocities as FP32 ``(n, 4)`` records (v, 0).
+
+    A stand-in with the order of magnitude of a virialised Plummer sphere
+    (sigma ~ 0.5 in units G = M = a = 1); the jerk is defined for any
+    velocities, so no distribution function is sampled.
+    """
+    rng = _rng(seed)
+    v = scale * rng.standard_normal((n, 3))
+    out = np.zeros((n, 4), dtype=np.float32)
+    out[:, :3] = v.astype(np.float32)
+    return out

@@ -301,3 +301,74 @@ def test_cumulative_error_trend_matches_table(n):
     assert t_direct / 3 < e_direct < t_direct * 3
     assert t_loop / 3 < e_loop < t_loop * 3
     assert e_direct > e_loop > e_exact
+
+
+# ---------------------------------------------------------------- force, jerk, potential (appendix pipeline)
+
+def _vel(v):
+    v = np.asarray(v, dtype=np.float32).reshape(-1, 3)
+    out = np.zeros((v.shape[0], 4), dtype=np.float32)
+    out[:, :3] = v
+    return out
+
+
+def test_jerk_two_body_exact():
+    """Partner at d = (3, 4, 0), eps = 0, mass m: with relative velocity
+    (0, 0, 1) the jerk is m (0, 0, 1/125); with (1, 0, 0), d.w = 3 and the
+    jerk is m [(1, 0, 0)/125 - 9 (3, 4, 0)/3125] = m (-0.00064, -0.01152, 0)."""
+    m = 0.5
+    p = rec([[0, 0, 0], [3, 4, 0]], [1.0, m])
+    for w, expect in (([0, 0, 1], [0, 0, m / 125]), ([1, 0, 0], [-0.00064 * m, -0.01152 * m, 0.0])):
+        v = _vel([[0, 0, 0], w])
+        a, j, phi = oracle.force_jerk(p, v, p, v, 0.0)
+        assert a[0] == pytest.approx([m * 3 / 125, m * 4 / 125, 0.0], rel=1e-15, abs=0)
+        assert j[0] == pytest.approx(expect, rel=1e-14, abs=1e-17)
+        assert phi[0] == pytest.approx(-m / 5, rel=1e-15)
+
+
+def test_jerk_is_time_derivative_of_acceleration():
+    """j_i = d a_i / dt for straight-line motion x(t) = x + v t
+    (Richardson-extrapolated central differences of the oracle's own force)."""
+    n = 64
+    p = synth.plummer(n, 12)
+    v = synth.plummer_velocities(n, 13)
+    eps2 = 0.01
+    a, j, _ = oracle.force_jerk(p, v, p, v, eps2)
+    est = []
+    for h in (2.0 ** -10, 2.0 ** -11):
+        pp = p.astype(np.float64).copy()
+        pm = p.astype(np.float64).copy()
+        pp[:, :3] += h * v[:, :3]
+        pm[:, :3] -= h * v[:, :3]
+        # the oracle takes FP32 records: difference quotients in FP64 need the
+        # moved positions exactly, so evaluate the FP64 definition directly
+        def acc64(q):
+            d = q[None, :, :3] - q[:, None, :3]
+            s = (d ** 2).sum(-1) + np.float64(np.float32(eps2))
+            w = q[None, :, 3] / (s * np.sqrt(s))
+            return (w[:, :, None] * d).sum(1)
+        est.append((acc64(pp) - acc64(pm)) / (2 * h))
+    fd = (4 * est[1] - est[0]) / 3
+    assert np.abs(fd - j).max() <= 1e-8 * np.abs(j).max()
+    assert np.abs(acc64(p.astype(np.float64)) - a).max() <= 1e-12 * np.abs(a).max()
+
+
+def test_jerk_invariants():
+    """sum_i m_i j_i = 0 (i set = j set), and a common velocity shift leaves
+    the jerk unchanged (it depends on velocity differences only)."""
+    n = 500
+    p = synth.plummer(n, 31)
+    v = synth.plummer_velocities(n, 32)
+    _, j, _ = oracle.force_jerk(p, v, p, v, 1e-3)
+    m = p[:, 3].astype(np.float64)
+    scale = (m * np.linalg.norm(j, axis=1)).sum()
+    assert np.abs((m[:, None] * j).sum(0)).max() <= 1e-13 * scale
+    v2 = v.copy()
+    v2[:, :3] += np.float32(0.25)
+    exact = np.array_equal(v2[:, :3].astype(np.float64) - 0.25, v[:, :3].astype(np.float64))
+    _, j2, _ = oracle.force_jerk(p, v2, p, v2, 1e-3)
+    assert np.abs(j2 - j).max() <= (1e-14 if exact else 1e-6) * np.abs(j).max()
+    # the acceleration and potential agree with the force-only oracle
+    a0, phi0 = oracle.force(p, p, 1e-3)
+    a1, _, phi1 = oracle.force_jerk(p, v, p, v, 1e-3)
+    assert np.array_equal(a0, a1) and np.array_equal(phi0, phi1)
