@@ -164,6 +164,41 @@ def gpu_selector(torch, device):
         return vis.split(",")[device.index] if vis else str(device.index)
 
 
+# ------------------------------------------------------------------ profile evidence
+
+KERNEL_SOURCES = ("cn_pair.cuh", "cn_device.cuh", "cn_kernels.h", "cn_force_f32.cu")
+PROFILE_F32 = os.path.join(ROOT, "profiles", "pair_f32_n131072.md")
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_astro_ph_0703100_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def profiled_traffic(shape: dict):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the kernel as it is now and in this launch shape; else None."""
+    try:
+        kv = {}
+        with open(PROFILE_F32) as f:
+            for line in f:
+                if ":" in line and line.startswith("- `"):
+                    k, v = line[3:].split("`", 1)[0].split(":", 1)
+                    kv[k.strip()] = v.strip()
+        same_shape = kv.get("launch_shape") == "{},{},{},{}".format(
+            shape["i_per_thread"], shape["threads"], shape["j_tile"], shape["stages"])
+        if kv.get("source_sha256") == kernel_source_hash() and same_shape:
+            return float(kv["dram_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        pass
+    return None
+
+
 # ------------------------------------------------------------------ workload
 
 def workload(n: int, seed: int):
@@ -242,12 +277,10 @@ def run_ours(args):
     acc = torch.empty((n, 3), dtype=torch.float32, device=device)
     acc_dd = torch.empty((n, 3), dtype=torch.float64, device=device)
 
-    tuned = None
-    if not args.no_autotune:
+    tuned = tuned_dd = None
+    if args.autotune:
         tuned = cn.cn_autotune("f32", t, t, eps2, reps=2)
         tuned_dd = cn.cn_autotune("dd", t, t, eps2, reps=1)
-    else:
-        tuned_dd = None
     f32_step = lambda: cn.cn_force(t, t, eps2, acc_out=acc)
     dd_step = lambda: cn.cn_force_dd(t, t, eps2, acc_out=acc_dd)
     for _ in range(args.warmup):
@@ -327,7 +360,7 @@ def run_ours(args):
             "peak": peak / 1e9,
             "unit": "Gpair/s",
             "frac": achieved / peak,
-            "traffic": None,
+            "traffic": profiled_traffic(tuned or cn.cn_tune_get("f32", n, n)),
             "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {SM_MAX_MHZ:.0f} MHz / "
                           f"{ISSUE_PER_PAIR} issue slots per pair (12 FP32 + 1 MUFU)",
             "frac_at_observed_clock": achieved / (peak * obs_mhz / SM_MAX_MHZ),
@@ -356,7 +389,216 @@ def run_ours(args):
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p, eps2, {"f32": acc.cpu().numpy(), "dd": acc_dd.cpu().numpy()},
                                             args.cpu_budget)
+    if not args.no_rows:
+        line["rows"] = measure_rows(args, cn, torch, device, peak)
     return line
+
+
+ADJOINT_ISSUE_PER_PAIR = 31  # 30 FP32 + 1 MUFU (adjoint pair, see the kernel notes)
+DD_ISSUE_PER_PAIR = 104      # double-single pair term + per-term TwoSum (FP32 instructions)
+JERK_ISSUE_PER_PAIR = 31     # 27 FP32 + 1 MUFU + 3 for the potential (force-jerk-potential pair)
+
+
+def _events_ms(torch, fn, reps, stream):
+    t = time_steps(torch, fn, reps, stream, None)
+    return statistics.mean(t)
+
+
+def _graph_us(torch, fn, reps, device):
+    """Device time per call: `reps` calls captured in one CUDA graph, replayed."""
+    s = torch.cuda.Stream(device)
+    with torch.cuda.stream(s):
+        fn(s)  # warm-up on the capture stream (grows its library workspace)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            for _ in range(reps):
+                fn(s)
+        g.replay()
+        torch.cuda.synchronize()
+        ms = _events_ms(torch, g.replay, 5, s)
+    return 1e3 * ms / reps
+
+
+def measure_rows(args, cn, torch, device, peak):
+    """The other workloads of the path, each with its oracle leg (timed on
+    the host cores on a bounded sample, which also gives the errors)."""
+    import oracle
+    from paper_astro_ph_0703100_gb300 import synth
+
+    stream = torch.cuda.current_stream(device)
+    rows = {}
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    lane_rate = sms * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6
+
+    # C1: N = 1024, acceleration + potential, one evaluation (latency-bound size)
+    p = synth.plummer(1024, 1001)
+    eps2 = float(np.float32(1 / 64) ** 2)
+    t = torch.from_numpy(p).to(device)
+    acc, pot = cn.cn_force(t, t, eps2, potential=True)
+    ms = _events_ms(torch, lambda: cn.cn_force(t, t, eps2, acc_out=acc, pot_out=pot), 50, stream)
+    us_dev = _graph_us(torch, lambda st: cn.cn_force(t, t, eps2, acc_out=acc, pot_out=pot, stream=st), 50, device)
+    t0 = time.perf_counter()
+    ref_a, ref_p = oracle.force(p, p, eps2)
+    dt = time.perf_counter() - t0
+    rows["c1_plummer1024_acc_pot"] = {
+        "pairs_per_s": 1024.0 ** 2 / (us_dev / 1e6), "us_per_eval_device": us_dev, "us_per_call_direct": 1e3 * ms,
+        "emax": oracle.e_max(acc.cpu().numpy(), ref_a),
+        "pot_rel_err": float(np.max(np.abs(pot.cpu().numpy() - ref_p) / np.abs(ref_p))),
+        "cpu_baseline": {"value": 1024.0 ** 2 / dt, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+                         "sample": "all 1024 rows"}}
+
+    # C2 small sizes: N = 2048 (all rows checked) and 16384 (4096 rows)
+    for n, n_rows in ((2048, 2048), (16384, 4096)):
+        p = synth.plummer(n, n)
+        eps2 = float(np.float32(synth.plummer_eps(n)) ** 2)
+        t = torch.from_numpy(p).to(device)
+        cn.cn_autotune("f32", t, t, eps2, reps=20)
+        acc, _ = cn.cn_force(t, t, eps2)
+        ms = _events_ms(torch, lambda: cn.cn_force(t, t, eps2, acc_out=acc), 50, stream)
+        us_dev = _graph_us(torch, lambda st: cn.cn_force(t, t, eps2, acc_out=acc, stream=st), 50, device)
+        r = synth.sample_rows(n, n_rows, seed=n + 1)
+        t0 = time.perf_counter()
+        ref, _ = oracle.force(p, p, eps2, rows=r, potential=False)
+        dt = time.perf_counter() - t0
+        rows[f"c2_plummer{n}"] = {
+            "pairs_per_s": float(n) * n / (us_dev / 1e6), "us_per_eval_device": us_dev,
+            "us_per_call_direct": 1e3 * ms,
+            "frac": float(n) * n / (us_dev / 1e6) / peak, "launch_shape": cn.cn_tune_get("f32", n, n),
+            "emax": oracle.e_max(acc.cpu().numpy()[r], ref),
+            "cpu_baseline": {"value": r.size * n / dt, "unit": UNIT, "cores": oracle.max_threads(),
+                             "kind": "oracle", "sample": f"{r.size} of {n} rows"}}
+
+    # C3: N = 2^20 Hernquist, log-normal masses, eps = 1e-3: compensated vs plain
+    n = 1 << 20
+    h = synth.hernquist(n, 1048576)
+    eps2 = float(np.float32(1e-3) ** 2)
+    t = torch.from_numpy(h).to(device)
+    a32 = torch.empty((n, 3), dtype=torch.float32, device=device)
+    add = torch.empty((n, 3), dtype=torch.float64, device=device)
+    cn.cn_force(t, t, eps2, acc_out=a32)
+    cn.cn_force_dd(t, t, eps2, acc_out=add)
+    ms32 = _events_ms(torch, lambda: cn.cn_force(t, t, eps2, acc_out=a32), 3, stream)
+    msdd = _events_ms(torch, lambda: cn.cn_force_dd(t, t, eps2, acc_out=add), 2, stream)
+    r = synth.sample_rows(n, 8192, seed=8192)
+    t0 = time.perf_counter()
+    ref, _ = oracle.force(h, h, eps2, rows=r, potential=False)
+    dt = time.perf_counter() - t0
+    e32 = oracle.rel_errors(a32.cpu().numpy()[r], ref)
+    edd = oracle.rel_errors(add.cpu().numpy()[r], ref)
+    pairs = float(n) * n
+    rows["c3_hernquist_2p20"] = {
+        "f32": {"pairs_per_s": pairs / (ms32 / 1e3), "frac": pairs / (ms32 / 1e3) / peak,
+                "emax": float(e32.max()), "p99": float(np.percentile(e32, 99)), "median": float(np.median(e32))},
+        "compensated": {"pairs_per_s": pairs / (msdd / 1e3),
+                        "frac_of_own_roofline": pairs / (msdd / 1e3) / (lane_rate / DD_ISSUE_PER_PAIR),
+                        "emax": float(edd.max()), "p99": float(np.percentile(edd, 99)),
+                        "median": float(np.median(edd))},
+        "cpu_baseline": {"value": r.size * n / dt, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+                         "sample": f"8192 seeded rows of {n}"}}
+    del t, a32, add
+
+    # C4: 512 clusters in one persistent launch (graph-captured) vs per-cluster launches
+    rec, offs, eps2s = synth.ensemble(512, 512)
+    t = torch.from_numpy(rec).to(device)
+    tuned = cn.cn_autotune_batched(offs, eps2s, t, reps=2)
+    plan = cn.BatchPlan(offs, eps2s)
+    side = torch.cuda.Stream(device)
+    acc_b = torch.empty((rec.shape[0], 3), dtype=torch.float32, device=device)
+    with torch.cuda.stream(side):
+        ws = plan.new_workspace(device)
+        plan.capture(t, acc_b, workspace=ws, stream=side)
+        for _ in range(3):
+            plan.launch(side)
+        ms_graph = _events_ms(torch, lambda: plan.launch(side), 20, side)
+        ms_direct = _events_ms(torch, lambda: plan.run(t, acc_out=acc_b, workspace=ws, stream=side), 20, side)
+        sep = torch.empty_like(acc_b)
+        sl = [(int(offs[c]), int(offs[c + 1]), float(eps2s[c])) for c in range(512)]
+
+        def separate():
+            for lo, hi, e in sl:
+                cn.cn_force(t[lo:hi], t[lo:hi], e, acc_out=sep[lo:hi], stream=side)
+        separate()
+        ms_sep = _events_ms(torch, separate, 5, side)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=side):
+            separate()
+        g.replay()
+        ms_sep_graph = _events_ms(torch, g.replay, 10, side)
+    torch.cuda.synchronize()
+    useful = plan.pairs
+    rng = np.random.default_rng(512)
+    errs, n_rows, t_or = [], 0, 0.0
+    a_host = acc_b.cpu().numpy()
+    for c in range(0, 512, 4):
+        lo, hi = int(offs[c]), int(offs[c + 1])
+        rr = np.sort(rng.choice(hi - lo, size=min(64, hi - lo), replace=False))
+        t0 = time.perf_counter()
+        ref, _ = oracle.force(rec[lo:hi], rec[lo:hi], eps2s[c], rows=rr, potential=False)
+        t_or += time.perf_counter() - t0
+        n_rows += rr.size * (hi - lo)
+        errs.append(oracle.e_max(a_host[lo:hi][rr], ref))
+    rows["c4_ensemble512"] = {
+        "useful_pairs": useful,
+        "persistent_graph": {"pairs_per_s": useful / (ms_graph / 1e3), "ms": ms_graph,
+                             "frac": useful / (ms_graph / 1e3) / peak},
+        "persistent_direct": {"pairs_per_s": useful / (ms_direct / 1e3), "ms": ms_direct},
+        "separate_launches": {"pairs_per_s": useful / (ms_sep / 1e3), "ms": ms_sep},
+        "graph_of_separate_launches": {"pairs_per_s": useful / (ms_sep_graph / 1e3), "ms": ms_sep_graph},
+        "launch_shape": tuned,
+        "emax": max(errs),
+        "cpu_baseline": {"value": n_rows / t_or, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+                         "sample": "64 seeded rows of every 4th cluster"}}
+    plan.close()
+    del t
+
+    # Force + jerk + potential (the appendix's Hermite pipeline), N = 131072,
+    # i set = j set, the appendix's eps2 = 1/256^2
+    n = 131072
+    p = synth.plummer(n, 131072)
+    v = synth.plummer_velocities(n, 131073)
+    eps2 = float(np.float32(1.0 / 256.0) ** 2)
+    tp = torch.from_numpy(p).to(device)
+    tv = torch.from_numpy(v).to(device)
+    a_h, j_h, p_h = cn.cn_force_jerk(tp, tv, tp, tv, eps2, potential=True)
+    ms = _events_ms(torch, lambda: cn.cn_force_jerk(tp, tv, tp, tv, eps2, acc_out=a_h, jerk_out=j_h, pot_out=p_h),
+                    5, stream)
+    r = synth.sample_rows(n, 512, seed=11)
+    t0 = time.perf_counter()
+    ra, rj, rp = oracle.force_jerk(p, v, p, v, eps2, rows=r)
+    dt = time.perf_counter() - t0
+    rows["hermite_jerk131072"] = {
+        "pairs_per_s": float(n) * n / (ms / 1e3), "ms": ms,
+        "frac": float(n) * n / (ms / 1e3) / (lane_rate / JERK_ISSUE_PER_PAIR),
+        "roofline_pairs_per_s": lane_rate / JERK_ISSUE_PER_PAIR,
+        "emax_acc": oracle.e_max(a_h.cpu().numpy()[r], ra), "emax_jerk": oracle.e_max(j_h.cpu().numpy()[r], rj),
+        "cpu_baseline": {"value": r.size * n / dt, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+                         "sample": "512 seeded rows"}}
+    del tp, tv, a_h, j_h, p_h
+
+    # C5: adjoint at N = 65536, eps = 0.01
+    n = 65536
+    p = synth.plummer(n, 65536)
+    w_np = synth.adjoint_weights(n, 65537)
+    eps2 = float(np.float32(0.01) ** 2)
+    t = torch.from_numpy(p).to(device)
+    w = torch.from_numpy(w_np).to(device)
+    gp, gm = cn.cn_force_adjoint(t, eps2, w)
+    ms = _events_ms(torch, lambda: cn.cn_force_adjoint(t, eps2, w, grad_pos=gp, grad_mass=gm), 10, stream)
+    r = synth.sample_rows(n, 1024, seed=3)
+    t0 = time.perf_counter()
+    rp, rm = oracle.adjoint(p, eps2, w_np, rows=r)
+    dt = time.perf_counter() - t0
+    gph, gmh = gp.cpu().numpy().astype(np.float64), gm.cpu().numpy().astype(np.float64)
+    rows["c5_adjoint65536"] = {
+        "pairs_per_s": float(n) * n / (ms / 1e3), "ms": ms,
+        "frac": float(n) * n / (ms / 1e3) / (lane_rate / ADJOINT_ISSUE_PER_PAIR),
+        "roofline_pairs_per_s": lane_rate / ADJOINT_ISSUE_PER_PAIR,
+        "emax_grad_pos": oracle.e_max(gph[r], rp),
+        "max_rel_grad_mass": float(np.max(np.abs(gmh[r] - rm)) / np.max(np.abs(rm))),
+        "cpu_baseline": {"value": r.size * n / dt, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+                         "sample": "1024 seeded rows of the analytic FP64 gradient"}}
+    return rows
 
 
 def run_only(args):
@@ -461,8 +703,9 @@ def main(argv=None):
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--dd-steps", type=int, default=20)
-    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--autotune", action="store_true", help="autotune the headline launch shapes first")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-rows", action="store_true", help="skip the other workloads (C1, C2 small, C3, C4, C5)")
     ap.add_argument("--cpu-budget", type=float, default=10.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--ref-rows", type=int, default=256, help="oracle rows per step of --impl reference")
     ap.add_argument("--only", choices=("f32", "dd", "adjoint", "batched"),

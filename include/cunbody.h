@@ -78,7 +78,9 @@ typedef enum cn_variant {
     CN_VARIANT_DD_POT = 3,     /* cn_force_dd with potential      */
     CN_VARIANT_ADJOINT = 4,    /* cn_force_adjoint                */
     CN_VARIANT_BATCHED = 5,    /* cn_force_batched                */
-    CN_VARIANT_BATCHED_POT = 6 /* cn_force_batched with potential */
+    CN_VARIANT_BATCHED_POT = 6, /* cn_force_batched with potential */
+    CN_VARIANT_JERK = 7,        /* cn_force_jerk without potential */
+    CN_VARIANT_JERK_POT = 8     /* cn_force_jerk with potential    */
 } cn_variant;
 
 /* Launch shape of the pair kernels. Zero in a field means "library default". */
@@ -86,10 +88,13 @@ typedef struct cn_tune {
     int32_t i_per_thread; /* i-particles held in registers per thread: 1, 2, 4 or 8              */
     int32_t threads;      /* threads per CTA: 64, 128 or 256                                      */
     int32_t j_tile;       /* j records per shared-memory stage: multiple of 16, 16 .. 4096        */
-    int32_t stages;       /* shared-memory ring depth: 2 .. 8                                     */
+    int32_t stages;       /* shared-memory ring depth: 1 .. 8 (1: one tile in flight at a time)   */
     int32_t ctas_per_sm;  /* resident CTAs per SM to launch (0 = occupancy maximum)               */
     int32_t chunk_units;  /* 0 = static schedule (equal share per CTA); > 0 = dynamic queue chunks
                              of this many (i-tile x j-tile) units                                 */
+    int32_t j_lanes;      /* plain FP32 single-system form only: lanes sharing one i-particle
+                             (1, 2, 4, ..., 32; needs i_per_thread = 1 and j_tile a multiple of
+                             8 x j_lanes); their partial sums are combined by warp shuffles       */
 } cn_tune;
 
 /* ------------------------------------------------------------------ force */
@@ -112,10 +117,11 @@ CN_API cn_status cn_force(int64_t n_i, const float *pos_i, int64_t n_j, const fl
 
 /* cn_force with a caller-owned workspace of ws_bytes >= cn_workspace_bytes(
  * pot_out ? CN_VARIANT_F32_POT : CN_VARIANT_F32, n_i, n_j), 256-byte
- * aligned. Its first 4 KiB must be zero before the first use (every call
- * leaves them zero); the rest needs no initialisation and may hold anything
- * between calls. No allocation happens inside this call. Calls sharing a
- * workspace must not overlap in time on the device. */
+ * aligned. It needs no initialisation: each call clears the workspace's
+ * control head (queue words and split-tile arrival counters) with one
+ * cudaMemsetAsync on `stream` before the kernel. No allocation happens
+ * inside this call. Calls sharing a workspace must not overlap in time on
+ * the device. */
 CN_API cn_status cn_force_ws(int64_t n_i, const float *pos_i, int64_t n_j, const float *pos_mass_j, float eps2,
                       float *acc_out, float *pot_out, void *workspace, size_t ws_bytes, cn_stream stream);
 
@@ -200,9 +206,9 @@ CN_API cn_status cn_batch_plan_info(const cn_batch_plan *plan, int64_t *n_total,
  *   pos_mass  : float[n_total][4] records of all clusters
  *   acc_out   : float[n_total][3]; pot_out : float[n_total] or NULL
  *   workspace : caller-owned, >= cn_batch_plan_workspace_bytes(plan) bytes,
- *               256-byte aligned, its first 4 KiB zero before first use
- *               (every call leaves them zero); NULL to use the library
- *               workspace of `stream`.
+ *               256-byte aligned, no initialisation needed (its control
+ *               head is cleared on `stream` before the kernel); NULL to use
+ *               the library workspace of `stream`.
  * No allocation happens when a workspace is passed, so the call can be
  * captured into a CUDA graph (see cn_batch_plan_capture).
  */
@@ -230,6 +236,28 @@ CN_API cn_status cn_batch_plan_launch(const cn_batch_plan *plan, cn_stream strea
  */
 CN_API cn_status cn_force_adjoint(int64_t n, const float *pos_mass, float eps2, const float *w, float *grad_pos,
                            float *grad_mass, cn_stream stream);
+
+/* ------------------------------------------------------------------ force, jerk, potential */
+
+/*
+ * The outputs of the force-jerk-potential pipeline description of the
+ * appendix (what a Hermite integrator needs each step): for i-particles with
+ * positions x_i and velocities v_i and j-particles (x_j, m_j, v_j),
+ *   a_i   =  sum_j m_j d / s^(3/2)
+ *   j_i   =  sum_j m_j [ w / s^(3/2) - 3 (d . w) d / s^(5/2) ]   (= d a_i / dt)
+ *   phi_i = -sum_{j : d != 0} m_j / s^(1/2)
+ * with d = x_j - x_i, w = v_j - v_i, s = |d|^2 + eps2.
+ *   pos_i, vel_i        : float[n_i][4] (4th components ignored)
+ *   pos_mass_j, vel_j   : float[n_j][4] ((x, y, z, m) and (vx, vy, vz, -))
+ *   acc_out, jerk_out   : float[n_i][3]; pot_out : float[n_i] or NULL
+ * All four record arrays 16-byte aligned. FP32 pair arithmetic (27 FP32
+ * instructions and one MUFU inverse square root per pair), per-tile FP32
+ * partials folded into running sums, FP64 merge of split tiles. The
+ * appendix hard-wires eps2 = 1/256^2; here it is an argument.
+ */
+CN_API cn_status cn_force_jerk(int64_t n_i, const float *pos_i, const float *vel_i, int64_t n_j,
+                               const float *pos_mass_j, const float *vel_j, float eps2, float *acc_out,
+                               float *jerk_out, float *pot_out, cn_stream stream);
 
 /* ------------------------------------------------------------------ potential energy */
 

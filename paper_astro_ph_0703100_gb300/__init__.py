@@ -30,6 +30,7 @@ __all__ = [
     "BatchPlan",
     "cn_force_batched",
     "cn_force_adjoint",
+    "cn_force_jerk",
     "cn_potential_energy",
     "cn_potential_energy_dd",
     "cn_force_host",
@@ -56,6 +57,8 @@ VARIANT = {
     "adjoint": 4,
     "batched": 5,
     "batched_pot": 6,
+    "jerk": 7,
+    "jerk_pot": 8,
 }
 
 
@@ -127,7 +130,7 @@ def cn_force(pos_i, pos_mass_j, eps2, acc_out=None, pot_out=None, potential=Fals
 
 
 def cn_force_ws(pos_i, pos_mass_j, eps2, workspace, acc_out=None, pot_out=None, potential=False, stream=None):
-    """cn_force with a caller-owned workspace tensor (uint8 CUDA, zeroed before first use)."""
+    """cn_force with a caller-owned workspace tensor (uint8 CUDA, no initialisation needed)."""
     return _force("cn_force_ws", False, pos_i, pos_mass_j, eps2, acc_out, pot_out, potential, stream, workspace)
 
 
@@ -240,6 +243,26 @@ def cn_force_adjoint(pos_mass, eps2, w, grad_pos=None, grad_mass=None, stream=No
     check(load().cn_force_adjoint(n, _ptr(pos_mass), float(eps2), _ptr(w), _ptr(gp), _ptr(gm),
                                   _stream_handle(stream)), "cn_force_adjoint")
     return gp, gm
+
+
+def cn_force_jerk(pos_i, vel_i, pos_mass_j, vel_j, eps2, acc_out=None, jerk_out=None, pot_out=None,
+                  potential=False, stream=None):
+    """Acceleration, jerk (d a / dt) and optionally potential: the outputs of
+    the appendix's force-jerk-potential pipeline. Velocities are (n, 4) float32."""
+    torch = _torch()
+    for t, name in ((pos_i, "pos_i"), (vel_i, "vel_i"), (pos_mass_j, "pos_mass_j"), (vel_j, "vel_j")):
+        _records(t, name)
+    n_i, n_j = pos_i.shape[0], pos_mass_j.shape[0]
+    if vel_i.shape[0] != n_i or vel_j.shape[0] != n_j:
+        raise ValueError("velocity records must match the position records")
+    acc = _out(acc_out, (n_i, 3), torch.float32, pos_i.device, "acc_out")
+    jerk = _out(jerk_out, (n_i, 3), torch.float32, pos_i.device, "jerk_out")
+    pot = None
+    if potential or pot_out is not None:
+        pot = _out(pot_out, (n_i,), torch.float32, pos_i.device, "pot_out")
+    check(load().cn_force_jerk(n_i, _ptr(pos_i), _ptr(vel_i), n_j, _ptr(pos_mass_j), _ptr(vel_j), float(eps2),
+                               _ptr(acc), _ptr(jerk), _ptr(pot), _stream_handle(stream)), "cn_force_jerk")
+    return acc, jerk, pot
 
 
 def _energy(fn, pos_mass, pot, w_out, stream):

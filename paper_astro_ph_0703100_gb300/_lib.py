@@ -30,6 +30,7 @@ class cn_tune(ctypes.Structure):
         ("stages", c_i32),
         ("ctas_per_sm", c_i32),
         ("chunk_units", c_i32),
+        ("j_lanes", c_i32),
     ]
 
     def as_dict(self):
@@ -52,6 +53,7 @@ SIGNATURES = {
     "cn_batch_plan_capture": (c_int, [vp, vp, vp, vp, vp, c_size, vp]),
     "cn_batch_plan_launch": (c_int, [vp, vp]),
     "cn_force_adjoint": (c_int, [c_i64, vp, c_f32, vp, vp, vp, vp]),
+    "cn_force_jerk": (c_int, [c_i64, vp, vp, c_i64, vp, vp, c_f32, vp, vp, vp, vp]),
     "cn_potential_energy": (c_int, [c_i64, vp, vp, vp, vp]),
     "cn_potential_energy_dd": (c_int, [c_i64, vp, vp, vp, vp]),
     "cn_force_host": (c_int, [c_i64, vp, c_i64, vp, c_f32, vp, vp, vp]),

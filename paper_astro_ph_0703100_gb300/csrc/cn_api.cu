@@ -40,7 +40,8 @@ struct cn_batch_plan {
   int64_t n_chunks = 0;
   int grid = 0;
   size_t ws_bytes = 0;
-  size_t off_partials = 0;
+  size_t ctrl_bytes = 0;
+  size_t data_bytes = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
 };
@@ -53,14 +54,6 @@ constexpr size_t kMaxSmem = 227 * 1024;
 
 thread_local std::string g_last_error;
 std::atomic<uint64_t> g_wait_ns{kDefaultWaitNs};
-std::atomic<uint32_t> g_epoch{1};
-
-// A fresh nonzero launch number for the split-tile arrival counters.
-uint32_t next_epoch() {
-  uint32_t e = g_epoch.fetch_add(1);
-  if (e == 0) e = g_epoch.fetch_add(1);
-  return e;
-}
 
 cn_status fail(cn_status st, const std::string& msg) {
   g_last_error = msg;
@@ -129,9 +122,14 @@ cn_status current_device(int* dev_out, DeviceInfo** info) {
 }
 
 // ------------------------------------------------------------------ library workspaces
+// Per (device, stream): `ctrl` holds the queue words and the split-tile
+// arrival counters (zeroed when allocated, left zero by every kernel); `data`
+// holds partial sums and packed weights (no initialisation needed).
 struct LibWorkspace {
-  void* ptr = nullptr;
-  size_t bytes = 0;
+  void* ctrl = nullptr;
+  size_t ctrl_bytes = 0;
+  void* data = nullptr;
+  size_t data_bytes = 0;
   double* aux = nullptr;  // potential-energy block sums + counter
 };
 std::map<std::pair<int, cudaStream_t>, LibWorkspace> g_ws;
@@ -142,38 +140,58 @@ bool capturing(cudaStream_t s) {
   return cs != cudaStreamCaptureStatusNone;
 }
 
-cn_status library_workspace(cudaStream_t s, size_t need, void** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return fail_cuda(e, "cudaGetDevice");
-  std::lock_guard<std::mutex> lock(g_mu);
-  LibWorkspace& w = g_ws[{dev, s}];
-  if (w.ptr && w.bytes >= need) {
-    *out = w.ptr;
-    return CN_OK;
-  }
+cn_status grow(cudaStream_t s, void** buf, size_t* bytes, size_t need, bool zero, const char* what) {
+  if (*buf && *bytes >= need) return CN_OK;
   if (inject("capture") || capturing(s))
     return fail(CN_ERR_WORKSPACE,
                 "the library workspace of this stream must grow, which allocates; not allowed during graph "
                 "capture (make one call before capturing, or pass a workspace)");
   if (inject("alloc")) return fail(CN_ERR_CUDA, "cudaMalloc: injected allocation failure");
-  if (w.ptr) {
+  cudaError_t e;
+  if (*buf) {
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return fail_cuda(e, "cudaStreamSynchronize");
-    cudaFree(w.ptr);
-    w.ptr = nullptr;
-    w.bytes = 0;
+    cudaFree(*buf);
+    *buf = nullptr;
+    *bytes = 0;
   }
-  const size_t nb = align_up(std::max(need, static_cast<size_t>(1) << 20), static_cast<size_t>(1) << 20);
+  const size_t nb = align_up(std::max(need, static_cast<size_t>(1) << 16), static_cast<size_t>(1) << 16);
   void* p = nullptr;
-  if ((e = cudaMalloc(&p, nb)) != cudaSuccess) return fail_cuda(e, "cudaMalloc(workspace)");
-  if ((e = cudaMemsetAsync(p, 0, nb, s)) != cudaSuccess) {
+  if ((e = cudaMalloc(&p, nb)) != cudaSuccess) return fail_cuda(e, what);
+  if (zero && (e = cudaMemsetAsync(p, 0, nb, s)) != cudaSuccess) {
     cudaFree(p);
     return fail_cuda(e, "cudaMemsetAsync(workspace)");
   }
-  w.ptr = p;
-  w.bytes = nb;
-  *out = p;
+  *buf = p;
+  *bytes = nb;
   return CN_OK;
+}
+
+cn_status library_workspace(cudaStream_t s, size_t ctrl_need, size_t data_need, char** ctrl, char** data) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail_cuda(e, "cudaGetDevice");
+  std::lock_guard<std::mutex> lock(g_mu);
+  LibWorkspace& w = g_ws[{dev, s}];
+  cn_status st = grow(s, &w.ctrl, &w.ctrl_bytes, ctrl_need, true, "cudaMalloc(workspace control)");
+  if (st != CN_OK) return st;
+  if ((st = grow(s, &w.data, &w.data_bytes, std::max<size_t>(data_need, 256), false, "cudaMalloc(workspace)")) != CN_OK)
+    return st;
+  *ctrl = static_cast<char*>(w.ctrl);
+  *data = static_cast<char*>(w.data);
+  return CN_OK;
+}
+
+// Frees the library workspace of a stream that is about to be destroyed.
+void release_library_workspace(cudaStream_t s) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
+  std::lock_guard<std::mutex> lock(g_mu);
+  auto it = g_ws.find({dev, s});
+  if (it == g_ws.end()) return;
+  if (it->second.ctrl) cudaFree(it->second.ctrl);
+  if (it->second.data) cudaFree(it->second.data);
+  if (it->second.aux) cudaFree(it->second.aux);
+  g_ws.erase(it);
 }
 
 cn_status library_aux(cudaStream_t s, double** out) {
@@ -204,25 +222,48 @@ int bucket(int64_t n) {
 }
 
 bool valid_k(int variant, int k) {
-  if (variant == cn::kDD || variant == cn::kDDPot || variant == cn::kAdjoint) return k == 1 || k == 2 || k == 4;
+  if (variant == cn::kDD || variant == cn::kDDPot || variant == cn::kAdjoint || variant == cn::kJerk ||
+      variant == cn::kJerkPot)
+    return k == 1 || k == 2 || k == 4;
   return k == 1 || k == 2 || k == 4 || k == 8;
 }
+
+int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
 cn_tune default_tune(int variant, int64_t n_i, int64_t n_j) {
   cn_tune t{};
   const int64_t n = std::max(n_i, n_j);
   const bool dd = variant == cn::kDD || variant == cn::kDDPot;
-  const bool adj = variant == cn::kAdjoint;
+  // the adjoint and the force-jerk form stream two 16-byte records per j
+  const bool adj = variant == cn::kAdjoint || variant == cn::kJerk || variant == cn::kJerkPot;
+  const bool f32 = variant == cn::kF32 || variant == cn::kF32Pot;
   t.stages = 4;
   t.threads = 128;
+  t.j_lanes = 1;
+  if (f32 && n_i <= 4096) {
+    // small systems (measured at N = 1024 .. 4096): 16 lanes per i-particle
+    // (8 at N = 4096) and, where it fits, the whole j set in one single-stage
+    // tile, so that each CTA covers whole i-tiles and nothing is merged
+    const int jl = n_i <= 2048 ? 16 : 8;
+    t.i_per_thread = 1;
+    t.j_lanes = jl;
+    t.threads = n_i <= 2048 ? 128 : 256;
+    const int64_t unit = 8 * jl;
+    t.j_tile = static_cast<int32_t>(std::min<int64_t>(round_up(std::max<int64_t>(n_j, 1), unit), 4096));
+    t.stages = n_j <= t.j_tile ? 1 : 3;
+    return t;
+  }
   if (variant == cn::kBatched || variant == cn::kBatchedPot) {
     t.i_per_thread = 4;
     t.j_tile = 256;
   } else if (n >= 32768) {
-    t.i_per_thread = adj ? 2 : (dd ? 4 : 8);
-    t.j_tile = 512;
+    // measured optimum at N = 131072: FP32 K = 8 x 128 threads, DD K = 2 x 256 threads;
+    // the adjoint's 32-byte j records keep its stages at 256 records (4 CTAs per SM)
+    t.i_per_thread = adj ? 2 : (dd ? 2 : 8);
+    t.threads = dd ? 256 : 128;
+    t.j_tile = adj ? 256 : 1024;
   } else if (n >= 4096) {
-    t.i_per_thread = adj ? 2 : 4;
+    t.i_per_thread = 2;  // measured at N = 16384: K = 2 x 128 threads x 256 records
     t.j_tile = 256;
   } else {
     t.i_per_thread = adj ? 1 : 2;
@@ -239,9 +280,22 @@ cn_status check_tune(int variant, const cn_tune& t) {
     return fail(CN_ERR_INVALID_ARG, "threads must be 64, 128 or 256");
   if (t.j_tile && (t.j_tile < 16 || t.j_tile > 4096 || t.j_tile % 16))
     return fail(CN_ERR_INVALID_ARG, "j_tile must be a multiple of 16 in 16..4096");
-  if (t.stages && (t.stages < 2 || t.stages > 8)) return fail(CN_ERR_INVALID_ARG, "stages must be 2..8");
+  if (t.stages && (t.stages < 1 || t.stages > 8)) return fail(CN_ERR_INVALID_ARG, "stages must be 1..8");
   if (t.ctas_per_sm < 0 || t.chunk_units < 0) return fail(CN_ERR_INVALID_ARG, "negative tuning field");
+  if (t.j_lanes < 0 || t.j_lanes > 32 || (t.j_lanes & (t.j_lanes - 1)))
+    return fail(CN_ERR_INVALID_ARG, "j_lanes must be 0 or a power of two up to 32");
+  if (t.j_lanes > 1) {
+    if (variant != cn::kF32 && variant != cn::kF32Pot)
+      return fail(CN_ERR_INVALID_ARG, "j_lanes > 1 is offered for the plain FP32 single-system form only");
+    if (t.i_per_thread > 1) return fail(CN_ERR_INVALID_ARG, "j_lanes > 1 needs i_per_thread = 1");
+    if (t.j_tile && t.j_tile % (8 * t.j_lanes))
+      return fail(CN_ERR_INVALID_ARG, "with j_lanes > 1, j_tile must be a multiple of 8 x j_lanes");
+  }
   return CN_OK;
+}
+
+bool two_records(int variant) {
+  return variant == cn::kAdjoint || variant == cn::kJerk || variant == cn::kJerkPot;
 }
 
 cn_status resolve_plan(int dev, int variant, int64_t n_i, int64_t n_j, bool guard, const cn_tune* explicit_tune,
@@ -269,6 +323,7 @@ cn_status resolve_plan(int dev, int variant, int64_t n_i, int64_t n_j, bool guar
     if (chosen.stages) t.stages = chosen.stages;
     t.ctas_per_sm = chosen.ctas_per_sm;
     t.chunk_units = chosen.chunk_units;
+    t.j_lanes = chosen.j_lanes > 1 ? chosen.j_lanes : 1;
   }
   p->k = guard ? 1 : t.i_per_thread;
   p->threads = t.threads;
@@ -276,7 +331,12 @@ cn_status resolve_plan(int dev, int variant, int64_t n_i, int64_t n_j, bool guar
   p->stages = t.stages;
   p->ctas_per_sm = t.ctas_per_sm;
   p->chunk_units = t.chunk_units;
-  const size_t smem = variant == cn::kAdjoint ? cn::adjoint_smem_bytes(*p) : cn::ring_smem_bytes(*p);
+  p->j_lanes = t.j_lanes > 1 ? t.j_lanes : 1;
+  if (p->j_lanes > 1) {
+    p->k = 1;
+    if (p->j_tile % (8 * p->j_lanes)) return fail(CN_ERR_INVALID_ARG, "j_tile must be a multiple of 8 x j_lanes");
+  }
+  const size_t smem = two_records(variant) ? cn::adjoint_smem_bytes(*p) : cn::ring_smem_bytes(*p);
   if (smem > kMaxSmem) return fail(CN_ERR_INVALID_ARG, "j_tile x stages exceeds the shared memory of one CTA");
   return CN_OK;
 }
@@ -289,15 +349,16 @@ struct Geometry {
   int64_t n_chunks = 0;
   int grid = 0;
   size_t smem = 0;
-  size_t off_partials = 0;
-  size_t off_wrec = 0;
-  size_t ws_bytes = 0;
+  size_t ctrl_bytes = 0;  // queue words + arrival counters (must be zero at launch)
+  size_t data_bytes = 0;  // partial sums (+ packed weights)
+  size_t off_wrec = 0;    // packed weights, from the start of the data region
+  size_t ws_bytes = 0;    // one caller buffer: control region, then data region
 };
 
-std::map<std::tuple<int, int, bool, bool, int, int, size_t>, int> g_occ;
+std::map<std::tuple<int, int, bool, int, int, int, size_t>, int> g_occ;
 
 cn_status occupancy(int dev, int variant, bool guard, const Plan& p, size_t smem, int* ctas) {
-  const auto key = std::make_tuple(dev, variant, guard, false, p.k, p.threads, smem);
+  const auto key = std::make_tuple(dev, variant, guard, p.j_lanes, p.k, p.threads, smem);
   {
     std::lock_guard<std::mutex> lock(g_mu);
     auto it = g_occ.find(key);
@@ -316,6 +377,8 @@ cn_status occupancy(int dev, int variant, bool guard, const Plan& p, size_t smem
     case cn::kAdjoint: e = cn::occupancy_adjoint(p, guard, smem, &c); break;
     case cn::kBatched: e = cn::occupancy_f32(p, false, guard, true, smem, &c); break;
     case cn::kBatchedPot: e = cn::occupancy_f32(p, true, guard, true, smem, &c); break;
+    case cn::kJerk: e = cn::occupancy_jerk(p, false, guard, smem, &c); break;
+    case cn::kJerkPot: e = cn::occupancy_jerk(p, true, guard, smem, &c); break;
     default: return fail(CN_ERR_INVALID_ARG, "unknown variant");
   }
   if (e != cudaSuccess) return fail_cuda(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
@@ -326,14 +389,16 @@ cn_status occupancy(int dev, int variant, bool guard, const Plan& p, size_t smem
   return CN_OK;
 }
 
-int slot_f4(int variant) { return (variant == cn::kDD || variant == cn::kDDPot) ? 2 : 1; }
+int slot_f4(int variant) {
+  return (variant == cn::kDD || variant == cn::kDDPot || variant == cn::kJerk || variant == cn::kJerkPot) ? 2 : 1;
+}
 
 // Grid and workspace layout for `units` units over `n_tiles` i-tiles.
 cn_status layout(int dev, const DeviceInfo& d, int variant, bool guard, const Plan& p, int64_t n_tiles,
                  int64_t units, int64_t n_wrec, Geometry* g) {
   g->n_tiles = n_tiles;
   g->units = units;
-  g->smem = variant == cn::kAdjoint ? cn::adjoint_smem_bytes(p) : cn::ring_smem_bytes(p);
+  g->smem = two_records(variant) ? cn::adjoint_smem_bytes(p) : cn::ring_smem_bytes(p);
   int occ = 0;
   cn_status st = occupancy(dev, variant, guard, p, g->smem, &occ);
   if (st != CN_OK) return st;
@@ -348,12 +413,12 @@ cn_status layout(int dev, const DeviceInfo& d, int variant, bool guard, const Pl
   }
   if (g->n_tiles > INT32_MAX || g->n_chunks > INT32_MAX)
     return fail(CN_ERR_INVALID_ARG, "problem too large for one launch");
-  const size_t counters = align_up(kCtrlBytes + static_cast<size_t>(n_tiles) * 8, 256);
-  g->off_partials = counters;
+  g->ctrl_bytes = align_up(kCtrlBytes + static_cast<size_t>(n_tiles) * 4, 256);
   const size_t partial_bytes =
       static_cast<size_t>(g->n_chunks) * 2 * static_cast<size_t>(p.i_tile()) * 16 * slot_f4(variant);
-  g->off_wrec = align_up(g->off_partials + partial_bytes, 256);
-  g->ws_bytes = g->off_wrec + static_cast<size_t>(n_wrec) * 16;
+  g->off_wrec = align_up(partial_bytes, 256);
+  g->data_bytes = g->off_wrec + static_cast<size_t>(n_wrec) * 16;
+  g->ws_bytes = g->ctrl_bytes + g->data_bytes;
   return CN_OK;
 }
 
@@ -366,12 +431,11 @@ cn_status single_geometry(int dev, const DeviceInfo& d, int variant, bool guard,
   return layout(dev, d, variant, guard, p, n_tiles, n_tiles * njt, variant == cn::kAdjoint ? n_i : 0, g);
 }
 
-PairArgs base_args(void* ws, const Geometry& g, const Plan& p, int* status) {
+PairArgs base_args(char* ctrl, char* data, const Geometry& g, const Plan& p, int* status) {
   PairArgs a{};
-  char* base = static_cast<char*>(ws);
-  a.queue = reinterpret_cast<int*>(base);
-  a.counters = reinterpret_cast<unsigned long long*>(base + kCtrlBytes);
-  a.partials = reinterpret_cast<float4*>(base + g.off_partials);
+  a.queue = reinterpret_cast<int*>(ctrl);
+  a.counters = reinterpret_cast<unsigned int*>(ctrl + kCtrlBytes);
+  a.partials = reinterpret_cast<float4*>(data);
   a.status = status;
   a.total_units = g.units;
   a.chunk_units = p.chunk_units;
@@ -380,9 +444,23 @@ PairArgs base_args(void* ws, const Geometry& g, const Plan& p, int* status) {
   a.njt = static_cast<int32_t>(g.njt);
   a.j_tile = p.j_tile;
   a.stages = p.stages;
+  a.j_lanes = p.j_lanes;
   a.wait_ns = g_wait_ns.load();
-  a.epoch = next_epoch();
   return a;
+}
+
+// Resolves the workspace of a launch: the library's (per stream) or one
+// caller buffer whose control head is cleared here, on the stream.
+cn_status launch_workspace(cudaStream_t s, const Geometry& g, void* ws, size_t ws_bytes, bool lib_ws, char** ctrl,
+                           char** data) {
+  if (lib_ws) return library_workspace(s, g.ctrl_bytes, g.data_bytes, ctrl, data);
+  if (!ws || ws_bytes < g.ws_bytes) return fail(CN_ERR_WORKSPACE, "workspace smaller than the size this call needs");
+  if (!aligned(ws, 256)) return fail(CN_ERR_MISALIGNED, "workspace must be 256-byte aligned");
+  cudaError_t e = cudaMemsetAsync(ws, 0, g.ctrl_bytes, s);
+  if (e != cudaSuccess) return fail_cuda(e, "cudaMemsetAsync(workspace control)");
+  *ctrl = static_cast<char*>(ws);
+  *data = static_cast<char*>(ws) + g.ctrl_bytes;
+  return CN_OK;
 }
 
 cn_status check_eps2(float eps2) {
@@ -435,14 +513,9 @@ cn_status force_common(bool dd, int64_t n_i, const float* pos_i, int64_t n_j, co
   if ((st = resolve_plan(dev, variant, n_i, n_j, guard, nullptr, &p)) != CN_OK) return st;
   Geometry g;
   if ((st = single_geometry(dev, *d, variant, guard, p, n_i, n_j, &g)) != CN_OK) return st;
-  if (lib_ws) {
-    if ((st = library_workspace(s, g.ws_bytes, &ws)) != CN_OK) return st;
-  } else if (!ws || ws_bytes < g.ws_bytes) {
-    return fail(CN_ERR_WORKSPACE, "workspace smaller than cn_workspace_bytes()");
-  } else if (!aligned(ws, 256)) {
-    return fail(CN_ERR_MISALIGNED, "workspace must be 256-byte aligned");
-  }
-  PairArgs a = base_args(ws, g, p, d->status);
+  char *ctrl = nullptr, *data = nullptr;
+  if ((st = launch_workspace(s, g, ws, ws_bytes, lib_ws, &ctrl, &data)) != CN_OK) return st;
+  PairArgs a = base_args(ctrl, data, g, p, d->status);
   a.pos_i = reinterpret_cast<const float4*>(pos_i);
   a.pos_j = reinterpret_cast<const float4*>(pos_mass_j);
   a.acc_out = acc_out;
@@ -454,6 +527,67 @@ cn_status force_common(bool dd, int64_t n_i, const float* pos_i, int64_t n_j, co
   e = dd ? cn::launch_dd(a, p, pot, guard, g.grid, s) : cn::launch_f32(a, p, pot, guard, false, g.grid, s);
   if (e != cudaSuccess) return fail_cuda(e, "pair kernel launch");
   return CN_OK;
+}
+
+cn_status jerk_common(int64_t n_i, const float* pos_i, const float* vel_i, int64_t n_j, const float* pos_mass_j,
+                      const float* vel_j, float eps2, float* acc_out, float* jerk_out, float* pot_out,
+                      cudaStream_t s) {
+  if (n_i < 0 || n_j < 0) return fail(CN_ERR_INVALID_ARG, "n_i and n_j must be >= 0");
+  cn_status st;
+  if ((st = check_eps2(eps2)) != CN_OK) return st;
+  if ((st = check_records(pos_i, n_i, "pos_i")) != CN_OK) return st;
+  if ((st = check_records(vel_i, n_i, "vel_i")) != CN_OK) return st;
+  if ((st = check_records(pos_mass_j, n_j, "pos_mass_j")) != CN_OK) return st;
+  if ((st = check_records(vel_j, n_j, "vel_j")) != CN_OK) return st;
+  if (n_i > 0 && (!acc_out || !jerk_out)) return fail(CN_ERR_INVALID_ARG, "acc_out and jerk_out are required");
+  if ((acc_out && !aligned(acc_out, 4)) || (jerk_out && !aligned(jerk_out, 4)) || (pot_out && !aligned(pot_out, 4)))
+    return fail(CN_ERR_MISALIGNED, "outputs must be 4-byte aligned");
+  const size_t ob = static_cast<size_t>(n_i) * 12, pb = pot_out ? static_cast<size_t>(n_i) * 4 : 0;
+  const size_t ib = static_cast<size_t>(n_i) * 16, jb = static_cast<size_t>(n_j) * 16;
+  const void* ins[4] = {pos_i, vel_i, pos_mass_j, vel_j};
+  const size_t insz[4] = {ib, ib, jb, jb};
+  const void* outs[3] = {acc_out, jerk_out, pot_out};
+  const size_t outsz[3] = {ob, ob, pb};
+  for (int o = 0; o < 3; ++o) {
+    for (int q = 0; q < 4; ++q)
+      if (overlaps(outs[o], outsz[o], ins[q], insz[q])) return fail(CN_ERR_INVALID_ARG, "outputs overlap inputs");
+    for (int q = o + 1; q < 3; ++q)
+      if (overlaps(outs[o], outsz[o], outs[q], outsz[q])) return fail(CN_ERR_INVALID_ARG, "outputs overlap each other");
+  }
+  if (n_i == 0) return CN_OK;
+  int dev = 0;
+  DeviceInfo* d = nullptr;
+  if ((st = current_device(&dev, &d)) != CN_OK) return st;
+  cudaError_t e;
+  if (n_j == 0) {
+    for (int o = 0; o < 3; ++o)
+      if (outs[o] && (e = cudaMemsetAsync(const_cast<void*>(outs[o]), 0, outsz[o], s)) != cudaSuccess)
+        return fail_cuda(e, "cudaMemsetAsync");
+    return CN_OK;
+  }
+  const bool pot = pot_out != nullptr;
+  const bool guard = needs_guard(eps2);
+  const int variant = pot ? cn::kJerkPot : cn::kJerk;
+  Plan p;
+  if ((st = resolve_plan(dev, variant, n_i, n_j, guard, nullptr, &p)) != CN_OK) return st;
+  Geometry g;
+  if ((st = single_geometry(dev, *d, variant, guard, p, n_i, n_j, &g)) != CN_OK) return st;
+  char *ctrl = nullptr, *data = nullptr;
+  if ((st = library_workspace(s, g.ctrl_bytes, g.data_bytes, &ctrl, &data)) != CN_OK) return st;
+  PairArgs a = base_args(ctrl, data, g, p, d->status);
+  a.pos_i = reinterpret_cast<const float4*>(pos_i);
+  a.pos_i2 = reinterpret_cast<const float4*>(vel_i);
+  a.pos_j = reinterpret_cast<const float4*>(pos_mass_j);
+  a.pos_j2 = reinterpret_cast<const float4*>(vel_j);
+  a.acc_out = acc_out;
+  a.jerk_out = jerk_out;
+  a.pot_out = pot_out;
+  a.n_i = n_i;
+  a.n_j = n_j;
+  a.eps2 = eps2;
+  if (inject("launch")) return fail(CN_ERR_CUDA, "kernel launch: injected launch failure");
+  e = cn::launch_jerk(a, p, pot, guard, g.grid, s);
+  return e == cudaSuccess ? CN_OK : fail_cuda(e, "force-jerk kernel launch");
 }
 
 cn_status run_batched(const cn_batch_plan* plan, const float* pos_mass, float* acc_out, float* pot_out, void* ws,
@@ -480,19 +614,16 @@ cn_status run_batched(const cn_batch_plan* plan, const float* pos_mass, float* a
       return fail_cuda(e, "cudaMemsetAsync");
     return CN_OK;
   }
-  if (!ws) {
-    if ((st = library_workspace(s, plan->ws_bytes, &ws)) != CN_OK) return st;
-  } else if (ws_bytes < plan->ws_bytes) {
-    return fail(CN_ERR_WORKSPACE, "workspace smaller than cn_batch_plan_workspace_bytes()");
-  } else if (!aligned(ws, 256)) {
-    return fail(CN_ERR_MISALIGNED, "workspace must be 256-byte aligned");
-  }
   Geometry g;
   g.units = plan->units;
   g.n_chunks = plan->n_chunks;
   g.n_tiles = plan->n_tiles;
-  g.off_partials = plan->off_partials;
-  PairArgs a = base_args(ws, g, plan->plan, d->status);
+  g.ctrl_bytes = plan->ctrl_bytes;
+  g.data_bytes = plan->data_bytes;
+  g.ws_bytes = plan->ws_bytes;
+  char *ctrl = nullptr, *data = nullptr;
+  if ((st = launch_workspace(s, g, ws, ws_bytes, ws == nullptr, &ctrl, &data)) != CN_OK) return st;
+  PairArgs a = base_args(ctrl, data, g, plan->plan, d->status);
   a.pos_i = reinterpret_cast<const float4*>(pos_mass);
   a.pos_j = reinterpret_cast<const float4*>(pos_mass);
   a.acc_out = acc_out;
@@ -574,7 +705,8 @@ cn_status build_batch_plan(int32_t n_clusters, const int64_t* offsets, const flo
   plan->n_chunks = g.n_chunks;
   plan->grid = g.grid;
   plan->ws_bytes = tiles.empty() ? 0 : g.ws_bytes;
-  plan->off_partials = g.off_partials;
+  plan->ctrl_bytes = g.ctrl_bytes;
+  plan->data_bytes = g.data_bytes;
   if (!tiles.empty()) {
     if (inject("alloc")) {
       delete plan;
@@ -685,7 +817,9 @@ cn_status cn_force_dd_ws(int64_t n_i, const float* pos_i, int64_t n_j, const flo
 }
 
 size_t cn_workspace_bytes(int variant, int64_t n_i, int64_t n_j) {
-  if (n_i <= 0 || n_j <= 0 || variant < cn::kF32 || variant > cn::kAdjoint) return 0;
+  if (n_i <= 0 || n_j <= 0 || variant < cn::kF32 || variant > cn::kJerkPot || variant == cn::kBatched ||
+      variant == cn::kBatchedPot)
+    return 0;
   int dev = 0;
   DeviceInfo* d = nullptr;
   if (current_device(&dev, &d) != CN_OK) return 0;
@@ -790,13 +924,13 @@ cn_status cn_force_adjoint(int64_t n, const float* pos_mass, float eps2, const f
   if ((st = resolve_plan(dev, cn::kAdjoint, n, n, guard, nullptr, &p)) != CN_OK) return st;
   Geometry g;
   if ((st = single_geometry(dev, *d, cn::kAdjoint, guard, p, n, n, &g)) != CN_OK) return st;
-  void* ws = nullptr;
-  if ((st = library_workspace(s, g.ws_bytes, &ws)) != CN_OK) return st;
-  float4* wrec = reinterpret_cast<float4*>(static_cast<char*>(ws) + g.off_wrec);
+  char *ctrl = nullptr, *data = nullptr;
+  if ((st = library_workspace(s, g.ctrl_bytes, g.data_bytes, &ctrl, &data)) != CN_OK) return st;
+  float4* wrec = reinterpret_cast<float4*>(data + g.off_wrec);
   if (inject("launch")) return fail(CN_ERR_CUDA, "kernel launch: injected launch failure");
   cudaError_t e = cn::launch_pack_w(w, wrec, n, s);
   if (e != cudaSuccess) return fail_cuda(e, "weight packing launch");
-  PairArgs a = base_args(ws, g, p, d->status);
+  PairArgs a = base_args(ctrl, data, g, p, d->status);
   a.pos_i = reinterpret_cast<const float4*>(pos_mass);
   a.pos_j = reinterpret_cast<const float4*>(pos_mass);
   a.pos_i2 = wrec;
@@ -808,6 +942,13 @@ cn_status cn_force_adjoint(int64_t n, const float* pos_mass, float eps2, const f
   a.eps2 = eps2;
   e = cn::launch_adjoint(a, p, guard, g.grid, s);
   return e == cudaSuccess ? CN_OK : fail_cuda(e, "adjoint kernel launch");
+}
+
+cn_status cn_force_jerk(int64_t n_i, const float* pos_i, const float* vel_i, int64_t n_j, const float* pos_mass_j,
+                        const float* vel_j, float eps2, float* acc_out, float* jerk_out, float* pot_out,
+                        cn_stream stream) {
+  return jerk_common(n_i, pos_i, vel_i, n_j, pos_mass_j, vel_j, eps2, acc_out, jerk_out, pot_out,
+                     reinterpret_cast<cudaStream_t>(stream));
 }
 
 cn_status cn_potential_energy(int64_t n, const float* pos_mass, const float* pot, double* w_out, cn_stream stream) {
@@ -880,7 +1021,7 @@ cn_status cn_force_host_f64(const double* xj, const double* mj, const double* xi
 }
 
 cn_status cn_tune_get(int variant, int64_t n_i, int64_t n_j, cn_tune* out) {
-  if (!out || variant < cn::kF32 || variant > cn::kBatchedPot || n_i < 0 || n_j < 0)
+  if (!out || variant < cn::kF32 || variant > cn::kJerkPot || n_i < 0 || n_j < 0)
     return fail(CN_ERR_INVALID_ARG, "bad variant, size or NULL output");
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -894,11 +1035,12 @@ cn_status cn_tune_get(int variant, int64_t n_i, int64_t n_j, cn_tune* out) {
   out->stages = p.stages;
   out->ctas_per_sm = p.ctas_per_sm;
   out->chunk_units = static_cast<int32_t>(p.chunk_units);
+  out->j_lanes = p.j_lanes;
   return CN_OK;
 }
 
 cn_status cn_tune_set(int variant, int64_t n_i, int64_t n_j, const cn_tune* tune) {
-  if (variant < cn::kF32 || variant > cn::kBatchedPot || n_i < 0 || n_j < 0)
+  if (variant < cn::kF32 || variant > cn::kJerkPot || n_i < 0 || n_j < 0)
     return fail(CN_ERR_INVALID_ARG, "bad variant or size");
   if (tune) {
     cn_status st = check_tune(variant, *tune);
@@ -934,41 +1076,86 @@ cn_status cn_autotune(int variant, int64_t n_i, const float* pos_i, int64_t n_j,
   float best_ms = 1e30f;
   cn_tune best{};
   cn_status result = CN_OK;
+  std::vector<cn_tune> cands;
   for (int k : ks) {
     if (!valid_k(variant, k)) continue;
     for (int th : ths) {
       if (static_cast<int64_t>(k) * th > 4 * std::max<int64_t>(n_i, 256)) continue;  // tile far larger than the i set
       for (int jt : tiles) {
         if (jt > 4 * std::max<int64_t>(n_j, 64)) continue;
-        cn_tune t{k, th, jt, 4, 0, 0};
-        cn_tune_set(variant, n_i, n_j, &t);
-        auto call = [&]() {
-          return force_common(dd, n_i, pos_i, n_j, pos_mass_j, eps2, acc_out, pot ? pot_out : nullptr, nullptr, 0,
-                              true, s);
-        };
-        cn_status st = call();  // warm-up (and workspace growth)
-        if (st != CN_OK) {
-          if (st == CN_ERR_INVALID_ARG) continue;  // shape does not fit
-          result = st;
-          break;
-        }
-        cudaEventRecord(e0, s);
-        for (int r = 0; r < reps; ++r) call();
-        cudaEventRecord(e1, s);
-        if (cudaEventSynchronize(e1) != cudaSuccess) {
-          result = fail(CN_ERR_CUDA, "autotune: event synchronisation failed");
-          break;
-        }
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best_ms) {
-          best_ms = ms;
-          best = t;
-        }
+        cands.push_back(cn_tune{k, th, jt, 4, 0, 0, 1});
       }
-      if (result != CN_OK) break;
     }
-    if (result != CN_OK) break;
+  }
+  if (!dd && n_i <= 16384) {  // split-j shapes for small systems
+    for (int jl : {2, 4, 8, 16, 32}) {
+      if (n_i * jl > 262144) continue;
+      for (int th : {128, 256})
+        for (int64_t jt : {static_cast<int64_t>(512), static_cast<int64_t>(2048), round_up(std::max<int64_t>(n_j, 1), 8 * jl),
+                           static_cast<int64_t>(4096)}) {
+          if (jt % (8 * jl) || jt > 4096 || jt < 8 * jl) continue;
+          cands.push_back(cn_tune{1, th, static_cast<int32_t>(jt), jt >= n_j ? 1 : 3, 0, 0, jl});
+        }
+    }
+  }
+  // Candidates are timed as one CUDA graph of `reps` calls, so that the host
+  // cost of a call does not hide the device time of small problems. Capture
+  // needs a non-default stream: the legacy stream gets a private one.
+  cudaStream_t ts = s;
+  const bool own_stream = (s == nullptr);
+  if (own_stream && cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return fail(CN_ERR_CUDA, "autotune: cudaStreamCreate failed");
+  }
+  auto call = [&]() {
+    return force_common(dd, n_i, pos_i, n_j, pos_mass_j, eps2, acc_out, pot ? pot_out : nullptr, nullptr, 0, true,
+                        ts);
+  };
+  for (const cn_tune& t : cands) {
+    if (check_tune(variant, t) != CN_OK) continue;
+    cn_tune_set(variant, n_i, n_j, &t);
+    cn_status st = call();  // warm-up (and workspace growth)
+    if (st == CN_ERR_INVALID_ARG) continue;  // shape does not fit
+    if (st != CN_OK) {
+      result = st;
+      break;
+    }
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    if (cudaStreamBeginCapture(ts, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      result = fail(CN_ERR_CUDA, "autotune: cudaStreamBeginCapture failed");
+      break;
+    }
+    for (int r = 0; r < reps && st == CN_OK; ++r) st = call();
+    cudaError_t e = cudaStreamEndCapture(ts, &graph);
+    if (st == CN_OK && e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (st == CN_OK && e == cudaSuccess) e = cudaGraphLaunch(exec, ts);  // warm
+    if (st == CN_OK && e == cudaSuccess) e = cudaEventRecord(e0, ts);
+    if (st == CN_OK && e == cudaSuccess) e = cudaGraphLaunch(exec, ts);
+    if (st == CN_OK && e == cudaSuccess) e = cudaEventRecord(e1, ts);
+    if (st == CN_OK && e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (st == CN_OK && e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (st != CN_OK) {
+      result = st;
+      break;
+    }
+    if (e != cudaSuccess) {
+      result = fail_cuda(e, "autotune: timing a candidate");
+      break;
+    }
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = t;
+    }
+  }
+  if (own_stream) {
+    cudaStreamSynchronize(ts);
+    release_library_workspace(ts);
+    cudaStreamDestroy(ts);
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -1063,7 +1250,7 @@ cn_status cn_get_device_status(cn_stream stream) {
     std::lock_guard<std::mutex> lock(g_mu);
     for (auto& kv : g_ws)
       if (kv.first.first == dev) {
-        if (kv.second.ptr) cudaMemset(kv.second.ptr, 0, kv.second.bytes);
+        if (kv.second.ctrl) cudaMemset(kv.second.ctrl, 0, kv.second.ctrl_bytes);
         if (kv.second.aux) cudaMemset(kv.second.aux, 0, (cn::energy_workspace_doubles() + 1) * sizeof(double));
       }
   }

@@ -4,9 +4,9 @@
 namespace cn {
 namespace {
 
-template <int K, bool POT, bool GUARD, bool BATCHED>
+template <int K, bool POT, bool GUARD, bool BATCHED, bool SPLITJ = false>
 const void* fn() {
-  return reinterpret_cast<const void*>(&pair_kernel<F32Policy<K, POT, GUARD>, K, BATCHED>);
+  return reinterpret_cast<const void*>(&pair_kernel<F32Policy<K, POT, GUARD, SPLITJ>, K, BATCHED>);
 }
 
 template <bool POT, bool GUARD, bool BATCHED>
@@ -24,7 +24,12 @@ const void* by_k(int k) {
   }
 }
 
-const void* select(int k, bool pot, bool guard, bool batched) {
+const void* select(int k, bool pot, bool guard, bool batched, int j_lanes) {
+  if (j_lanes > 1) {  // split-j kernels: one i-particle per j-lane group, single systems
+    if (k != 1 || batched) return nullptr;
+    if (pot) return guard ? fn<1, true, true, false, true>() : fn<1, true, false, false, true>();
+    return guard ? fn<1, false, true, false, true>() : fn<1, false, false, false, true>();
+  }
   if (batched) {
     if (pot) return guard ? by_k<true, true, true>(k) : by_k<true, false, true>(k);
     return guard ? by_k<false, true, true>(k) : by_k<false, false, true>(k);
@@ -36,7 +41,7 @@ const void* select(int k, bool pot, bool guard, bool batched) {
 }  // namespace
 
 cudaError_t occupancy_f32(const Plan& p, bool pot, bool guard, bool batched, size_t smem, int* ctas) {
-  const void* f = select(p.k, pot, guard, batched);
+  const void* f = select(p.k, pot, guard, batched, p.j_lanes);
   if (!f) return cudaErrorInvalidValue;
   cudaError_t e = prepare_kernel(f, smem);
   if (e != cudaSuccess) return e;
@@ -45,7 +50,7 @@ cudaError_t occupancy_f32(const Plan& p, bool pot, bool guard, bool batched, siz
 
 cudaError_t launch_f32(const PairArgs& a, const Plan& p, bool pot, bool guard, bool batched, int grid,
                        cudaStream_t s) {
-  const void* f = select(p.k, pot, guard, batched);
+  const void* f = select(p.k, pot, guard, batched, p.j_lanes);
   if (!f) return cudaErrorInvalidValue;
   const size_t smem = ring_smem_bytes(p);
   cudaError_t e = prepare_kernel(f, smem);

@@ -39,8 +39,9 @@ struct PairArgs {
   const float4* pos_j2;   // second j record (adjoint: loss weights), else unused
   void* acc_out;          // float[n_i][3] (FP32 forms), double[n_i][3] (compensated), dL/dx (adjoint)
   void* pot_out;          // float[n_i] / double[n_i] / dL/dm (adjoint) or nullptr
+  void* jerk_out;         // float[n_i][3] (force-jerk-potential form) or nullptr
   float4* partials;       // [n_chunks][2][i_tile] float4 (x2 for hi/lo in the compensated form)
-  unsigned long long* counters;  // [n_tiles] arrival counters: (launch epoch << 32) | arrivals
+  unsigned int* counters;  // [n_tiles] arrival counters (zero at launch; the merging CTA re-zeroes its own)
   int* queue;             // [0] next chunk, [1] finished CTAs (dynamic schedule; zero between launches)
   int* status;            // device status word
   const TileDesc* tiles;  // batched schedule only
@@ -54,7 +55,7 @@ struct PairArgs {
   int32_t j_tile;
   int32_t stages;
   float eps2;             // single system
-  uint32_t epoch;         // nonzero launch number: counters carrying another epoch count as zero
+  int32_t j_lanes;        // lanes sharing one i-particle (split-j FP32 kernels; 1 otherwise)
   uint64_t wait_ns;       // bound on every barrier wait
 };
 
@@ -66,7 +67,8 @@ struct Plan {
   int stages = 4;         // ring depth
   int ctas_per_sm = 0;    // 0: occupancy maximum
   int64_t chunk_units = 0;  // 0: static schedule
-  int i_tile() const { return k * threads; }
+  int j_lanes = 1;          // lanes sharing one i-particle (split-j kernels, k = 1)
+  int i_tile() const { return k * threads / j_lanes; }
 };
 
 enum Variant : int {
@@ -77,6 +79,8 @@ enum Variant : int {
   kAdjoint = 4,
   kBatched = 5,
   kBatchedPot = 6,
+  kJerk = 7,
+  kJerkPot = 8,
 };
 
 // Kernel selection, occupancy and launch (defined in the per-variant
@@ -89,6 +93,8 @@ cudaError_t occupancy_dd(const Plan& p, bool pot, bool guard, size_t smem, int* 
 cudaError_t launch_adjoint(const PairArgs& a, const Plan& p, bool guard, int grid, cudaStream_t s);
 cudaError_t occupancy_adjoint(const Plan& p, bool guard, size_t smem, int* ctas);
 cudaError_t launch_pack_w(const float* w, float4* wrec, int64_t n, cudaStream_t s);
+cudaError_t launch_jerk(const PairArgs& a, const Plan& p, bool pot, bool guard, int grid, cudaStream_t s);
+cudaError_t occupancy_jerk(const Plan& p, bool pot, bool guard, size_t smem, int* ctas);
 cudaError_t launch_energy(int64_t n, const float4* pos_mass, const float* pot_f, const double* pot_d,
                           double* partials, int* counter, double* w_out, cudaStream_t s);
 

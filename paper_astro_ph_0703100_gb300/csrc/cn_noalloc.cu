@@ -26,10 +26,6 @@ namespace {
 // which this library's device code is loaded holds it until the process
 // exits, whether or not this entry point is ever called there.
 constexpr size_t kStaticScratchBytes = static_cast<size_t>(32) << 20;
-// Head of the scratch that must be zero when a call starts (the dynamic
-// schedule's queue words); the rest needs no initialisation.
-constexpr size_t kZeroHeadBytes = 4096;
-
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
 std::mutex g_mu;
@@ -74,11 +70,10 @@ extern "C" cn_status cn_force_noalloc(int64_t n_i, const float* pos_i, int64_t n
                                std::to_string(kStaticScratchBytes) +
                                " bytes (use cn_force or cn_force_ws, or a launch shape with fewer i-tiles)");
     if (need > 0) {
+      // the force call below clears the scratch's control head (queue words
+      // and arrival counters) on the stream before it launches
       cn_status st = scratch_address(&scratch);
       if (st != CN_OK) return st;
-      cudaError_t e = cudaMemsetAsync(scratch, 0, kZeroHeadBytes, s);
-      if (e != cudaSuccess)
-        return cn::set_error(CN_ERR_CUDA, std::string("cudaMemsetAsync(static scratch): ") + cudaGetErrorString(e));
     }
   }
   return cn::force_f32_on_workspace(n_i, pos_i, n_j, pos_mass_j, eps2, acc_out, pot_out, scratch,

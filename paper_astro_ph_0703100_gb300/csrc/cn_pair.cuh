@@ -27,23 +27,6 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-// Counts one arrival on a split tile's counter and returns the number of
-// earlier arrivals of this launch. The counter word is (epoch << 32) |
-// arrivals; a word left by another launch or holding stale workspace bytes
-// carries another epoch and counts as zero. Lock-free: each failed CAS means
-// another CTA's arrival succeeded.
-__device__ __forceinline__ int arrive_counter(unsigned long long* c, uint32_t epoch) {
-  unsigned long long cur = *reinterpret_cast<volatile unsigned long long*>(c);
-  for (;;) {
-    const unsigned long long next = (static_cast<uint32_t>(cur >> 32) == epoch)
-                                        ? cur + 1ull
-                                        : ((static_cast<unsigned long long>(epoch) << 32) | 1ull);
-    const unsigned long long seen = atomicCAS(c, cur, next);
-    if (seen == cur) return static_cast<int>(static_cast<uint32_t>(next)) - 1;
-    cur = seen;
-  }
-}
-
 // ------------------------------------------------------------------ schedule
 struct Sched {
   int64_t U;  // total units
@@ -127,11 +110,19 @@ __device__ __forceinline__ void pair_f32(const float4 pj, const float (&xi)[K][3
 
 // ------------------------------------------------------------------ policies
 // Plain FP32: per-tile FP32 partial folded into an FP32 running sum.
-template <int K, bool POT, bool GUARD>
+// SPLITJ: groups of j_lanes consecutive lanes share one i-particle, lane
+// `sub` of a group taking j records sub, sub + j_lanes, ... of each tile;
+// the group's sums are combined by a fixed xor butterfly of warp shuffles
+// at the end of each segment (small systems: many threads, no cross-CTA
+// merge).
+template <int K, bool POT, bool GUARD, bool SPLITJ = false>
 struct F32Policy {
   static constexpr int NC = POT ? 4 : 3;
   static constexpr int kSlotF4 = 1;  // float4 per i-particle in a workspace slot
+  static constexpr int kSums = 4;    // FP64 sums in the split-tile merge
   static constexpr int kJRec = 1;    // float4 per j record
+  static constexpr bool kSplitJ = SPLITJ;
+  static constexpr int kMinBlocks = K >= 8 ? 1 : 2;  // 256-thread CTAs per SM the register budget must allow
   float xi[K][3];
   float run[K][NC];
 
@@ -151,23 +142,42 @@ struct F32Policy {
   }
 
   __device__ __forceinline__ void tile(const float4* js, int T, float eps2, int64_t /*self_off*/, bool /*diag*/,
-                                       int /*tid*/, int /*NT*/) {
+                                       int /*row*/, int /*rows*/, int sub, int jl) {
     float part[K][NC];
 #pragma unroll
     for (int k = 0; k < K; ++k)
 #pragma unroll
       for (int c = 0; c < NC; ++c) part[k][c] = 0.f;
-    // 16 j records per loop trip (j_tile is a multiple of 16): enough
-    // independent pair terms in flight to cover the MUFU and FMA latencies.
+    if constexpr (SPLITJ) {
+      // this lane's j records: sub, sub + jl, ... (j_tile is a multiple of 8 jl)
 #pragma unroll 1
-    for (int j = 0; j < T; j += 16) {
+      for (int j = sub; j < T; j += 8 * jl) {
 #pragma unroll
-      for (int jj = 0; jj < 16; ++jj) pair_f32<K, POT, GUARD>(js[j + jj], xi, eps2, part);
+        for (int jj = 0; jj < 8; ++jj) pair_f32<K, POT, GUARD>(js[j + jj * jl], xi, eps2, part);
+      }
+    } else {
+      // 16 j records per loop trip (j_tile is a multiple of 16): enough
+      // independent pair terms in flight to cover the MUFU and FMA latencies.
+#pragma unroll 1
+      for (int j = 0; j < T; j += 16) {
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) pair_f32<K, POT, GUARD>(js[j + jj], xi, eps2, part);
+      }
     }
 #pragma unroll
     for (int k = 0; k < K; ++k)
 #pragma unroll
       for (int c = 0; c < NC; ++c) run[k][c] += part[k][c];
+  }
+
+  // sums the running sums of the j_lanes lanes of each group (xor butterfly)
+  __device__ __forceinline__ void reduce_lanes(int jl) {
+    for (int off = jl >> 1; off > 0; off >>= 1) {
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) run[k][c] += __shfl_xor_sync(0xffffffffu, run[k][c], off);
+    }
   }
 
   __device__ __forceinline__ void store_final(const PairArgs& a, int64_t i, int k) const {
@@ -184,15 +194,15 @@ struct F32Policy {
     slot[il] = make_float4(run[k][0], run[k][1], run[k][2], POT ? run[k][3] : 0.f);
   }
 
-  __device__ static __forceinline__ void add_partial(const float4* slot, int il, int /*i_tile*/, double (&s)[4]) {
-    const float4 v = __ldcg(slot + il);
-    s[0] += v.x;
-    s[1] += v.y;
-    s[2] += v.z;
-    s[3] += v.w;
+  // adds one loaded partial (its kSlotF4 float4 words) to the FP64 sums
+  __device__ static __forceinline__ void add_partial(const float4 (&v)[kSlotF4], double (&s)[kSums]) {
+    s[0] += v[0].x;
+    s[1] += v[0].y;
+    s[2] += v[0].z;
+    s[3] += v[0].w;
   }
 
-  __device__ static __forceinline__ void store_merged(const PairArgs& a, int64_t i, const double (&s)[4]) {
+  __device__ static __forceinline__ void store_merged(const PairArgs& a, int64_t i, const double (&s)[kSums]) {
     float* acc = static_cast<float*>(a.acc_out) + 3 * i;
     acc[0] = static_cast<float>(s[0]);
     acc[1] = static_cast<float>(s[1]);
@@ -284,7 +294,11 @@ template <int K, bool POT, bool GUARD>
 struct DDPolicy {
   static constexpr int NC = POT ? 4 : 3;
   static constexpr int kSlotF4 = 2;  // hi float4 then lo float4
+  static constexpr int kSums = 4;
   static constexpr int kJRec = 1;
+  static constexpr bool kSplitJ = false;
+  static constexpr int kMinBlocks = K >= 4 ? 1 : 2;
+  __device__ __forceinline__ void reduce_lanes(int) {}
   float xi[K][3];
   float hi[K][NC];
   float lo[K][NC];
@@ -305,7 +319,7 @@ struct DDPolicy {
   }
 
   __device__ __forceinline__ void tile(const float4* js, int T, float eps2, int64_t /*self_off*/, bool /*diag*/,
-                                       int /*tid*/, int /*NT*/) {
+                                       int /*row*/, int /*rows*/, int /*sub*/, int /*jl*/) {
 #pragma unroll 1
     for (int j = 0; j < T; j += 8) {
 #pragma unroll
@@ -329,16 +343,16 @@ struct DDPolicy {
     slot[i_tile + il] = make_float4(lo[k][0], lo[k][1], lo[k][2], POT ? lo[k][3] : 0.f);
   }
 
-  __device__ static __forceinline__ void add_partial(const float4* slot, int il, int i_tile, double (&s)[4]) {
-    const float4 h = __ldcg(slot + il);
-    const float4 l = __ldcg(slot + i_tile + il);
+  __device__ static __forceinline__ void add_partial(const float4 (&v)[kSlotF4], double (&s)[kSums]) {
+    const float4 h = v[0];
+    const float4 l = v[1];
     s[0] += static_cast<double>(h.x) + static_cast<double>(l.x);
     s[1] += static_cast<double>(h.y) + static_cast<double>(l.y);
     s[2] += static_cast<double>(h.z) + static_cast<double>(l.z);
     s[3] += static_cast<double>(h.w) + static_cast<double>(l.w);
   }
 
-  __device__ static __forceinline__ void store_merged(const PairArgs& a, int64_t i, const double (&s)[4]) {
+  __device__ static __forceinline__ void store_merged(const PairArgs& a, int64_t i, const double (&s)[kSums]) {
     double* acc = static_cast<double*>(a.acc_out) + 3 * i;
     acc[0] = s[0];
     acc[1] = s[1];
@@ -387,7 +401,11 @@ template <int K, bool GUARD>
 struct AdjointPolicy {
   static constexpr int NC = 4;
   static constexpr int kSlotF4 = 1;
+  static constexpr int kSums = 4;
   static constexpr int kJRec = 2;  // (x, y, z, m) then (wx, wy, wz, 0)
+  static constexpr bool kSplitJ = false;
+  static constexpr int kMinBlocks = K >= 4 ? 1 : 2;
+  __device__ __forceinline__ void reduce_lanes(int) {}
   float xk[K][3];
   float mk[K];
   float wk[K][3];
@@ -417,8 +435,8 @@ struct AdjointPolicy {
   }
 
   // self_off = (first j index of the tile) - (first i index of the i-tile)
-  __device__ __forceinline__ void tile(const float4* js, int T, float eps2, int64_t self_off, bool diag, int tid,
-                                       int NT) {
+  __device__ __forceinline__ void tile(const float4* js, int T, float eps2, int64_t self_off, bool diag, int row,
+                                       int rows, int /*sub*/, int /*jl*/) {
     const float4* jw = js + T;
     float part[K][4];
 #pragma unroll
@@ -429,7 +447,7 @@ struct AdjointPolicy {
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       // the j slot (0 .. T-1) holding this thread's own particle, or -1
-      const int64_t sj = static_cast<int64_t>(k * NT + tid) - self_off;
+      const int64_t sj = static_cast<int64_t>(k * rows + row) - self_off;
       self_j[k] = (sj >= 0 && sj < T) ? static_cast<int>(sj) : -1;
     }
     if (!diag) {
@@ -465,15 +483,14 @@ struct AdjointPolicy {
     slot[il] = make_float4(run[k][0], run[k][1], run[k][2], run[k][3]);
   }
 
-  __device__ static __forceinline__ void add_partial(const float4* slot, int il, int /*i_tile*/, double (&s)[4]) {
-    const float4 v = __ldcg(slot + il);
-    s[0] += v.x;
-    s[1] += v.y;
-    s[2] += v.z;
-    s[3] += v.w;
+  __device__ static __forceinline__ void add_partial(const float4 (&v)[kSlotF4], double (&s)[kSums]) {
+    s[0] += v[0].x;
+    s[1] += v[0].y;
+    s[2] += v[0].z;
+    s[3] += v[0].w;
   }
 
-  __device__ static __forceinline__ void store_merged(const PairArgs& a, int64_t i, const double (&s)[4]) {
+  __device__ static __forceinline__ void store_merged(const PairArgs& a, int64_t i, const double (&s)[kSums]) {
     float* g = static_cast<float*>(a.acc_out) + 3 * i;
     g[0] = static_cast<float>(s[0]);
     g[1] = static_cast<float>(s[1]);
@@ -482,18 +499,163 @@ struct AdjointPolicy {
   }
 };
 
+// Force, jerk and potential (the force-jerk-potential pipeline description
+// of the appendix) for particles moving with velocities v. Per pair, with
+// d = x_j - x_i, w = v_j - v_i, s = |d|^2 + eps2, r = s^-1/2 and q = m r^3:
+//   a += q d;   jerk += q (w - b d) with b = 3 (d . w) r^2;   pot += m r
+// (d a / dt for straight-line motion): 3 + 3 FADD, 3 FFMA, MUFU, 3 FMUL for
+// r^2, m r, q, 3 for d . w, 2 for b, 1 for q b, 3 into a, 6 into the jerk:
+// 27 FP32 issue slots + 1 MUFU (the potential adds 3).
+template <int K, bool POT, bool GUARD>
+__device__ __forceinline__ void pair_jerk(const float4 pj, const float4 vj, const float (&xi)[K][3],
+                                          const float (&vi)[K][3], float eps2, float (&part)[K][7]) {
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const float dx = pj.x - xi[k][0];
+    const float dy = pj.y - xi[k][1];
+    const float dz = pj.z - xi[k][2];
+    const float wx = vj.x - vi[k][0];
+    const float wy = vj.y - vi[k][1];
+    const float wz = vj.z - vi[k][2];
+    float s, d2 = 0.f;
+    if constexpr (POT) {
+      d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+      s = d2 + eps2;
+    } else {
+      s = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+    }
+    float r = rsqrt_mufu(s);
+    if constexpr (GUARD) r = (s > 0.f) ? r : 0.f;
+    const float r2 = r * r;
+    const float mr = pj.w * r;
+    const float q = mr * r2;
+    const float b = (3.0f * r2) * fmaf(dx, wx, fmaf(dy, wy, dz * wz));
+    const float qb = q * b;
+    part[k][0] = fmaf(q, dx, part[k][0]);
+    part[k][1] = fmaf(q, dy, part[k][1]);
+    part[k][2] = fmaf(q, dz, part[k][2]);
+    part[k][3] = fmaf(-qb, dx, fmaf(q, wx, part[k][3]));
+    part[k][4] = fmaf(-qb, dy, fmaf(q, wy, part[k][4]));
+    part[k][5] = fmaf(-qb, dz, fmaf(q, wz, part[k][5]));
+    if constexpr (POT) part[k][6] += (d2 != 0.f) ? mr : 0.f;
+  }
+}
+
+template <int K, bool POT, bool GUARD>
+struct JerkPolicy {
+  static constexpr int kSlotF4 = 2;  // (ax, ay, az, jx) then (jy, jz, pot, 0)
+  static constexpr int kSums = 7;
+  static constexpr int kJRec = 2;    // (x, y, z, m) then (vx, vy, vz, -)
+  static constexpr bool kSplitJ = false;
+  static constexpr int kMinBlocks = 1;  // 20 registers of state per i-particle
+  __device__ __forceinline__ void reduce_lanes(int) {}
+  float xi[K][3];
+  float vi[K][3];
+  float run[K][7];
+
+  __device__ __forceinline__ void load_i(const PairArgs& a, int64_t gi, bool valid, int k) {
+    float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (valid) {
+      p = __ldg(a.pos_i + gi);
+      v = __ldg(a.pos_i2 + gi);
+    }
+    xi[k][0] = p.x;
+    xi[k][1] = p.y;
+    xi[k][2] = p.z;
+    vi[k][0] = v.x;
+    vi[k][1] = v.y;
+    vi[k][2] = v.z;
+  }
+
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+      for (int c = 0; c < 7; ++c) run[k][c] = 0.f;
+  }
+
+  __device__ __forceinline__ void tile(const float4* js, int T, float eps2, int64_t /*self_off*/, bool /*diag*/,
+                                       int /*row*/, int /*rows*/, int /*sub*/, int /*jl*/) {
+    const float4* jv = js + T;
+    float part[K][7];
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+      for (int c = 0; c < 7; ++c) part[k][c] = 0.f;
+#pragma unroll 1
+    for (int j = 0; j < T; j += 4) {
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) pair_jerk<K, POT, GUARD>(js[j + jj], jv[j + jj], xi, vi, eps2, part);
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+      for (int c = 0; c < 7; ++c) run[k][c] += part[k][c];
+  }
+
+  __device__ __forceinline__ void store_final(const PairArgs& a, int64_t i, int k) const {
+    float* acc = static_cast<float*>(a.acc_out) + 3 * i;
+    float* jk = static_cast<float*>(a.jerk_out) + 3 * i;
+    acc[0] = run[k][0];
+    acc[1] = run[k][1];
+    acc[2] = run[k][2];
+    jk[0] = run[k][3];
+    jk[1] = run[k][4];
+    jk[2] = run[k][5];
+    if constexpr (POT) {
+      if (a.pot_out) static_cast<float*>(a.pot_out)[i] = -run[k][6];
+    }
+  }
+
+  __device__ __forceinline__ void store_partial(float4* slot, int il, int i_tile, int k) const {
+    slot[il] = make_float4(run[k][0], run[k][1], run[k][2], run[k][3]);
+    slot[i_tile + il] = make_float4(run[k][4], run[k][5], run[k][6], 0.f);
+  }
+
+  __device__ static __forceinline__ void add_partial(const float4 (&v)[kSlotF4], double (&s)[kSums]) {
+    s[0] += v[0].x;
+    s[1] += v[0].y;
+    s[2] += v[0].z;
+    s[3] += v[0].w;
+    s[4] += v[1].x;
+    s[5] += v[1].y;
+    s[6] += v[1].z;
+  }
+
+  __device__ static __forceinline__ void store_merged(const PairArgs& a, int64_t i, const double (&s)[kSums]) {
+    float* acc = static_cast<float*>(a.acc_out) + 3 * i;
+    float* jk = static_cast<float*>(a.jerk_out) + 3 * i;
+    acc[0] = static_cast<float>(s[0]);
+    acc[1] = static_cast<float>(s[1]);
+    acc[2] = static_cast<float>(s[2]);
+    jk[0] = static_cast<float>(s[3]);
+    jk[1] = static_cast<float>(s[4]);
+    jk[2] = static_cast<float>(s[5]);
+    if constexpr (POT) {
+      if (a.pot_out) static_cast<float*>(a.pot_out)[i] = static_cast<float>(-s[6]);
+    }
+  }
+};
+
 // ------------------------------------------------------------------ kernel
-// Register budget: with K <= 4 two 256-thread CTAs must fit on an SM (up to
-// 128 registers per thread); K = 8 may use up to 255.
+// Register budget per policy: Policy::kMinBlocks 256-thread CTAs must fit
+// on an SM (2: up to 128 registers per thread; 1: up to 255).
 template <class Policy, int K, bool BATCHED>
-__global__ void __launch_bounds__(256, (K >= 8 ? 1 : 2)) pair_kernel(const __grid_constant__ PairArgs a) {
+__global__ void __launch_bounds__(256, Policy::kMinBlocks) pair_kernel(const __grid_constant__ PairArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int NT = blockDim.x;
   const int tid = threadIdx.x;
   const int lane = tid & 31;
   const int T = a.j_tile;
   const int S = a.stages;
-  const int IT = NT * K;
+  // thread -> (i row, j lane): rows = threads / j_lanes i-particles per k
+  constexpr bool SJ = Policy::kSplitJ;
+  const int JL = SJ ? a.j_lanes : 1;
+  const int sub = SJ ? tid % JL : 0;
+  const int row = SJ ? tid / JL : tid;
+  const int ROWS = SJ ? NT / JL : NT;
+  const int IT = ROWS * K;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem);
   uint64_t* empty = full + S;
   volatile int* ctl = reinterpret_cast<volatile int*>(smem + 16 * S);  // [0] abort [1] last [2] chunk
@@ -512,7 +674,10 @@ __global__ void __launch_bounds__(256, (K >= 8 ? 1 : 2)) pair_kernel(const __gri
 
   const Sched sc{a.total_units, a.n_chunks, a.chunk_units};
   const bool dynamic = a.chunk_units > 0;
-  const uint32_t D = S > 2 ? static_cast<uint32_t>(S - 2) : 1u;  // prefetch distance in tiles
+  // prefetch distance in tiles: a stage is refilled once every warp has left
+  // the tile two loads back (one tile of slack); a 2-stage ring refills the
+  // stage of the previous tile, a 1-stage ring loads one tile at a time
+  const uint32_t D = S > 2 ? static_cast<uint32_t>(S - 2) : static_cast<uint32_t>(S - 1);
   uint32_t issued = 0;    // loads issued (thread 0 only)
   uint32_t consumed = 0;  // tiles consumed (identical in every thread)
   constexpr int JR = Policy::kJRec;
@@ -574,7 +739,7 @@ __global__ void __launch_bounds__(256, (K >= 8 ? 1 : 2)) pair_kernel(const __gri
         if (!seg_open) {
 #pragma unroll
           for (int k = 0; k < K; ++k) {
-            const int il = k * NT + tid;
+            const int il = k * ROWS + row;
             acc.load_i(a, td.i0 + il, il < td.ni, k);
           }
           acc.zero();
@@ -596,7 +761,7 @@ __global__ void __launch_bounds__(256, (K >= 8 ? 1 : 2)) pair_kernel(const __gri
           // j-range of this unit relative to the i-tile (used by the adjoint's self-pair exclusion)
           const int64_t self_off = td.j0 + jt * T - td.i0;
           const bool diag = self_off < IT && self_off + T > 0;
-          acc.tile(ring + static_cast<size_t>(slot) * T * JR, T, td.eps2, self_off, diag, tid, NT);
+          acc.tile(ring + static_cast<size_t>(slot) * T * JR, T, td.eps2, self_off, diag, row, ROWS, sub, JL);
           __syncwarp();
           if (lane == 0) mbar_arrive(&empty[slot]);
         }
@@ -604,43 +769,60 @@ __global__ void __launch_bounds__(256, (K >= 8 ? 1 : 2)) pair_kernel(const __gri
         ++jt;
         if (jt == td.njt || uc + 1 == ue) {
           // ---- end of a segment: write the tile or its partial
+          if constexpr (SJ) acc.reduce_lanes(JL);
           const int64_t qf = sc.chunk_of(td.unit0);
           const int64_t ql = sc.chunk_of(td.unit0 + td.njt - 1);
           if (qf == ql) {
 #pragma unroll
             for (int k = 0; k < K; ++k) {
-              const int il = k * NT + tid;
-              if (il < td.ni) acc.store_final(a, td.i0 + il, k);
+              const int il = k * ROWS + row;
+              if (il < td.ni && sub == 0) acc.store_final(a, td.i0 + il, k);
             }
           } else {
             const int which = (seg_u0 == ub) ? 0 : 1;
             float4* slotp = a.partials + static_cast<size_t>(q * 2 + which) * IT * Policy::kSlotF4;
 #pragma unroll
             for (int k = 0; k < K; ++k) {
-              const int il = k * NT + tid;
-              acc.store_partial(slotp, il, IT, k);
+              const int il = k * ROWS + row;
+              if (sub == 0) acc.store_partial(slotp, il, IT, k);
             }
             __threadfence();
             __syncthreads();
             if (tid == 0) {
-              const int before = arrive_counter(&a.counters[tc], a.epoch);
-              ctl[1] = (before == static_cast<int>(ql - qf)) ? 1 : 0;
+              const unsigned before = atomicAdd(&a.counters[tc], 1u);
+              ctl[1] = (before == static_cast<unsigned>(ql - qf)) ? 1 : 0;
             }
             __syncthreads();
             if (ctl[1]) {
               __threadfence();
               for (int k = 0; k < K; ++k) {
-                const int il = k * NT + tid;
-                if (il >= td.ni) continue;
-                double s[4] = {0.0, 0.0, 0.0, 0.0};
-                for (int64_t p = qf; p <= ql; ++p) {
-                  const int w = (sc.begin(p) >= td.unit0) ? 0 : 1;
-                  Policy::add_partial(a.partials + static_cast<size_t>(p * 2 + w) * IT * Policy::kSlotF4, il, IT,
-                                      s);
+                const int il = k * ROWS + row;
+                if (il >= td.ni || sub != 0) continue;
+                double s[Policy::kSums];
+#pragma unroll
+                for (int c = 0; c < Policy::kSums; ++c) s[c] = 0.0;
+                // A batch of partials is loaded at once (independent L2 reads
+                // in flight together), then added in chunk order.
+                constexpr int kBatch = 8 / Policy::kSlotF4;
+                for (int64_t p0 = qf; p0 <= ql; p0 += kBatch) {
+                  float4 v[kBatch][Policy::kSlotF4];
+#pragma unroll
+                  for (int u = 0; u < kBatch; ++u) {
+                    const int64_t p = p0 + u;
+                    if (p <= ql) {
+                      const int w = (sc.begin(p) >= td.unit0) ? 0 : 1;
+                      const float4* slot = a.partials + static_cast<size_t>(p * 2 + w) * IT * Policy::kSlotF4;
+#pragma unroll
+                      for (int h = 0; h < Policy::kSlotF4; ++h) v[u][h] = __ldcg(slot + h * IT + il);
+                    }
+                  }
+#pragma unroll
+                  for (int u = 0; u < kBatch; ++u)
+                    if (p0 + u <= ql) Policy::add_partial(v[u], s);
                 }
                 Policy::store_merged(a, td.i0 + il, s);
               }
-              if (tid == 0) a.counters[tc] = 0ull;
+              if (tid == 0) a.counters[tc] = 0u;
             }
           }
           seg_open = false;

@@ -79,6 +79,12 @@ TUNES = [
     {"i_per_thread": 8, "threads": 128, "j_tile": 512, "stages": 6},
     {"i_per_thread": 4, "threads": 64, "j_tile": 128, "stages": 4, "chunk_units": 3},
     {"i_per_thread": 2, "threads": 128, "j_tile": 32, "stages": 4, "ctas_per_sm": 1},
+    # split-j shapes: lanes of a warp share one i-particle, shuffle-reduced
+    {"i_per_thread": 1, "threads": 128, "j_tile": 256, "stages": 2, "j_lanes": 32},
+    {"i_per_thread": 1, "threads": 64, "j_tile": 64, "stages": 3, "j_lanes": 4},
+    {"i_per_thread": 1, "threads": 256, "j_tile": 128, "stages": 4, "j_lanes": 16, "chunk_units": 2},
+    {"i_per_thread": 1, "threads": 128, "j_tile": 128, "stages": 1, "j_lanes": 16},
+    {"i_per_thread": 4, "threads": 128, "j_tile": 64, "stages": 1},
 ]
 
 
@@ -105,7 +111,8 @@ def test_ragged_shapes_and_launch_shapes(shape, tune):
 
 
 @pytest.mark.parametrize("tune", [None, {"i_per_thread": 2, "threads": 64, "j_tile": 64, "stages": 3},
-                                  {"i_per_thread": 4, "threads": 128, "j_tile": 128, "chunk_units": 5}])
+                                  {"i_per_thread": 4, "threads": 128, "j_tile": 128, "chunk_units": 5},
+                                  {"i_per_thread": 1, "threads": 128, "j_tile": 512, "stages": 3, "j_lanes": 8}])
 def test_bitwise_deterministic(tune):
     cn = lib()
     torch = torch_cuda()
@@ -167,9 +174,10 @@ def test_workspace_form_matches_library_workspace():
     t = dev_tensor(p)
     nbytes = cn.cn_workspace_bytes("f32_pot", 5000, 5000)
     assert nbytes > 0
-    ws = torch.zeros(nbytes, dtype=torch.uint8, device="cuda")
+    ws = torch.full((nbytes,), 0xAB, dtype=torch.uint8, device="cuda")  # no initialisation needed
     a1, p1 = cn.cn_force_ws(t, t, 1e-3, ws, potential=True)
-    a2, p2 = cn.cn_force_ws(t, t, 1e-3, ws, potential=True)  # counters were left zero by the first call
+    ws.fill_(0x5C)  # stale bytes between calls are harmless
+    a2, p2 = cn.cn_force_ws(t, t, 1e-3, ws, potential=True)
     a3, p3 = cn.cn_force(t, t, 1e-3, potential=True)
     torch.cuda.synchronize()
     assert torch.equal(a1, a3) and torch.equal(a2, a3) and torch.equal(p1, p3)

@@ -1,0 +1,86 @@
+"""Parity of cn_force_jerk (acceleration, jerk, potential) with the FP64 oracle.
+
+Tolerances per particle (relative to the oracle's vector norm): acceleration
+and potential 1e-5 as for the plain FP32 form; jerk 1e-4, since its pair term
+w - 3 (d . w) d / s is a difference of two FP32 products whose cancellation
+amplifies the FP32 rounding (measured ~1e-6 .. 1e-5).
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from gpu_common import dev_tensor, e_max, lib, rel_pot_err, torch_cuda
+from paper_astro_ph_0703100_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL_ACC = 1e-5
+TOL_JERK = 1e-4
+
+
+def run(cn, pi, vi, pj, vj, eps2, potential=True):
+    torch = torch_cuda()
+    a, j, p = cn.cn_force_jerk(dev_tensor(pi), dev_tensor(vi), dev_tensor(pj), dev_tensor(vj), eps2,
+                               potential=potential)
+    torch.cuda.synchronize()
+    assert cn.cn_get_device_status() == 0
+    return a.cpu().numpy(), j.cpu().numpy(), (p.cpu().numpy() if p is not None else None)
+
+
+@pytest.mark.parametrize("tune", [None, {"i_per_thread": 1, "threads": 64, "j_tile": 16, "stages": 2},
+                                  {"i_per_thread": 2, "threads": 128, "j_tile": 64, "stages": 3},
+                                  {"i_per_thread": 4, "threads": 256, "j_tile": 128, "stages": 4, "chunk_units": 3},
+                                  {"i_per_thread": 2, "threads": 128, "j_tile": 256, "stages": 1}])
+@pytest.mark.parametrize("shape", [(1, 1), (33, 31), (1000, 777), (4097, 2049)])
+def test_jerk_ragged_and_launch_shapes(shape, tune):
+    cn = lib()
+    n_i, n_j = shape
+    pj, vj = synth.plummer(n_j, 10 + n_j), synth.plummer_velocities(n_j, 20 + n_j)
+    pi, vi = synth.plummer(n_i, 30 + n_i), synth.plummer_velocities(n_i, 40 + n_i)
+    for v in ("jerk", "jerk_pot"):
+        cn.cn_tune_set(v, n_i, n_j, tune)
+    try:
+        a, j, p = run(cn, pi, vi, pj, vj, 1e-3)
+        a2, j2, _ = run(cn, pi, vi, pj, vj, 1e-3, potential=False)
+    finally:
+        for v in ("jerk", "jerk_pot"):
+            cn.cn_tune_set(v, n_i, n_j, None)
+    ra, rj, rp = oracle.force_jerk(pi, vi, pj, vj, 1e-3)
+    assert e_max(a, ra) <= TOL_ACC and e_max(a2, ra) <= TOL_ACC
+    assert e_max(j, rj) <= TOL_JERK and e_max(j2, rj) <= TOL_JERK
+    assert rel_pot_err(p, rp) <= TOL_ACC
+
+
+def test_jerk_hermite_plummer_sampled():
+    """N = 65536 Plummer sphere with velocities, i set = j set, the appendix's eps2 = 1/256^2."""
+    cn = lib()
+    n = 65536
+    p, v = synth.plummer(n, 5), synth.plummer_velocities(n, 6)
+    eps2 = float(np.float32(1.0 / 256.0) ** 2)
+    a, j, phi = run(cn, p, v, p, v, eps2)
+    rows = synth.sample_rows(n, 1024, seed=7)
+    ra, rj, rp = oracle.force_jerk(p, v, p, v, eps2, rows=rows)
+    assert e_max(a[rows], ra) <= TOL_ACC
+    assert e_max(j[rows], rj) <= TOL_JERK
+    assert rel_pot_err(phi[rows], rp) <= TOL_ACC
+    # the acceleration agrees with the force-only kernel's
+    torch = torch_cuda()
+    acc, _ = cn.cn_force(dev_tensor(p), dev_tensor(p), eps2)
+    torch.cuda.synchronize()
+    assert e_max(a, acc.cpu().numpy().astype(np.float64)) <= 2 * TOL_ACC
+
+
+def test_jerk_zero_softening_and_empty_j():
+    cn = lib()
+    torch = torch_cuda()
+    p, v = synth.plummer(300, 2), synth.plummer_velocities(300, 3)
+    p[5] = p[4]
+    a, j, phi = run(cn, p, v, p, v, 0.0)
+    ra, rj, rp = oracle.force_jerk(p, v, p, v, 0.0)
+    assert np.all(np.isfinite(a)) and np.all(np.isfinite(j)) and np.all(np.isfinite(phi))
+    assert e_max(a, ra) <= TOL_ACC and e_max(j, rj) <= TOL_JERK
+    z = torch.zeros((0, 4), dtype=torch.float32, device="cuda")
+    acc, jerk, pot = cn.cn_force_jerk(dev_tensor(p), dev_tensor(v), z, z, 0.01, potential=True)
+    torch.cuda.synchronize()
+    assert torch.count_nonzero(acc) == 0 and torch.count_nonzero(jerk) == 0 and torch.count_nonzero(pot) == 0

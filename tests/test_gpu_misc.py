@@ -60,11 +60,14 @@ def test_host_forms():
 
 def test_tune_roundtrip_and_probe():
     cn = lib()
-    t = {"i_per_thread": 2, "threads": 256, "j_tile": 64, "stages": 3, "ctas_per_sm": 0, "chunk_units": 0}
+    t = {"i_per_thread": 2, "threads": 256, "j_tile": 64, "stages": 3, "ctas_per_sm": 0, "chunk_units": 0,
+         "j_lanes": 1}
     cn.cn_tune_set("f32", 5000, 7000, t)
     assert cn.cn_tune_get("f32", 5000, 7000) == t
     cn.cn_tune_set("f32", 5000, 7000, None)
     assert cn.cn_tune_get("f32", 5000, 7000) != t
+    with pytest.raises(cn.CunbodyError):  # split-j lanes are offered for the FP32 form only
+        cn.cn_tune_set("dd", 5000, 7000, dict(t, i_per_thread=1, j_lanes=8))
     peaks = cn.cn_probe_peaks()
     assert peaks["sms"] >= 100
     assert peaks["ffma_per_s"] > 1e12 and peaks["mufu_rsqrt_per_s"] > 1e11 and peaks["pair_mix_per_s"] > 1e11
