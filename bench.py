@@ -627,6 +627,18 @@ def run_only(args):
         out = torch.empty((n, 3), dtype=torch.float32 if args.only == "f32" else torch.float64, device=device)
         step = lambda: fn(t, t, eps2, acc_out=out)
         pairs = float(n) * n
+    elif args.only == "jerk":
+        p, eps2 = synth.plummer(n, n), float(np.float32(1.0 / 256.0) ** 2)
+        v = synth.plummer_velocities(n, n + 1)
+        t = torch.from_numpy(p).to(device)
+        tv = torch.from_numpy(v).to(device)
+        if tune:
+            cn.cn_tune_set("jerk_pot", n, n, tune)
+        a_o = torch.empty((n, 3), dtype=torch.float32, device=device)
+        j_o = torch.empty((n, 3), dtype=torch.float32, device=device)
+        p_o = torch.empty((n,), dtype=torch.float32, device=device)
+        step = lambda: cn.cn_force_jerk(t, tv, t, tv, eps2, acc_out=a_o, jerk_out=j_o, pot_out=p_o)
+        pairs = float(n) * n
     elif args.only == "adjoint":
         p = synth.plummer(n, n)
         eps2 = float(np.float32(0.01) ** 2)
@@ -708,7 +720,7 @@ def main(argv=None):
     ap.add_argument("--no-rows", action="store_true", help="skip the other workloads (C1, C2 small, C3, C4, C5)")
     ap.add_argument("--cpu-budget", type=float, default=10.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--ref-rows", type=int, default=256, help="oracle rows per step of --impl reference")
-    ap.add_argument("--only", choices=("f32", "dd", "adjoint", "batched"),
+    ap.add_argument("--only", choices=("f32", "dd", "adjoint", "batched", "jerk"),
                     help="time one kernel family alone (profiling mode; prints its own JSON)")
     ap.add_argument("--tune", help="pinned launch shape for --only: i_per_thread,threads,j_tile,stages")
     ap.add_argument("--chunk", type=int, default=0, help="dynamic chunk size for --only batched")
