@@ -397,6 +397,10 @@ def run_ours(args):
 ADJOINT_ISSUE_PER_PAIR = 31  # 30 FP32 + 1 MUFU (adjoint pair, see the kernel notes)
 DD_ISSUE_PER_PAIR = 104      # double-single pair term + per-term TwoSum (FP32 instructions)
 JERK_ISSUE_PER_PAIR = 31     # 27 FP32 + 1 MUFU + 3 for the potential (force-jerk-potential pair)
+# symmetric form: 16 FP32 + 1 MUFU per unordered pair, plus the warp
+# reduce-scatter (27 SHFL + 27 FADD per 8 j records per lane, i.e. 54 / (8 K)
+# per unordered pair at K particles per thread; K = 8 by default)
+SYM_ISSUE_PER_UNORDERED_PAIR = 17 + 54 / 64
 
 
 def _events_ms(torch, fn, reps, stream):
@@ -576,6 +580,58 @@ def measure_rows(args, cn, torch, device, peak):
                          "sample": "512 seeded rows"}}
     del tp, tv, a_h, j_h, p_h
 
+    # Symmetric form (Newton's third law, each unordered pair once) on the
+    # headline system; the rate counts the N^2 ordered pairs it resolves
+    p, eps2 = workload(131072, 131072)
+    n = p.shape[0]
+    tp = torch.from_numpy(p).to(device)
+    a_s = cn.cn_force_symmetric(tp, eps2)
+    ms = _events_ms(torch, lambda: cn.cn_force_symmetric(tp, eps2, acc_out=a_s), 10, stream)
+    r = synth.sample_rows(n, 512, seed=13)
+    t0 = time.perf_counter()
+    ra, _ = oracle.force(p, p, eps2, rows=r, potential=False)
+    dt = time.perf_counter() - t0
+    sym_roof = 2.0 * lane_rate / SYM_ISSUE_PER_UNORDERED_PAIR
+    rows["symmetric131072"] = {
+        "pairs_per_s": float(n) * n / (ms / 1e3), "ms": ms,
+        "frac": float(n) * n / (ms / 1e3) / sym_roof, "roofline_pairs_per_s": sym_roof,
+        "launch_shape": cn.cn_tune_get("symmetric", n, n),
+        "emax": oracle.e_max(a_s.cpu().numpy()[r], ra),
+        "cpu_baseline": {"value": r.size * n / dt, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+                         "sample": "512 seeded rows"}}
+    del tp, a_s
+
+    # Interaction lists (Section 4.4 use): N = 131072 particles in groups of
+    # 256, each against its own list of 4096 records (particles + pseudo-particles)
+    pos_i, i_off, lists, jb, jc = synth.interaction_lists(131072, 256, 4096, seed=131072)
+    eps2 = float(np.float32(0.01) ** 2)
+    lp = cn.ListPlan(i_off, jb, jc, eps2)
+    ti, tj = torch.from_numpy(pos_i).to(device), torch.from_numpy(lists).to(device)
+    acc_l = torch.empty((pos_i.shape[0], 3), dtype=torch.float32, device=device)
+    with torch.cuda.stream(side):
+        ws_l = lp.new_workspace(device)
+        lp.capture(ti, tj, acc_l, workspace=ws_l, stream=side)
+        for _ in range(3):
+            lp.launch(side)
+        ms_l = _events_ms(torch, lambda: lp.launch(side), 20, side)
+    torch.cuda.synchronize()
+    a_host = acc_l.cpu().numpy()
+    errs, t_or, n_or = [], 0.0, 0
+    for g in range(0, len(jc), 64):
+        lo, hi = int(i_off[g]), int(i_off[g + 1])
+        t0 = time.perf_counter()
+        ref, _ = oracle.force(pos_i[lo:hi], lists[jb[g]:jb[g] + jc[g]], eps2, potential=False)
+        t_or += time.perf_counter() - t0
+        n_or += (hi - lo) * int(jc[g])
+        errs.append(oracle.e_max(a_host[lo:hi], ref))
+    rows["tree_lists131072"] = {
+        "pairs": lp.pairs, "pairs_per_s": lp.pairs / (ms_l / 1e3), "ms": ms_l,
+        "frac": lp.pairs / (ms_l / 1e3) / peak, "emax": max(errs),
+        "cpu_baseline": {"value": n_or / t_or, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+                         "sample": "every 64th group against its list"}}
+    lp.close()
+    del ti, tj, acc_l, ws_l
+
     # C5: adjoint at N = 65536, eps = 0.01
     n = 65536
     p = synth.plummer(n, 65536)
@@ -626,6 +682,14 @@ def run_only(args):
         fn = cn.cn_force if args.only == "f32" else cn.cn_force_dd
         out = torch.empty((n, 3), dtype=torch.float32 if args.only == "f32" else torch.float64, device=device)
         step = lambda: fn(t, t, eps2, acc_out=out)
+        pairs = float(n) * n
+    elif args.only == "sym":
+        p, eps2 = workload(n, n)
+        t = torch.from_numpy(p).to(device)
+        if tune:
+            cn.cn_tune_set("symmetric", n, n, tune)
+        out = torch.empty((n, 3), dtype=torch.float32, device=device)
+        step = lambda: cn.cn_force_symmetric(t, eps2, acc_out=out)
         pairs = float(n) * n
     elif args.only == "jerk":
         p, eps2 = synth.plummer(n, n), float(np.float32(1.0 / 256.0) ** 2)
@@ -720,7 +784,7 @@ def main(argv=None):
     ap.add_argument("--no-rows", action="store_true", help="skip the other workloads (C1, C2 small, C3, C4, C5)")
     ap.add_argument("--cpu-budget", type=float, default=10.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--ref-rows", type=int, default=256, help="oracle rows per step of --impl reference")
-    ap.add_argument("--only", choices=("f32", "dd", "adjoint", "batched", "jerk"),
+    ap.add_argument("--only", choices=("f32", "dd", "adjoint", "batched", "jerk", "sym"),
                     help="time one kernel family alone (profiling mode; prints its own JSON)")
     ap.add_argument("--tune", help="pinned launch shape for --only: i_per_thread,threads,j_tile,stages")
     ap.add_argument("--chunk", type=int, default=0, help="dynamic chunk size for --only batched")

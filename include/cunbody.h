@@ -80,7 +80,8 @@ typedef enum cn_variant {
     CN_VARIANT_BATCHED = 5,    /* cn_force_batched                */
     CN_VARIANT_BATCHED_POT = 6, /* cn_force_batched with potential */
     CN_VARIANT_JERK = 7,        /* cn_force_jerk without potential */
-    CN_VARIANT_JERK_POT = 8     /* cn_force_jerk with potential    */
+    CN_VARIANT_JERK_POT = 8,    /* cn_force_jerk with potential    */
+    CN_VARIANT_SYMMETRIC = 9    /* cn_force_symmetric              */
 } cn_variant;
 
 /* Launch shape of the pair kernels. Zero in a field means "library default". */
@@ -177,6 +178,21 @@ CN_API size_t cn_workspace_bytes(int variant, int64_t n_i, int64_t n_j);
 CN_API cn_status cn_force_noalloc(int64_t n_i, const float *pos_i, int64_t n_j, const float *pos_mass_j, float eps2,
                                   float *acc_out, float *pot_out, cn_stream stream);
 
+/*
+ * Accelerations of n particles under each other's gravity (i set = j set)
+ * evaluating every unordered pair once (Newton's third law: the pair term
+ * is added to one particle and subtracted, with the other mass, from the
+ * other). Not in the paper, whose kernel evaluates every ordered pair; about
+ * 16 FP32 instructions and one MUFU per unordered pair plus a warp
+ * reduce-scatter of the j-side sums, against 2 x 13 for the two ordered
+ * pairs. Results are accumulated per (tile, partner tile) and merged in
+ * FP64 in a fixed order (bitwise reproducible for a given launch shape).
+ *   pos_mass : float[n][4]; acc_out : float[n][3]
+ * Uses a library workspace of n_tiles x n_pad x 16 bytes (268 MB at
+ * n = 131072 with the default 1024-particle tiles).
+ */
+CN_API cn_status cn_force_symmetric(int64_t n, const float *pos_mass, float eps2, float *acc_out, cn_stream stream);
+
 /* ------------------------------------------------------------------ batched */
 
 /* An ensemble of independent systems ("clusters") stored back to back:
@@ -220,6 +236,37 @@ CN_API cn_status cn_force_batched(const cn_batch_plan *plan, const float *pos_ma
 CN_API cn_status cn_batch_plan_capture(cn_batch_plan *plan, const float *pos_mass, float *acc_out, float *pot_out,
                                 void *workspace, size_t ws_bytes, cn_stream stream);
 CN_API cn_status cn_batch_plan_launch(const cn_batch_plan *plan, cn_stream stream);
+
+/* Interaction lists: the use of the O(N^2) engine inside the modified tree
+ * algorithm (Section 4.4), where a group of neighbouring i-particles shares
+ * one list of j records (particles and tree-node pseudo-particles, each an
+ * (x, y, z, m) record) gathered by the tree code. Group g evaluates the
+ * i-particles i_offsets[g] .. i_offsets[g+1]-1 of pos_i against the j
+ * records j_begin[g] .. j_begin[g] + j_count[g] - 1 of pos_mass_j with
+ * softening eps2[g]; lists may overlap or be shared. The plan (a unit table
+ * in device memory) is built once per list structure on the current device.
+ *   i_offsets_host : int64[n_groups + 1], non-decreasing, i_offsets[0] == 0
+ *   j_begin_host, j_count_host : int64[n_groups], >= 0
+ *   eps2_host      : float[n_groups]
+ * Destroy with cn_batch_plan_destroy; workspace size from
+ * cn_batch_plan_workspace_bytes; cn_batch_plan_info reports the number of
+ * i-particles and the pair count sum_g n_i,g n_j,g. */
+CN_API cn_status cn_list_plan_create(int32_t n_groups, const int64_t *i_offsets_host, const int64_t *j_begin_host,
+                                     const int64_t *j_count_host, const float *eps2_host, const cn_tune *tune,
+                                     int with_potential, cn_batch_plan **plan_out);
+
+/* One persistent launch over all groups of a list plan.
+ *   pos_i      : float[n_i][4] (n_i = i_offsets[n_groups]; 4th component ignored)
+ *   pos_mass_j : float[*][4] lists, long enough for every group's range
+ *   acc_out    : float[n_i][3]; pot_out : float[n_i] or NULL (groups with an
+ *                empty list get zeros)
+ *   workspace  : as for cn_force_batched. */
+CN_API cn_status cn_force_lists(const cn_batch_plan *plan, const float *pos_i, const float *pos_mass_j,
+                                float *acc_out, float *pot_out, void *workspace, size_t ws_bytes, cn_stream stream);
+/* cn_batch_plan_capture for list plans (cn_batch_plan_launch replays it). */
+CN_API cn_status cn_list_plan_capture(cn_batch_plan *plan, const float *pos_i, const float *pos_mass_j,
+                                      float *acc_out, float *pot_out, void *workspace, size_t ws_bytes,
+                                      cn_stream stream);
 
 /* ------------------------------------------------------------------ adjoint */
 

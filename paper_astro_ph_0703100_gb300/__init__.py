@@ -27,8 +27,11 @@ __all__ = [
     "cn_force_dd",
     "cn_force_dd_ws",
     "cn_workspace_bytes",
+    "cn_force_symmetric",
     "BatchPlan",
     "cn_force_batched",
+    "ListPlan",
+    "cn_force_lists",
     "cn_force_adjoint",
     "cn_force_jerk",
     "cn_potential_energy",
@@ -59,6 +62,7 @@ VARIANT = {
     "batched_pot": 6,
     "jerk": 7,
     "jerk_pot": 8,
+    "symmetric": 9,
 }
 
 
@@ -141,6 +145,17 @@ def cn_force_dd(pos_i, pos_mass_j, eps2, acc_out=None, pot_out=None, potential=F
 
 def cn_force_dd_ws(pos_i, pos_mass_j, eps2, workspace, acc_out=None, pot_out=None, potential=False, stream=None):
     return _force("cn_force_dd_ws", True, pos_i, pos_mass_j, eps2, acc_out, pot_out, potential, stream, workspace)
+
+
+def cn_force_symmetric(pos_mass, eps2, acc_out=None, stream=None):
+    """Accelerations of all particles, each unordered pair evaluated once."""
+    torch = _torch()
+    _records(pos_mass, "pos_mass")
+    n = pos_mass.shape[0]
+    acc = _out(acc_out, (n, 3), torch.float32, pos_mass.device, "acc_out")
+    check(load().cn_force_symmetric(n, _ptr(pos_mass), float(eps2), _ptr(acc), _stream_handle(stream)),
+          "cn_force_symmetric")
+    return acc
 
 
 def cn_workspace_bytes(variant, n_i, n_j) -> int:
@@ -226,6 +241,98 @@ def cn_force_batched(plan: BatchPlan, pos_mass, acc_out=None, pot_out=None, work
     nbytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
     check(load().cn_force_batched(plan._h, _ptr(pos_mass), _ptr(acc), _ptr(pot), _ptr(workspace), nbytes,
                                   _stream_handle(stream)), "cn_force_batched")
+    return acc, pot
+
+
+class ListPlan:
+    """Groups of i-particles, each against its own list of j records (Section 4.4).
+
+    Group g: i-particles ``i_offsets[g]:i_offsets[g+1]`` of ``pos_i`` against
+    records ``j_begin[g]:j_begin[g]+j_count[g]`` of ``pos_mass_j``, softening
+    ``eps2[g]`` (a scalar applies to every group).
+    """
+
+    def __init__(self, i_offsets, j_begin, j_count, eps2, tune=None, potential=False):
+        self.i_offsets = np.ascontiguousarray(np.asarray(i_offsets, dtype=np.int64))
+        n_groups = self.i_offsets.shape[0] - 1
+        self.j_begin = np.ascontiguousarray(np.asarray(j_begin, dtype=np.int64))
+        self.j_count = np.ascontiguousarray(np.asarray(j_count, dtype=np.int64))
+        e = np.asarray(eps2, dtype=np.float32)
+        self.eps2 = np.ascontiguousarray(np.full(n_groups, e, dtype=np.float32) if e.ndim == 0 else e)
+        if n_groups < 0 or self.j_begin.shape[0] != n_groups or self.j_count.shape[0] != n_groups or \
+                self.eps2.shape[0] != n_groups:
+            raise ValueError("i_offsets needs n_groups + 1 entries; j_begin, j_count and eps2 n_groups")
+        handle = ctypes.c_void_p()
+        t = ctypes.byref(_tune_struct(tune)) if tune is not None else None
+        lib = load()
+        vpd = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+        check(lib.cn_list_plan_create(n_groups, vpd(self.i_offsets), vpd(self.j_begin), vpd(self.j_count),
+                                      vpd(self.eps2), t, int(bool(potential)), ctypes.byref(handle)),
+              "cn_list_plan_create")
+        self._h = handle
+        self.potential = bool(potential)
+        self.n_groups = n_groups
+        n_total = ctypes.c_int64()
+        pairs = ctypes.c_double()
+        check(lib.cn_batch_plan_info(self._h, ctypes.byref(n_total), ctypes.byref(pairs)), "cn_batch_plan_info")
+        self.n_i = int(n_total.value)
+        self.n_j = int(max((self.j_begin + self.j_count)[self.j_count > 0].max(initial=0), 0)) if n_groups else 0
+        self.pairs = float(pairs.value)
+        self._keep = None
+
+    @property
+    def workspace_bytes(self) -> int:
+        return int(load().cn_batch_plan_workspace_bytes(self._h))
+
+    def new_workspace(self, device="cuda"):
+        torch = _torch()
+        return torch.zeros(max(self.workspace_bytes, 256), dtype=torch.uint8, device=device)
+
+    def _args(self, pos_i, pos_mass_j, acc_out, pot_out):
+        torch = _torch()
+        _records(pos_i, "pos_i")
+        _records(pos_mass_j, "pos_mass_j")
+        if pos_i.shape[0] != self.n_i or pos_mass_j.shape[0] < self.n_j:
+            raise ValueError("pos_i must hold n_i records and pos_mass_j every listed record")
+        acc = _out(acc_out, (self.n_i, 3), torch.float32, pos_i.device, "acc_out")
+        pot = None
+        if self.potential or pot_out is not None:
+            pot = _out(pot_out, (self.n_i,), torch.float32, pos_i.device, "pot_out")
+        return acc, pot
+
+    def run(self, pos_i, pos_mass_j, acc_out=None, pot_out=None, workspace=None, stream=None):
+        return cn_force_lists(self, pos_i, pos_mass_j, acc_out, pot_out, workspace, stream)
+
+    def capture(self, pos_i, pos_mass_j, acc_out, pot_out=None, workspace=None, stream=None):
+        acc, pot = self._args(pos_i, pos_mass_j, acc_out, pot_out)
+        if workspace is None:
+            workspace = self.new_workspace(pos_i.device)
+        self._keep = (pos_i, pos_mass_j, acc, pot, workspace)
+        check(load().cn_list_plan_capture(self._h, _ptr(pos_i), _ptr(pos_mass_j), _ptr(acc), _ptr(pot),
+                                          _ptr(workspace), workspace.numel(), _stream_handle(stream)),
+              "cn_list_plan_capture")
+        return acc, pot
+
+    def launch(self, stream=None):
+        check(load().cn_batch_plan_launch(self._h, _stream_handle(stream)), "cn_batch_plan_launch")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().cn_batch_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def cn_force_lists(plan: ListPlan, pos_i, pos_mass_j, acc_out=None, pot_out=None, workspace=None, stream=None):
+    acc, pot = plan._args(pos_i, pos_mass_j, acc_out, pot_out)
+    nbytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
+    check(load().cn_force_lists(plan._h, _ptr(pos_i), _ptr(pos_mass_j), _ptr(acc), _ptr(pot), _ptr(workspace),
+                                nbytes, _stream_handle(stream)), "cn_force_lists")
     return acc, pot
 
 

@@ -45,6 +45,7 @@ SIGNATURES = {
     "cn_force_dd_ws": (c_int, [c_i64, vp, c_i64, vp, c_f32, vp, vp, vp, c_size, vp]),
     "cn_workspace_bytes": (c_size, [c_int, c_i64, c_i64]),
     "cn_force_noalloc": (c_int, [c_i64, vp, c_i64, vp, c_f32, vp, vp, vp]),
+    "cn_force_symmetric": (c_int, [c_i64, vp, c_f32, vp, vp]),
     "cn_batch_plan_create": (c_int, [c_i32, vp, vp, vp, c_int, ctypes.POINTER(vp)]),
     "cn_batch_plan_destroy": (c_int, [vp]),
     "cn_batch_plan_workspace_bytes": (c_size, [vp]),
@@ -52,6 +53,9 @@ SIGNATURES = {
     "cn_force_batched": (c_int, [vp, vp, vp, vp, vp, c_size, vp]),
     "cn_batch_plan_capture": (c_int, [vp, vp, vp, vp, vp, c_size, vp]),
     "cn_batch_plan_launch": (c_int, [vp, vp]),
+    "cn_list_plan_create": (c_int, [c_i32, vp, vp, vp, vp, vp, c_int, ctypes.POINTER(vp)]),
+    "cn_force_lists": (c_int, [vp, vp, vp, vp, vp, vp, c_size, vp]),
+    "cn_list_plan_capture": (c_int, [vp, vp, vp, vp, vp, vp, c_size, vp]),
     "cn_force_adjoint": (c_int, [c_i64, vp, c_f32, vp, vp, vp, vp]),
     "cn_force_jerk": (c_int, [c_i64, vp, vp, c_i64, vp, vp, c_f32, vp, vp, vp, vp]),
     "cn_potential_energy": (c_int, [c_i64, vp, vp, vp, vp]),

@@ -28,8 +28,11 @@ using cn::PairArgs;
 
 struct cn_batch_plan {
   int dev = -1;
+  bool lists = false;       // interaction-list plan: separate i and j arrays
+  bool zero_first = false;  // some group has i-particles but an empty list: clear outputs first
   int32_t n_clusters = 0;
-  int64_t n_total = 0;
+  int64_t n_total = 0;      // i-particles (cluster plans: also the j records)
+  int64_t n_j_total = 0;    // j records a list plan reads (max of begin + count)
   double pairs = 0.0;
   Plan plan;
   bool guard = false;
@@ -222,6 +225,7 @@ int bucket(int64_t n) {
 }
 
 bool valid_k(int variant, int k) {
+  if (variant == cn::kSym) return k == 1 || k == 2 || k == 4 || k == 8;
   if (variant == cn::kDD || variant == cn::kDDPot || variant == cn::kAdjoint || variant == cn::kJerk ||
       variant == cn::kJerkPot)
     return k == 1 || k == 2 || k == 4;
@@ -251,6 +255,14 @@ cn_tune default_tune(int variant, int64_t n_i, int64_t n_j) {
     const int64_t unit = 8 * jl;
     t.j_tile = static_cast<int32_t>(std::min<int64_t>(round_up(std::max<int64_t>(n_j, 1), unit), 4096));
     t.stages = n_j <= t.j_tile ? 1 : 3;
+    return t;
+  }
+  if (variant == cn::kSym) {
+    // tiles of threads x K particles; j_tile is the ring stage (divides the tile)
+    t.i_per_thread = n >= 32768 ? 8 : (n >= 4096 ? 4 : 1);
+    t.threads = n >= 4096 ? 128 : 64;
+    t.j_tile = n >= 4096 ? 256 : 64;
+    t.stages = 4;
     return t;
   }
   if (variant == cn::kBatched || variant == cn::kBatchedPot) {
@@ -332,12 +344,18 @@ cn_status resolve_plan(int dev, int variant, int64_t n_i, int64_t n_j, bool guar
   p->ctas_per_sm = t.ctas_per_sm;
   p->chunk_units = t.chunk_units;
   p->j_lanes = t.j_lanes > 1 ? t.j_lanes : 1;
+  if (p->j_lanes > 1 && variant == cn::kSym) return fail(CN_ERR_INVALID_ARG, "the symmetric form takes no j_lanes");
   if (p->j_lanes > 1) {
     p->k = 1;
     if (p->j_tile % (8 * p->j_lanes)) return fail(CN_ERR_INVALID_ARG, "j_tile must be a multiple of 8 x j_lanes");
   }
-  const size_t smem = two_records(variant) ? cn::adjoint_smem_bytes(*p) : cn::ring_smem_bytes(*p);
-  if (smem > kMaxSmem) return fail(CN_ERR_INVALID_ARG, "j_tile x stages exceeds the shared memory of one CTA");
+  const size_t smem = variant == cn::kSym
+                          ? cn::sym_smem_bytes(p->threads, p->k, p->j_tile, p->stages)
+                          : (two_records(variant) ? cn::adjoint_smem_bytes(*p) : cn::ring_smem_bytes(*p));
+  if (smem > kMaxSmem) return fail(CN_ERR_INVALID_ARG, "the launch shape exceeds the shared memory of one CTA");
+  if (variant == cn::kSym && p->i_tile() % p->j_tile) p->j_tile = std::min(p->j_tile, p->i_tile());
+  if (variant == cn::kSym && (p->i_tile() % p->j_tile || p->j_tile % 8))
+    return fail(CN_ERR_INVALID_ARG, "symmetric form: j_tile must divide threads x i_per_thread and be a multiple of 8");
   return CN_OK;
 }
 
@@ -590,29 +608,78 @@ cn_status jerk_common(int64_t n_i, const float* pos_i, const float* vel_i, int64
   return e == cudaSuccess ? CN_OK : fail_cuda(e, "force-jerk kernel launch");
 }
 
-cn_status run_batched(const cn_batch_plan* plan, const float* pos_mass, float* acc_out, float* pot_out, void* ws,
-                      size_t ws_bytes, cudaStream_t s) {
+cn_status symmetric_common(int64_t n, const float* pos_mass, float eps2, float* acc_out, cudaStream_t s) {
+  if (n < 0) return fail(CN_ERR_INVALID_ARG, "n must be >= 0");
+  cn_status st;
+  if ((st = check_eps2(eps2)) != CN_OK) return st;
+  if ((st = check_records(pos_mass, n, "pos_mass")) != CN_OK) return st;
+  if (n > 0 && !acc_out) return fail(CN_ERR_INVALID_ARG, "acc_out is NULL");
+  if (acc_out && !aligned(acc_out, 4)) return fail(CN_ERR_MISALIGNED, "acc_out must be 4-byte aligned");
+  if (overlaps(acc_out, static_cast<size_t>(n) * 12, pos_mass, static_cast<size_t>(n) * 16))
+    return fail(CN_ERR_INVALID_ARG, "acc_out overlaps pos_mass");
+  if (n == 0) return CN_OK;
+  int dev = 0;
+  DeviceInfo* d = nullptr;
+  if ((st = current_device(&dev, &d)) != CN_OK) return st;
+  const bool guard = needs_guard(eps2);
+  Plan p;
+  if ((st = resolve_plan(dev, cn::kSym, n, n, guard, nullptr, &p)) != CN_OK) return st;
+  const int64_t B = p.i_tile();
+  const int64_t T = ceil_div(n, B);
+  if (T > 65535) return fail(CN_ERR_INVALID_ARG, "too many tiles for the symmetric form");
+  const size_t smem = cn::sym_smem_bytes(p.threads, p.k, p.j_tile, p.stages);
+  int occ = 0;
+  cudaError_t e = cn::occupancy_sym(p.k, guard, p.threads, smem, &occ);
+  if (e != cudaSuccess) return fail_cuda(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+  if (occ <= 0) return fail(CN_ERR_INVALID_ARG, "launch shape does not fit on one SM");
+  cn::SymArgs a{};
+  a.n = n;
+  a.n_pad = T * B;
+  a.n_tiles = static_cast<int32_t>(T);
+  a.units = T * (T + 1) / 2;
+  a.sub_tile = p.j_tile;
+  a.stages = p.stages;
+  a.eps2 = eps2;
+  a.pos = reinterpret_cast<const float4*>(pos_mass);
+  a.acc_out = acc_out;
+  a.status = d->status;
+  a.wait_ns = g_wait_ns.load();
+  const int64_t slots = static_cast<int64_t>(p.ctas_per_sm > 0 ? std::min(p.ctas_per_sm, occ) : occ) * d->sms;
+  const int grid = static_cast<int>(std::min<int64_t>(slots, a.units));
+  char *ctrl = nullptr, *data = nullptr;
+  if ((st = library_workspace(s, kCtrlBytes, static_cast<size_t>(T) * a.n_pad * 16, &ctrl, &data)) != CN_OK)
+    return st;
+  a.slots = reinterpret_cast<float4*>(data);
+  if (inject("launch")) return fail(CN_ERR_CUDA, "kernel launch: injected launch failure");
+  e = cn::launch_sym(a, guard ? 1 : p.k, guard, p.threads, grid, smem, s);
+  return e == cudaSuccess ? CN_OK : fail_cuda(e, "symmetric kernel launch");
+}
+
+cn_status run_batched(const cn_batch_plan* plan, const float* pos_i, const float* pos_j, float* acc_out,
+                      float* pot_out, void* ws, size_t ws_bytes, cudaStream_t s) {
   if (!plan) return fail(CN_ERR_INVALID_ARG, "plan is NULL");
   cn_status st;
-  if ((st = check_records(pos_mass, plan->n_total, "pos_mass")) != CN_OK) return st;
+  if ((st = check_records(pos_i, plan->n_total, "pos_i")) != CN_OK) return st;
+  if ((st = check_records(pos_j, plan->n_j_total, "pos_mass_j")) != CN_OK) return st;
   if (plan->n_total > 0 && !acc_out) return fail(CN_ERR_INVALID_ARG, "acc_out is NULL");
   if ((acc_out && !aligned(acc_out, 4)) || (pot_out && !aligned(pot_out, 4)))
     return fail(CN_ERR_MISALIGNED, "outputs must be 4-byte aligned");
   if (pot_out && !plan->pot) return fail(CN_ERR_INVALID_ARG, "plan was created without the potential form");
-  const size_t n = static_cast<size_t>(plan->n_total);
-  if (overlaps(acc_out, n * 12, pos_mass, n * 16) || overlaps(pot_out, n * 4, pos_mass, n * 16) ||
+  const size_t n = static_cast<size_t>(plan->n_total), nj = static_cast<size_t>(plan->n_j_total);
+  if (overlaps(acc_out, n * 12, pos_i, n * 16) || overlaps(pot_out, n * 4, pos_i, n * 16) ||
+      overlaps(acc_out, n * 12, pos_j, nj * 16) || overlaps(pot_out, n * 4, pos_j, nj * 16) ||
       overlaps(acc_out, n * 12, pot_out, n * 4))
     return fail(CN_ERR_INVALID_ARG, "outputs overlap inputs or each other");
   int dev = 0;
   DeviceInfo* d = nullptr;
   if ((st = current_device(&dev, &d)) != CN_OK) return st;
   if (dev != plan->dev) return fail(CN_ERR_INVALID_ARG, "plan was built on another device");
-  if (plan->units == 0) {
-    cudaError_t e;
+  cudaError_t e;
+  if (plan->units == 0 || plan->zero_first) {
     if (n && (e = cudaMemsetAsync(acc_out, 0, n * 12, s)) != cudaSuccess) return fail_cuda(e, "cudaMemsetAsync");
     if (n && pot_out && (e = cudaMemsetAsync(pot_out, 0, n * 4, s)) != cudaSuccess)
       return fail_cuda(e, "cudaMemsetAsync");
-    return CN_OK;
+    if (plan->units == 0) return CN_OK;
   }
   Geometry g;
   g.units = plan->units;
@@ -624,66 +691,70 @@ cn_status run_batched(const cn_batch_plan* plan, const float* pos_mass, float* a
   char *ctrl = nullptr, *data = nullptr;
   if ((st = launch_workspace(s, g, ws, ws_bytes, ws == nullptr, &ctrl, &data)) != CN_OK) return st;
   PairArgs a = base_args(ctrl, data, g, plan->plan, d->status);
-  a.pos_i = reinterpret_cast<const float4*>(pos_mass);
-  a.pos_j = reinterpret_cast<const float4*>(pos_mass);
+  a.pos_i = reinterpret_cast<const float4*>(pos_i);
+  a.pos_j = reinterpret_cast<const float4*>(pos_j);
   a.acc_out = acc_out;
   a.pot_out = pot_out;
   a.tiles = plan->d_tiles;
   a.n_i = plan->n_total;
-  a.n_j = plan->n_total;
+  a.n_j = plan->n_j_total;
   if (inject("launch")) return fail(CN_ERR_CUDA, "kernel launch: injected launch failure");
-  cudaError_t e = cn::launch_f32(a, plan->plan, plan->pot, plan->guard, true, plan->grid, s);
+  e = cn::launch_f32(a, plan->plan, plan->pot, plan->guard, true, plan->grid, s);
   if (e != cudaSuccess) return fail_cuda(e, "batched pair kernel launch");
   return CN_OK;
 }
 
-cn_status build_batch_plan(int32_t n_clusters, const int64_t* offsets, const float* eps2, const cn_tune* tune,
-                           int with_pot, cn_batch_plan** out) {
-  if (!out) return fail(CN_ERR_INVALID_ARG, "plan_out is NULL");
-  *out = nullptr;
-  if (n_clusters < 0 || (n_clusters > 0 && (!offsets || !eps2)))
-    return fail(CN_ERR_INVALID_ARG, "n_clusters < 0 or NULL offsets/eps2");
-  if (n_clusters > 0 && offsets[0] != 0) return fail(CN_ERR_INVALID_ARG, "offsets[0] must be 0");
-  bool guard = false;
+// One group of the work: i-particles [i_begin, i_begin + ni) against the j
+// records [j_begin, j_begin + nj) with softening eps2.
+struct Group {
+  int64_t i_begin, ni, j_begin, nj;
+  float eps2;
+};
+
+// Builds the (group, i-tile, j-tile) unit table of a plan and uploads it.
+cn_status build_group_plan(const std::vector<Group>& groups, bool lists, int64_t n_i_total, int64_t n_j_total,
+                           const cn_tune* tune, int with_pot, cn_batch_plan** out) {
+  bool guard = false, zero_first = false;
   double pairs = 0.0;
-  for (int32_t c = 0; c < n_clusters; ++c) {
-    if (offsets[c + 1] < offsets[c]) return fail(CN_ERR_INVALID_ARG, "offsets must be non-decreasing");
-    cn_status st = check_eps2(eps2[c]);
+  for (const Group& gr : groups) {
+    cn_status st = check_eps2(gr.eps2);
     if (st != CN_OK) return st;
-    const int64_t nc = offsets[c + 1] - offsets[c];
-    if (nc > 0 && needs_guard(eps2[c])) guard = true;
-    pairs += static_cast<double>(nc) * static_cast<double>(nc);
+    if (gr.ni > 0 && gr.nj > 0 && needs_guard(gr.eps2)) guard = true;
+    if (gr.ni > 0 && gr.nj == 0) zero_first = true;
+    pairs += static_cast<double>(gr.ni) * static_cast<double>(gr.nj);
   }
   int dev = 0;
   DeviceInfo* d = nullptr;
   cn_status st = current_device(&dev, &d);
   if (st != CN_OK) return st;
-  const int64_t n_total = n_clusters > 0 ? offsets[n_clusters] : 0;
   const int variant = with_pot ? cn::kBatchedPot : cn::kBatched;
   Plan p;
-  if ((st = resolve_plan(dev, variant, n_clusters, n_total, guard, tune, &p)) != CN_OK) return st;
-  // tiles in order of decreasing cluster size (largest work first for the dynamic queue)
-  std::vector<int32_t> order(static_cast<size_t>(n_clusters));
-  for (int32_t c = 0; c < n_clusters; ++c) order[c] = c;
-  std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
-    return offsets[x + 1] - offsets[x] > offsets[y + 1] - offsets[y];
+  if ((st = resolve_plan(dev, variant, static_cast<int64_t>(groups.size()), n_i_total, guard, tune, &p)) != CN_OK)
+    return st;
+  if (p.j_lanes > 1) p.j_lanes = 1;  // the batched kernels hold whole i-particles per lane
+  // tiles in order of decreasing work (largest first for the dynamic queue)
+  std::vector<size_t> order(groups.size());
+  for (size_t c = 0; c < groups.size(); ++c) order[c] = c;
+  std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) {
+    return groups[x].ni * groups[x].nj > groups[y].ni * groups[y].nj;
   });
   std::vector<cn::TileDesc> tiles;
   int64_t units = 0;
   const int it = p.i_tile();
-  for (int32_t c : order) {
-    const int64_t nc = offsets[c + 1] - offsets[c];
-    if (nc == 0) continue;
-    const int64_t njt = ceil_div(nc, p.j_tile);
-    for (int64_t i0 = 0; i0 < nc; i0 += it) {
+  for (size_t c : order) {
+    const Group& gr = groups[c];
+    if (gr.ni == 0 || gr.nj == 0) continue;
+    const int64_t njt = ceil_div(gr.nj, p.j_tile);
+    if (njt > INT32_MAX) return fail(CN_ERR_INVALID_ARG, "a j set is too large");
+    for (int64_t i0 = 0; i0 < gr.ni; i0 += it) {
       cn::TileDesc t{};
-      t.i0 = offsets[c] + i0;
-      t.j0 = offsets[c];
-      t.nj = nc;
+      t.i0 = gr.i_begin + i0;
+      t.j0 = gr.j_begin;
+      t.nj = gr.nj;
       t.unit0 = units;
-      t.ni = static_cast<int32_t>(std::min<int64_t>(it, nc - i0));
+      t.ni = static_cast<int32_t>(std::min<int64_t>(it, gr.ni - i0));
       t.njt = static_cast<int32_t>(njt);
-      t.eps2 = eps2[c];
+      t.eps2 = gr.eps2;
       tiles.push_back(t);
       units += njt;
     }
@@ -694,8 +765,11 @@ cn_status build_batch_plan(int32_t n_clusters, const int64_t* offsets, const flo
     return st;
   auto* plan = new cn_batch_plan();
   plan->dev = dev;
-  plan->n_clusters = n_clusters;
-  plan->n_total = n_total;
+  plan->lists = lists;
+  plan->zero_first = zero_first;
+  plan->n_clusters = static_cast<int32_t>(groups.size());
+  plan->n_total = n_i_total;
+  plan->n_j_total = n_j_total;
   plan->pairs = pairs;
   plan->plan = p;
   plan->guard = guard;
@@ -723,6 +797,42 @@ cn_status build_batch_plan(int32_t n_clusters, const int64_t* offsets, const flo
   }
   *out = plan;
   return CN_OK;
+}
+
+cn_status build_batch_plan(int32_t n_clusters, const int64_t* offsets, const float* eps2, const cn_tune* tune,
+                           int with_pot, cn_batch_plan** out) {
+  if (!out) return fail(CN_ERR_INVALID_ARG, "plan_out is NULL");
+  *out = nullptr;
+  if (n_clusters < 0 || (n_clusters > 0 && (!offsets || !eps2)))
+    return fail(CN_ERR_INVALID_ARG, "n_clusters < 0 or NULL offsets/eps2");
+  if (n_clusters > 0 && offsets[0] != 0) return fail(CN_ERR_INVALID_ARG, "offsets[0] must be 0");
+  std::vector<Group> groups(static_cast<size_t>(n_clusters));
+  for (int32_t c = 0; c < n_clusters; ++c) {
+    if (offsets[c + 1] < offsets[c]) return fail(CN_ERR_INVALID_ARG, "offsets must be non-decreasing");
+    const int64_t nc = offsets[c + 1] - offsets[c];
+    groups[c] = Group{offsets[c], nc, offsets[c], nc, eps2[c]};
+  }
+  const int64_t n_total = n_clusters > 0 ? offsets[n_clusters] : 0;
+  return build_group_plan(groups, false, n_total, n_total, tune, with_pot, out);
+}
+
+cn_status build_list_plan(int32_t n_groups, const int64_t* i_offsets, const int64_t* j_begin, const int64_t* j_count,
+                          const float* eps2, const cn_tune* tune, int with_pot, cn_batch_plan** out) {
+  if (!out) return fail(CN_ERR_INVALID_ARG, "plan_out is NULL");
+  *out = nullptr;
+  if (n_groups < 0 || (n_groups > 0 && (!i_offsets || !j_begin || !j_count || !eps2)))
+    return fail(CN_ERR_INVALID_ARG, "n_groups < 0 or a NULL array");
+  if (n_groups > 0 && i_offsets[0] != 0) return fail(CN_ERR_INVALID_ARG, "i_offsets[0] must be 0");
+  std::vector<Group> groups(static_cast<size_t>(n_groups));
+  int64_t n_j_total = 0;
+  for (int32_t c = 0; c < n_groups; ++c) {
+    if (i_offsets[c + 1] < i_offsets[c]) return fail(CN_ERR_INVALID_ARG, "i_offsets must be non-decreasing");
+    if (j_begin[c] < 0 || j_count[c] < 0) return fail(CN_ERR_INVALID_ARG, "negative list begin or count");
+    groups[c] = Group{i_offsets[c], i_offsets[c + 1] - i_offsets[c], j_begin[c], j_count[c], eps2[c]};
+    if (j_count[c] > 0) n_j_total = std::max(n_j_total, j_begin[c] + j_count[c]);
+  }
+  const int64_t n_i_total = n_groups > 0 ? i_offsets[n_groups] : 0;
+  return build_group_plan(groups, true, n_i_total, n_j_total, tune, with_pot, out);
 }
 
 // Host staging buffers of cn_force_host, per (device, stream).
@@ -860,11 +970,27 @@ cn_status cn_batch_plan_info(const cn_batch_plan* plan, int64_t* n_total, double
 
 cn_status cn_force_batched(const cn_batch_plan* plan, const float* pos_mass, float* acc_out, float* pot_out,
                            void* workspace, size_t ws_bytes, cn_stream stream) {
-  return run_batched(plan, pos_mass, acc_out, pot_out, workspace, ws_bytes, reinterpret_cast<cudaStream_t>(stream));
+  if (plan && plan->lists) return fail(CN_ERR_INVALID_ARG, "an interaction-list plan runs with cn_force_lists");
+  return run_batched(plan, pos_mass, pos_mass, acc_out, pot_out, workspace, ws_bytes,
+                     reinterpret_cast<cudaStream_t>(stream));
 }
 
-cn_status cn_batch_plan_capture(cn_batch_plan* plan, const float* pos_mass, float* acc_out, float* pot_out,
-                                void* workspace, size_t ws_bytes, cn_stream stream) {
+cn_status cn_list_plan_create(int32_t n_groups, const int64_t* i_offsets_host, const int64_t* j_begin_host,
+                              const int64_t* j_count_host, const float* eps2_host, const cn_tune* tune,
+                              int with_potential, cn_batch_plan** plan_out) {
+  return build_list_plan(n_groups, i_offsets_host, j_begin_host, j_count_host, eps2_host, tune, with_potential,
+                         plan_out);
+}
+
+cn_status cn_force_lists(const cn_batch_plan* plan, const float* pos_i, const float* pos_mass_j, float* acc_out,
+                         float* pot_out, void* workspace, size_t ws_bytes, cn_stream stream) {
+  if (plan && !plan->lists) return fail(CN_ERR_INVALID_ARG, "a cluster plan runs with cn_force_batched");
+  return run_batched(plan, pos_i, pos_mass_j, acc_out, pot_out, workspace, ws_bytes,
+                     reinterpret_cast<cudaStream_t>(stream));
+}
+
+cn_status capture_plan(cn_batch_plan* plan, const float* pos_i, const float* pos_j, float* acc_out, float* pot_out,
+                       void* workspace, size_t ws_bytes, cn_stream stream) {
   if (!plan) return fail(CN_ERR_INVALID_ARG, "plan is NULL");
   auto s = reinterpret_cast<cudaStream_t>(stream);
   if (!s) return fail(CN_ERR_INVALID_ARG, "graph capture needs a non-default stream");
@@ -872,7 +998,7 @@ cn_status cn_batch_plan_capture(cn_batch_plan* plan, const float* pos_mass, floa
   if (inject("capture")) return fail(CN_ERR_CUDA, "cudaStreamBeginCapture: injected capture failure");
   cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return fail_cuda(e, "cudaStreamBeginCapture");
-  cn_status st = run_batched(plan, pos_mass, acc_out, pot_out, workspace, ws_bytes, s);
+  cn_status st = run_batched(plan, pos_i, pos_j, acc_out, pot_out, workspace, ws_bytes, s);
   cudaGraph_t graph = nullptr;
   e = cudaStreamEndCapture(s, &graph);
   if (st != CN_OK) {
@@ -891,6 +1017,18 @@ cn_status cn_batch_plan_capture(cn_batch_plan* plan, const float* pos_mass, floa
   plan->graph = graph;
   plan->exec = exec;
   return CN_OK;
+}
+
+cn_status cn_batch_plan_capture(cn_batch_plan* plan, const float* pos_mass, float* acc_out, float* pot_out,
+                                void* workspace, size_t ws_bytes, cn_stream stream) {
+  if (plan && plan->lists) return fail(CN_ERR_INVALID_ARG, "an interaction-list plan is captured with cn_list_plan_capture");
+  return capture_plan(plan, pos_mass, pos_mass, acc_out, pot_out, workspace, ws_bytes, stream);
+}
+
+cn_status cn_list_plan_capture(cn_batch_plan* plan, const float* pos_i, const float* pos_mass_j, float* acc_out,
+                               float* pot_out, void* workspace, size_t ws_bytes, cn_stream stream) {
+  if (plan && !plan->lists) return fail(CN_ERR_INVALID_ARG, "a cluster plan is captured with cn_batch_plan_capture");
+  return capture_plan(plan, pos_i, pos_mass_j, acc_out, pot_out, workspace, ws_bytes, stream);
 }
 
 cn_status cn_batch_plan_launch(const cn_batch_plan* plan, cn_stream stream) {
@@ -949,6 +1087,10 @@ cn_status cn_force_jerk(int64_t n_i, const float* pos_i, const float* vel_i, int
                         cn_stream stream) {
   return jerk_common(n_i, pos_i, vel_i, n_j, pos_mass_j, vel_j, eps2, acc_out, jerk_out, pot_out,
                      reinterpret_cast<cudaStream_t>(stream));
+}
+
+cn_status cn_force_symmetric(int64_t n, const float* pos_mass, float eps2, float* acc_out, cn_stream stream) {
+  return symmetric_common(n, pos_mass, eps2, acc_out, reinterpret_cast<cudaStream_t>(stream));
 }
 
 cn_status cn_potential_energy(int64_t n, const float* pos_mass, const float* pot, double* w_out, cn_stream stream) {
@@ -1021,7 +1163,7 @@ cn_status cn_force_host_f64(const double* xj, const double* mj, const double* xi
 }
 
 cn_status cn_tune_get(int variant, int64_t n_i, int64_t n_j, cn_tune* out) {
-  if (!out || variant < cn::kF32 || variant > cn::kJerkPot || n_i < 0 || n_j < 0)
+  if (!out || variant < cn::kF32 || variant > cn::kSym || n_i < 0 || n_j < 0)
     return fail(CN_ERR_INVALID_ARG, "bad variant, size or NULL output");
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -1040,7 +1182,7 @@ cn_status cn_tune_get(int variant, int64_t n_i, int64_t n_j, cn_tune* out) {
 }
 
 cn_status cn_tune_set(int variant, int64_t n_i, int64_t n_j, const cn_tune* tune) {
-  if (variant < cn::kF32 || variant > cn::kJerkPot || n_i < 0 || n_j < 0)
+  if (variant < cn::kF32 || variant > cn::kSym || n_i < 0 || n_j < 0)
     return fail(CN_ERR_INVALID_ARG, "bad variant or size");
   if (tune) {
     cn_status st = check_tune(variant, *tune);
@@ -1202,10 +1344,10 @@ cn_status cn_autotune_batched(int32_t n_clusters, const int64_t* offsets_host, c
             result = st;
             break;
           }
-          st = run_batched(plan, pos_mass, acc_out, pot_out, nullptr, 0, s);
+          st = run_batched(plan, pos_mass, pos_mass, acc_out, pot_out, nullptr, 0, s);
           if (st == CN_OK) {
             cudaEventRecord(e0, s);
-            for (int r = 0; r < reps; ++r) run_batched(plan, pos_mass, acc_out, pot_out, nullptr, 0, s);
+            for (int r = 0; r < reps; ++r) run_batched(plan, pos_mass, pos_mass, acc_out, pot_out, nullptr, 0, s);
             cudaEventRecord(e1, s);
             if (cudaEventSynchronize(e1) == cudaSuccess) {
               float ms = 0.f;

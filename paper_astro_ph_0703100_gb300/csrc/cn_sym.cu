@@ -1,0 +1,324 @@
+// Symmetric (Newton's third law) evaluation for an i set equal to the j set:
+// every unordered pair is evaluated once and its term is added to both
+// particles. The paper's kernel evaluates every ordered pair; this form does
+// about half the pair work.
+//
+// The particles are cut into square tiles of B = threads x K. A unit is a
+// tile pair (I, J) with I <= J. For I < J the CTA holds tile I in registers
+// (K particles per thread) and streams tile J through a shared-memory ring
+// (bulk copies, mbarriers). Per j record each lane adds m_j r^-3 d to its K
+// i-particles and collects -m_i r^-3 d over them; the collected j-side terms
+// of a batch of 8 j records are summed across the warp by a reduce-scatter
+// (each lane visits the batch in an order permuted by its lane bits, so
+// every exchange reads a fixed register: 27 shuffles and 27 adds per batch)
+// and each warp's sums go to its own shared-memory row; at the end of the
+// unit the rows are added in warp order. Diagonal units (I = J) use the
+// one-sided loop. Every unit writes its i-side sums to slot (I, J) and its
+// j-side sums to slot (J, I) of a [tiles][n_pad] float4 array; a second
+// kernel adds the slots of each particle in partner order in FP64 - a
+// deterministic result with no atomics on data.
+#include "cn_device.cuh"
+#include "cn_kernels.h"
+
+namespace cn {
+
+__device__ __forceinline__ void sym_fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+namespace {
+
+constexpr int kSymBatch = 8;  // j records per reduce-scatter batch
+
+// Unit u of the upper triangle (row-major: (0,0), (0,1), ..., (0,T-1), (1,1), ...).
+__device__ __forceinline__ void unit_tiles(int64_t u, int32_t T, int32_t* I, int32_t* J) {
+  // row I starts at I*T - I*(I-1)/2; find the last row start <= u
+  int32_t lo = 0, hi = T - 1;
+  while (lo < hi) {
+    const int32_t mid = (lo + hi + 1) >> 1;
+    const int64_t start = static_cast<int64_t>(mid) * T - static_cast<int64_t>(mid) * (mid - 1) / 2;
+    if (start <= u)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  const int64_t start = static_cast<int64_t>(lo) * T - static_cast<int64_t>(lo) * (lo - 1) / 2;
+  *I = lo;
+  *J = lo + static_cast<int32_t>(u - start);
+}
+
+template <int K, bool GUARD>
+__global__ void __launch_bounds__(256, 1) sym_kernel(const __grid_constant__ SymArgs a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int NT = blockDim.x;
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int warp = tid >> 5;
+  const int NW = NT >> 5;
+  const int B = NT * K;          // particles per tile
+  const int JS = a.sub_tile;     // j records per ring stage (divides B, multiple of 8)
+  const int S = a.stages;
+  const int subs = B / JS;       // ring stages per unit
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem);
+  uint64_t* empty = full + S;
+  volatile int* ctl = reinterpret_cast<volatile int*>(smem + 16 * S);  // [0] abort
+  float4* ring = reinterpret_cast<float4*>(smem + 256);
+  float* jrows = reinterpret_cast<float*>(ring + static_cast<size_t>(S) * JS);  // [NW][B][3]
+
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], NW);
+    }
+    ctl[0] = 0;
+    mbar_init_fence();
+  }
+  __syncthreads();
+
+  const int64_t U = a.units;
+  const int64_t G = gridDim.x;
+  const int64_t ub = (static_cast<int64_t>(blockIdx.x) * U) / G;
+  const int64_t ue = (static_cast<int64_t>(blockIdx.x + 1) * U) / G;
+  const uint32_t n_loads = static_cast<uint32_t>((ue - ub) * subs);
+  const uint32_t D = S > 2 ? static_cast<uint32_t>(S - 2) : static_cast<uint32_t>(S - 1);
+  uint32_t issued = 0, consumed = 0;
+  // lane permutation of a batch: lane visits j = t ^ perm
+  const int perm = (((lane >> 4) & 1) << 2) | (((lane >> 3) & 1) << 1) | ((lane >> 2) & 1);
+
+  float xi[K][3], mi[K], acc[K][3];
+  int32_t cur_I = -1;
+  for (int64_t u = ub; u < ue; ++u) {
+    int32_t I, J;
+    unit_tiles(u, a.n_tiles, &I, &J);
+    const bool diag = (I == J);
+    if (I != cur_I) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const int64_t p = static_cast<int64_t>(I) * B + k * NT + tid;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (p < a.n) v = __ldg(a.pos + p);
+        xi[k][0] = v.x;
+        xi[k][1] = v.y;
+        xi[k][2] = v.z;
+        mi[k] = v.w;
+      }
+      cur_I = I;
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[k][0] = acc[k][1] = acc[k][2] = 0.f;
+    if (!diag)
+      for (int e = tid; e < NW * B * 3; e += NT) jrows[e] = 0.f;
+    __syncthreads();
+    for (int sub = 0; sub < subs; ++sub) {
+      // ---- producer: keep D loads ahead (thread 0)
+      if (tid == 0) {
+        while (!ctl[0] && issued < n_loads && issued <= consumed + D) {
+          const int slot = static_cast<int>(issued % S);
+          if (issued >= static_cast<uint32_t>(S) &&
+              !mbar_wait(&empty[slot], ((issued / S) - 1) & 1u, a.wait_ns)) {
+            set_status(a.status, kStatusTimeoutEmpty);
+            ctl[0] = 1;
+            break;
+          }
+          const int64_t lu = ub + issued / subs;
+          const int ls = static_cast<int>(issued % subs);
+          int32_t LI, LJ;
+          unit_tiles(lu, a.n_tiles, &LI, &LJ);
+          const int64_t first = static_cast<int64_t>(LJ) * B + static_cast<int64_t>(ls) * JS;
+          const int64_t left = a.n - first;
+          const int cnt = static_cast<int>(left <= 0 ? 0 : (left < JS ? left : JS));
+          float4* dst = ring + static_cast<size_t>(slot) * JS;
+          for (int z = cnt; z < JS; ++z) dst[z] = make_float4(0.f, 0.f, 0.f, 0.f);
+          sym_fence_proxy_async();
+          mbar_arrive_expect_tx(&full[slot], static_cast<uint32_t>(cnt) * 16u);
+          if (cnt > 0) bulk_copy_g2s(dst, a.pos + first, static_cast<uint32_t>(cnt) * 16u, &full[slot]);
+          ++issued;
+        }
+      }
+      // ---- consumer
+      const int slot = static_cast<int>(consumed % S);
+      bool live = !ctl[0];
+      if (live && !mbar_wait(&full[slot], (consumed / S) & 1u, a.wait_ns)) {
+        set_status(a.status, kStatusTimeoutFull);
+        ctl[0] = 1;
+        live = false;
+      }
+      live = __all_sync(0xffffffffu, live);
+      if (live) {
+        const float4* js = ring + static_cast<size_t>(slot) * JS;
+        const float eps2 = a.eps2;
+        if (diag) {
+#pragma unroll 1
+          for (int j = 0; j < JS; j += 8) {
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj) {
+              const float4 pj = js[j + jj];
+#pragma unroll
+              for (int k = 0; k < K; ++k) {
+                const float dx = pj.x - xi[k][0], dy = pj.y - xi[k][1], dz = pj.z - xi[k][2];
+                const float s = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+                float r = rsqrt_mufu(s);
+                if constexpr (GUARD) r = (s > 0.f) ? r : 0.f;
+                const float q = (pj.w * r) * (r * r);
+                acc[k][0] = fmaf(q, dx, acc[k][0]);
+                acc[k][1] = fmaf(q, dy, acc[k][1]);
+                acc[k][2] = fmaf(q, dz, acc[k][2]);
+              }
+            }
+          }
+        } else {
+          float* myrow = jrows + static_cast<size_t>(warp) * B * 3;
+          const int jbase = sub * JS;
+#pragma unroll 1
+          for (int j = 0; j < JS; j += kSymBatch) {
+            float c[kSymBatch][3];
+#pragma unroll
+            for (int t = 0; t < kSymBatch; ++t) {
+              const float4 pj = js[j + (t ^ perm)];
+              float cx = 0.f, cy = 0.f, cz = 0.f;
+#pragma unroll
+              for (int k = 0; k < K; ++k) {
+                const float dx = pj.x - xi[k][0], dy = pj.y - xi[k][1], dz = pj.z - xi[k][2];
+                const float s = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+                float r = rsqrt_mufu(s);
+                if constexpr (GUARD) r = (s > 0.f) ? r : 0.f;
+                const float r3 = r * (r * r);
+                const float qi = pj.w * r3;  // m_j r^-3 onto particle i
+                const float qj = mi[k] * r3;  // m_i r^-3 onto particle j (opposite sign)
+                acc[k][0] = fmaf(qi, dx, acc[k][0]);
+                acc[k][1] = fmaf(qi, dy, acc[k][1]);
+                acc[k][2] = fmaf(qi, dz, acc[k][2]);
+                cx = fmaf(-qj, dx, cx);
+                cy = fmaf(-qj, dy, cy);
+                cz = fmaf(-qj, dz, cz);
+              }
+              c[t][0] = cx;
+              c[t][1] = cy;
+              c[t][2] = cz;
+            }
+            // reduce-scatter over the warp: after the three halving steps
+            // lane l holds, in c[0], the sum over the 8 lanes that share
+            // l & 3 for j = perm(l); two butterfly steps complete the sum
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+#pragma unroll
+              for (int d = 0; d < 3; ++d) c[t][d] += __shfl_xor_sync(0xffffffffu, c[t + 4][d], 16);
+#pragma unroll
+            for (int t = 0; t < 2; ++t)
+#pragma unroll
+              for (int d = 0; d < 3; ++d) c[t][d] += __shfl_xor_sync(0xffffffffu, c[t + 2][d], 8);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) c[0][d] += __shfl_xor_sync(0xffffffffu, c[1][d], 4);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+              c[0][d] += __shfl_xor_sync(0xffffffffu, c[0][d], 2);
+              c[0][d] += __shfl_xor_sync(0xffffffffu, c[0][d], 1);
+            }
+            if ((lane & 3) == 0) {
+              float* dst = myrow + static_cast<size_t>(jbase + j + perm) * 3;
+              dst[0] += c[0][0];
+              dst[1] += c[0][1];
+              dst[2] += c[0][2];
+            }
+          }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[slot]);
+      }
+      ++consumed;
+    }
+    // ---- end of the unit: i-side sums to slot (I, J), j-side to slot (J, I)
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int64_t p = static_cast<int64_t>(I) * B + k * NT + tid;
+      a.slots[static_cast<size_t>(J) * a.n_pad + p] = make_float4(acc[k][0], acc[k][1], acc[k][2], 0.f);
+    }
+    if (!diag) {
+      for (int jl = tid; jl < B; jl += NT) {
+        float sx = 0.f, sy = 0.f, sz = 0.f;
+        for (int w = 0; w < NW; ++w) {
+          const float* r = jrows + (static_cast<size_t>(w) * B + jl) * 3;
+          sx += r[0];
+          sy += r[1];
+          sz += r[2];
+        }
+        const int64_t p = static_cast<int64_t>(J) * B + jl;
+        a.slots[static_cast<size_t>(I) * a.n_pad + p] = make_float4(sx, sy, sz, 0.f);
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0 && ctl[0]) {
+    for (uint32_t c = issued > static_cast<uint32_t>(S) ? issued - S : 0u; c < issued; ++c) {
+      if (!mbar_wait(&full[c % S], (c / S) & 1u, a.wait_ns)) {
+        set_status(a.status, kStatusTimeoutDrain);
+        break;
+      }
+    }
+  }
+}
+
+// acc[p] = sum over partner tiles Q (in order) of slots[Q][p], in FP64.
+__global__ void sym_merge_kernel(const float4* __restrict__ slots, int64_t n, int64_t n_pad, int32_t n_tiles,
+                                 float* __restrict__ acc) {
+  const int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (p >= n) return;
+  double sx = 0.0, sy = 0.0, sz = 0.0;
+  for (int32_t q = 0; q < n_tiles; ++q) {
+    const float4 v = __ldcs(slots + static_cast<size_t>(q) * n_pad + p);
+    sx += v.x;
+    sy += v.y;
+    sz += v.z;
+  }
+  acc[3 * p + 0] = static_cast<float>(sx);
+  acc[3 * p + 1] = static_cast<float>(sy);
+  acc[3 * p + 2] = static_cast<float>(sz);
+}
+
+template <int K, bool GUARD>
+const void* sym_fn() {
+  return reinterpret_cast<const void*>(&sym_kernel<K, GUARD>);
+}
+
+const void* sym_select(int k, bool guard) {
+  if (guard) return k == 1 ? sym_fn<1, true>() : nullptr;
+  switch (k) {
+    case 1: return sym_fn<1, false>();
+    case 2: return sym_fn<2, false>();
+    case 4: return sym_fn<4, false>();
+    case 8: return sym_fn<8, false>();
+    default: return nullptr;
+  }
+}
+
+}  // namespace
+
+size_t sym_smem_bytes(int threads, int k, int sub_tile, int stages) {
+  const size_t b = static_cast<size_t>(threads) * k;
+  return 256 + static_cast<size_t>(stages) * sub_tile * 16 + (threads / 32) * b * 3 * sizeof(float);
+}
+
+cudaError_t occupancy_sym(int k, bool guard, int threads, size_t smem, int* ctas) {
+  const void* f = sym_select(k, guard);
+  if (!f) return cudaErrorInvalidValue;
+  cudaError_t e = prepare_kernel(f, smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, f, threads, smem);
+}
+
+cudaError_t launch_sym(const SymArgs& a, int k, bool guard, int threads, int grid, size_t smem, cudaStream_t s) {
+  const void* f = sym_select(k, guard);
+  if (!f) return cudaErrorInvalidValue;
+  cudaError_t e = prepare_kernel(f, smem);
+  if (e != cudaSuccess) return e;
+  void* args[] = {const_cast<SymArgs*>(&a)};
+  e = cudaLaunchKernel(f, dim3(grid), dim3(threads), args, smem, s);
+  if (e != cudaSuccess) return e;
+  const int mt = 256;
+  const int64_t mb = (a.n + mt - 1) / mt;
+  sym_merge_kernel<<<static_cast<unsigned>(mb), mt, 0, s>>>(a.slots, a.n, a.n_pad, a.n_tiles, a.acc_out);
+  return cudaGetLastError();
+}
+
+}  // namespace cn

@@ -33,6 +33,7 @@ __all__ = [
     "sample_rows",
     "plummer_eps",
     "plummer_velocities",
+    "interaction_lists",
 ]
 
 
@@ -164,3 +165,33 @@ def plummer_velocities(n: int, seed: int, scale: float = 0.5) -> np.ndarray:
     out = np.zeros((n, 4), dtype=np.float32)
     out[:, :3] = v.astype(np.float32)
     return out
+
+
+def interaction_lists(n_particles: int, group_size: int, list_size: int, seed: int, n_pseudo_frac: float = 0.5):
+    """A synthetic stand-in for the group / interaction-list structure a
+    modified tree code hands to the O(N^2) engine.
+
+    Particles of a Plummer sphere are ordered by their x coordinate and cut
+    into consecutive groups of ``group_size``; each group gets a list of
+    ``list_size`` j records: a seeded random subset of the particles plus
+    "pseudo-particles" (records at random positions carrying larger masses,
+    standing in for tree nodes). Returns ``(pos_i, i_offsets, lists, j_begin,
+    j_count)`` with FP32 records; lists of consecutive groups are stored back
+    to back. No force arithmetic happens here.
+    """
+    p = plummer(n_particles, seed)
+    pos_i = p[np.argsort(p[:, 0], kind="stable")]
+    n_groups = -(-n_particles // group_size)
+    i_offsets = np.minimum(np.arange(n_groups + 1, dtype=np.int64) * group_size, n_particles)
+    rng = _rng(seed + 1)
+    n_pseudo = int(list_size * n_pseudo_frac)
+    n_real = list_size - n_pseudo
+    lists = np.empty((n_groups * list_size, 4), dtype=np.float32)
+    for g in range(n_groups):
+        blk = lists[g * list_size:(g + 1) * list_size]
+        blk[:n_real] = pos_i[rng.choice(n_particles, size=n_real, replace=False)]
+        blk[n_real:, :3] = (4.0 * rng.standard_normal((n_pseudo, 3))).astype(np.float32)
+        blk[n_real:, 3] = (rng.uniform(1.0, 64.0, n_pseudo) / n_particles).astype(np.float32)
+    j_begin = np.arange(n_groups, dtype=np.int64) * list_size
+    j_count = np.full(n_groups, list_size, dtype=np.int64)
+    return pos_i, i_offsets, lists, j_begin, j_count

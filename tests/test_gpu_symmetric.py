@@ -1,0 +1,119 @@
+"""Parity of cn_force_symmetric (each unordered pair evaluated once) with the FP64 oracle.
+
+The symmetric form computes the same accelerations as the paper's kernel
+(Eq. 1 with the i set equal to the j set), so it is held to the same
+per-particle bound E_max <= 1e-5 as the plain FP32 form. Its partial sums
+are per (tile, partner tile) in FP32, merged in FP64 in partner order, so
+repeated calls with one launch shape are bitwise equal.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from gpu_common import dev_tensor, e_max, lib, torch_cuda
+from paper_astro_ph_0703100_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+def run(cn, p, eps2):
+    torch = torch_cuda()
+    a = cn.cn_force_symmetric(dev_tensor(p), eps2)
+    torch.cuda.synchronize()
+    assert cn.cn_get_device_status() == 0
+    return a.cpu().numpy()
+
+
+TUNES = [None,
+         {"i_per_thread": 1, "threads": 64, "j_tile": 16, "stages": 2},
+         {"i_per_thread": 2, "threads": 128, "j_tile": 64, "stages": 3},
+         {"i_per_thread": 4, "threads": 128, "j_tile": 128, "stages": 1},
+         {"i_per_thread": 8, "threads": 128, "j_tile": 256, "stages": 4, "ctas_per_sm": 1},
+         {"i_per_thread": 8, "threads": 256, "j_tile": 512, "stages": 2}]
+
+
+@pytest.mark.parametrize("tune", TUNES)
+@pytest.mark.parametrize("n", [1, 2, 33, 1000, 4097])
+def test_symmetric_ragged_and_launch_shapes(n, tune):
+    cn = lib()
+    p = synth.plummer(n, 50 + n)
+    cn.cn_tune_set("symmetric", n, n, tune)
+    try:
+        a = run(cn, p, 1e-3)
+    finally:
+        cn.cn_tune_set("symmetric", n, n, None)
+    ref, _ = oracle.force(p, p, 1e-3, potential=False)
+    assert e_max(a, ref) <= TOL
+
+
+def test_symmetric_unequal_masses_many_tiles():
+    """Log-normal masses: the i-side (m_j) and j-side (m_i) weights differ per pair."""
+    cn = lib()
+    n = 20000
+    p = synth.hernquist(n, 3)
+    cn.cn_tune_set("symmetric", n, n, {"i_per_thread": 2, "threads": 64, "j_tile": 32, "stages": 4})
+    try:
+        a = run(cn, p, 1e-4)
+    finally:
+        cn.cn_tune_set("symmetric", n, n, None)
+    ref, _ = oracle.force(p, p, 1e-4, potential=False)
+    assert e_max(a, ref) <= TOL
+
+
+def test_symmetric_zero_softening_guard():
+    """eps2 = 0 takes the guarded kernel: the self pair contributes nothing."""
+    cn = lib()
+    n = 777
+    p = synth.plummer(n, 8)
+    a = run(cn, p, 0.0)
+    ref, _ = oracle.force(p, p, 0.0, potential=False)
+    assert np.all(np.isfinite(a))
+    assert e_max(a, ref) <= TOL
+
+
+def test_symmetric_deterministic_and_matches_plain_form():
+    cn = lib()
+    torch = torch_cuda()
+    n = 9000
+    p = synth.plummer(n, 12)
+    d = dev_tensor(p)
+    a1 = cn.cn_force_symmetric(d, 1e-3)
+    a2 = cn.cn_force_symmetric(d, 1e-3)
+    plain, _ = cn.cn_force(d, d, 1e-3)
+    torch.cuda.synchronize()
+    assert torch.equal(a1, a2)
+    ref, _ = oracle.force(p, p, 1e-3, potential=False)
+    assert e_max(a1.cpu().numpy(), ref) <= TOL
+    assert e_max(plain.cpu().numpy(), ref) <= TOL
+
+
+def test_symmetric_empty():
+    cn = lib()
+    torch = torch_cuda()
+    a = cn.cn_force_symmetric(torch.empty((0, 4), dtype=torch.float32, device="cuda"), 1e-3)
+    assert a.shape == (0, 3)
+
+
+def test_symmetric_rejects_j_lanes():
+    """Split-j lanes are a plain-form option: the symmetric variant refuses them."""
+    import ctypes
+
+    cn = lib()
+    t = cn.cn_tune()
+    t.i_per_thread, t.threads, t.j_tile, t.stages, t.j_lanes = 1, 128, 128, 2, 4
+    assert cn.load().cn_tune_set(9, 100, 100, ctypes.byref(t)) == 1
+
+
+def test_symmetric_plummer_131072_sampled():
+    """The headline system (N = 131072 Plummer, eps = 4 / N^(1/3)) in the default launch shape."""
+    cn = lib()
+    n = 131072
+    p = synth.plummer(n, 1)
+    eps2 = float(np.float32(synth.plummer_eps(n)) ** 2)
+    a = run(cn, p, eps2)
+    rows = synth.sample_rows(n, 512, 7)
+    ref, _ = oracle.force(p, p, eps2, rows=rows, potential=False)
+    assert e_max(a[rows], ref) <= TOL
