@@ -683,6 +683,15 @@ def run_only(args):
         out = torch.empty((n, 3), dtype=torch.float32 if args.only == "f32" else torch.float64, device=device)
         step = lambda: fn(t, t, eps2, acc_out=out)
         pairs = float(n) * n
+    elif args.only == "lists":
+        pos_i, i_off, lists, jb, jc = synth.interaction_lists(n, 256, 4096, seed=n)
+        eps2 = float(np.float32(0.01) ** 2)
+        lp = cn.ListPlan(i_off, jb, jc, eps2, tune=dict(tune) if tune else None)
+        ti, tj = torch.from_numpy(pos_i).to(device), torch.from_numpy(lists).to(device)
+        out = torch.empty((pos_i.shape[0], 3), dtype=torch.float32, device=device)
+        ws_l = lp.new_workspace(device)
+        step = lambda: lp.run(ti, tj, acc_out=out, workspace=ws_l)
+        pairs = lp.pairs
     elif args.only == "sym":
         p, eps2 = workload(n, n)
         t = torch.from_numpy(p).to(device)
@@ -784,7 +793,7 @@ def main(argv=None):
     ap.add_argument("--no-rows", action="store_true", help="skip the other workloads (C1, C2 small, C3, C4, C5)")
     ap.add_argument("--cpu-budget", type=float, default=10.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--ref-rows", type=int, default=256, help="oracle rows per step of --impl reference")
-    ap.add_argument("--only", choices=("f32", "dd", "adjoint", "batched", "jerk", "sym"),
+    ap.add_argument("--only", choices=("f32", "dd", "adjoint", "batched", "jerk", "sym", "lists"),
                     help="time one kernel family alone (profiling mode; prints its own JSON)")
     ap.add_argument("--tune", help="pinned launch shape for --only: i_per_thread,threads,j_tile,stages")
     ap.add_argument("--chunk", type=int, default=0, help="dynamic chunk size for --only batched")

@@ -234,6 +234,47 @@ bool valid_k(int variant, int k) {
 
 int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
+// Launch shape of the symmetric form from a small model of its schedule.
+// The N(N+1)/2-style triangle of T tile pairs (tile B = threads x K) is cut
+// into equal static ranges over G = min(resident slots, units) CTAs; the SM
+// holding the most CTAs sets the time, at a rate that saturates once about
+// six warps share the SM. Saturated rates are the ones measured at
+// N = 131072 (ordered pairs / s): they favour large K (fewer warp
+// reductions per pair), while small systems need small tiles to fill the
+// SMs.
+cn_tune sym_default_tune(int64_t n, int sms) {
+  struct Shape {
+    int k, threads, j_tile, stages, slots_per_sm;
+    double rate;
+  };
+  static const Shape shapes[] = {
+      {8, 256, 256, 3, 1, 3.12e12}, {8, 128, 256, 4, 3, 3.03e12}, {8, 64, 128, 4, 8, 2.90e12},
+      {4, 128, 256, 4, 3, 2.81e12}, {4, 64, 128, 4, 8, 2.56e12},  {2, 64, 64, 4, 8, 1.80e12},
+      {1, 64, 64, 4, 9, 1.10e12}};
+  cn_tune best{};
+  double best_t = 0.0;
+  for (const Shape& sh : shapes) {
+    const int64_t b = static_cast<int64_t>(sh.k) * sh.threads;
+    const int64_t T = (std::max<int64_t>(n, 1) + b - 1) / b;
+    const int64_t units = T * (T + 1) / 2;
+    const int64_t g = std::min<int64_t>(static_cast<int64_t>(sh.slots_per_sm) * sms, units);
+    const int64_t per_sm = (g + sms - 1) / sms;
+    const int64_t per_cta = (units + g - 1) / g;
+    const double warps = static_cast<double>(per_sm) * sh.threads / 32.0;
+    const double sm_rate = sh.rate / sms * std::min(1.0, warps / 6.0);
+    const double t = static_cast<double>(per_sm * per_cta) * 2.0 * static_cast<double>(b * b) / sm_rate;
+    if (best_t == 0.0 || t < best_t) {
+      best_t = t;
+      best.i_per_thread = sh.k;
+      best.threads = sh.threads;
+      best.j_tile = sh.j_tile;
+      best.stages = sh.stages;
+    }
+  }
+  best.j_lanes = 1;
+  return best;
+}
+
 cn_tune default_tune(int variant, int64_t n_i, int64_t n_j) {
   cn_tune t{};
   const int64_t n = std::max(n_i, n_j);
@@ -257,14 +298,7 @@ cn_tune default_tune(int variant, int64_t n_i, int64_t n_j) {
     t.stages = n_j <= t.j_tile ? 1 : 3;
     return t;
   }
-  if (variant == cn::kSym) {
-    // tiles of threads x K particles; j_tile is the ring stage (divides the tile)
-    t.i_per_thread = n >= 32768 ? 8 : (n >= 4096 ? 4 : 1);
-    t.threads = n >= 4096 ? 128 : 64;
-    t.j_tile = n >= 4096 ? 256 : 64;
-    t.stages = 4;
-    return t;
-  }
+  if (variant == cn::kSym) return sym_default_tune(n, 152);
   if (variant == cn::kBatched || variant == cn::kBatchedPot) {
     t.i_per_thread = 4;
     t.j_tile = 256;
@@ -310,9 +344,23 @@ bool two_records(int variant) {
   return variant == cn::kAdjoint || variant == cn::kJerk || variant == cn::kJerkPot;
 }
 
+bool registered_tune(int dev, int variant, int64_t n_i, int64_t n_j) {
+  std::lock_guard<std::mutex> lock(g_mu);
+  return g_tune.count({dev, variant, bucket(n_i), bucket(n_j)}) > 0;
+}
+
 cn_status resolve_plan(int dev, int variant, int64_t n_i, int64_t n_j, bool guard, const cn_tune* explicit_tune,
                        Plan* p) {
   cn_tune t = default_tune(variant, n_i, n_j);
+  if (variant == cn::kSym) {
+    int sms = 0;
+    {
+      std::lock_guard<std::mutex> lock(g_mu);
+      auto it = g_devices.find(dev);
+      if (it != g_devices.end()) sms = it->second.sms;
+    }
+    if (sms > 0) t = sym_default_tune(std::max(n_i, n_j), sms);
+  }
   cn_tune chosen{};
   bool have = false;
   if (explicit_tune) {
@@ -728,9 +776,33 @@ cn_status build_group_plan(const std::vector<Group>& groups, bool lists, int64_t
   cn_status st = current_device(&dev, &d);
   if (st != CN_OK) return st;
   const int variant = with_pot ? cn::kBatchedPot : cn::kBatched;
+  const int64_t key_i = static_cast<int64_t>(groups.size());
+  cn_tune fitted{};
+  if (!tune && !registered_tune(dev, variant, key_i, n_i_total)) {
+    // i-tile fitted to the group sizes: every group is cut into whole i-tiles,
+    // so a tile larger than the typical group leaves lanes idle. Among
+    // K = 4, 2, 1 particles per thread (128 threads) take the one with the
+    // least evaluated-but-padded work, weighted by the relative pair rate
+    // of each K.
+    const int ks[3] = {4, 2, 1};
+    const double rate[3] = {1.0, 0.93, 0.78};
+    double best = -1.0;
+    for (int c = 0; c < 3; ++c) {
+      const int64_t it = static_cast<int64_t>(ks[c]) * 128;
+      double padded = 0.0;
+      for (const Group& gr : groups) padded += static_cast<double>(ceil_div(gr.ni, it) * it) * static_cast<double>(gr.nj);
+      const double score = padded > 0.0 ? pairs / padded * rate[c] : rate[c];
+      if (score > best) {
+        best = score;
+        fitted = default_tune(variant, key_i, n_i_total);
+        fitted.i_per_thread = ks[c];
+        fitted.threads = 128;
+      }
+    }
+    tune = &fitted;
+  }
   Plan p;
-  if ((st = resolve_plan(dev, variant, static_cast<int64_t>(groups.size()), n_i_total, guard, tune, &p)) != CN_OK)
-    return st;
+  if ((st = resolve_plan(dev, variant, key_i, n_i_total, guard, tune, &p)) != CN_OK) return st;
   if (p.j_lanes > 1) p.j_lanes = 1;  // the batched kernels hold whole i-particles per lane
   // tiles in order of decreasing work (largest first for the dynamic queue)
   std::vector<size_t> order(groups.size());

@@ -109,6 +109,27 @@ __device__ __forceinline__ void pair_f32(const float4 pj, const float (&xi)[K][3
 }
 
 // ------------------------------------------------------------------ policies
+// The kernel below is generic over the interaction, in the way the paper's
+// generalised library kernel (Section 4.5 and the appendix's pipeline
+// descriptions) is generic over the widths of the i record, the j record
+// and the result. A policy supplies:
+//   kJRec          float4 words per j record (1: (x, y, z, m); 2: a
+//                  velocity or a weight record follows)
+//   kSlotF4        float4 words per i-particle in a split tile's partial
+//   kSums          FP64 sums per i-particle in the merge (the result width)
+//   kSplitJ        lanes of a group share one i-particle (reduce_lanes)
+//   kMinBlocks     256-thread CTAs per SM its register budget is sized for
+//   load_i         i-particle k's record(s) into registers
+//   zero, tile     clear the running sums; fold one staged j-tile into them
+//   store_final    a whole i-tile's results to the outputs
+//   store_partial  a split tile's partial to its workspace slot
+//   add_partial    one loaded partial into the FP64 merge sums
+//   store_merged   the merged sums to the outputs
+// Gravity with or without the potential (F32Policy), its compensated form
+// (DDPolicy), the gradient of L = sum_i w_i . a_i (AdjointPolicy) and the
+// force-jerk-potential pipeline (JerkPolicy) all run through the one
+// staging, scheduling and merging loop of pair_kernel.
+//
 // Plain FP32: per-tile FP32 partial folded into an FP32 running sum.
 // SPLITJ: groups of j_lanes consecutive lanes share one i-particle, lane
 // `sub` of a group taking j records sub, sub + j_lanes, ... of each tile;

@@ -47,8 +47,14 @@ __device__ __forceinline__ void unit_tiles(int64_t u, int32_t T, int32_t* I, int
   *J = lo + static_cast<int32_t>(u - start);
 }
 
-template <int K, bool GUARD>
-__global__ void __launch_bounds__(256, 1) sym_kernel(const __grid_constant__ SymArgs a) {
+// Resident CTAs per SM the register budget is sized for, by block size:
+// 64-thread blocks 8 (<= 128 registers), 128-thread blocks 3 (<= 170),
+// 256-thread blocks 1. The shared-memory rows of the j-side sums grow with
+// the tile, so larger blocks cannot hold more CTAs anyway.
+constexpr int sym_min_blocks(int nt_max) { return nt_max <= 64 ? 8 : (nt_max <= 128 ? 3 : 1); }
+
+template <int K, bool GUARD, int NTMAX>
+__global__ void __launch_bounds__(NTMAX, sym_min_blocks(NTMAX)) sym_kernel(const __grid_constant__ SymArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int NT = blockDim.x;
   const int tid = threadIdx.x;
@@ -277,17 +283,20 @@ __global__ void sym_merge_kernel(const float4* __restrict__ slots, int64_t n, in
 }
 
 template <int K, bool GUARD>
-const void* sym_fn() {
-  return reinterpret_cast<const void*>(&sym_kernel<K, GUARD>);
+const void* sym_fn(int threads) {
+  if (threads <= 64) return reinterpret_cast<const void*>(&sym_kernel<K, GUARD, 64>);
+  if (threads <= 128) return reinterpret_cast<const void*>(&sym_kernel<K, GUARD, 128>);
+  return reinterpret_cast<const void*>(&sym_kernel<K, GUARD, 256>);
 }
 
-const void* sym_select(int k, bool guard) {
-  if (guard) return k == 1 ? sym_fn<1, true>() : nullptr;
+const void* sym_select(int k, bool guard, int threads) {
+  if (threads > 256) return nullptr;
+  if (guard) return k == 1 ? sym_fn<1, true>(threads) : nullptr;
   switch (k) {
-    case 1: return sym_fn<1, false>();
-    case 2: return sym_fn<2, false>();
-    case 4: return sym_fn<4, false>();
-    case 8: return sym_fn<8, false>();
+    case 1: return sym_fn<1, false>(threads);
+    case 2: return sym_fn<2, false>(threads);
+    case 4: return sym_fn<4, false>(threads);
+    case 8: return sym_fn<8, false>(threads);
     default: return nullptr;
   }
 }
@@ -300,7 +309,7 @@ size_t sym_smem_bytes(int threads, int k, int sub_tile, int stages) {
 }
 
 cudaError_t occupancy_sym(int k, bool guard, int threads, size_t smem, int* ctas) {
-  const void* f = sym_select(k, guard);
+  const void* f = sym_select(k, guard, threads);
   if (!f) return cudaErrorInvalidValue;
   cudaError_t e = prepare_kernel(f, smem);
   if (e != cudaSuccess) return e;
@@ -308,7 +317,7 @@ cudaError_t occupancy_sym(int k, bool guard, int threads, size_t smem, int* ctas
 }
 
 cudaError_t launch_sym(const SymArgs& a, int k, bool guard, int threads, int grid, size_t smem, cudaStream_t s) {
-  const void* f = sym_select(k, guard);
+  const void* f = sym_select(k, guard, threads);
   if (!f) return cudaErrorInvalidValue;
   cudaError_t e = prepare_kernel(f, smem);
   if (e != cudaSuccess) return e;
