@@ -38,7 +38,10 @@ METRIC = "pair interactions/s and % of FP32/MUFU roofline at N=131072, FP32 vs c
 UNIT = "pairs/s"
 N_DEFAULT = 131072
 FLOP_PER_PAIR = 38  # the paper's counting convention (Eq. 4)
-ISSUE_PER_PAIR = 13  # 12 FP32-pipe instructions + 1 MUFU per pair (plain kernel, no potential)
+# The plain kernel issues its FP32 work as packed f32x2 instructions (6 per
+# pair + 1 MUFU), so the bound is the FP32 pipe: 12 lane operations per pair
+# at 128 lanes per SM per clock.
+FP32_LANE_OPS_PER_PAIR = 12
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
 PAPER_PAIRS_PER_S = 256e9 / FLOP_PER_PAIR  # 8800GTX, N = 131072 (Table 3): context only
@@ -325,7 +328,7 @@ def run_ours(args):
     pairs = float(n) * float(n)
     value = aggregate_rate(pairs * args.steps, world, total_s)
     sms = torch.cuda.get_device_properties(device).multi_processor_count
-    peak = sms * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / ISSUE_PER_PAIR
+    peak = sms * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / FP32_LANE_OPS_PER_PAIR
     achieved = pairs / mean_kernel_s
     dd_rate = pairs / dd_mean_s
     peaks = cn.cn_probe_peaks()
@@ -362,9 +365,9 @@ def run_ours(args):
             "frac": achieved / peak,
             "traffic": profiled_traffic(tuned or cn.cn_tune_get("f32", n, n)),
             "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {SM_MAX_MHZ:.0f} MHz / "
-                          f"{ISSUE_PER_PAIR} issue slots per pair (12 FP32 + 1 MUFU)",
+                          f"{FP32_LANE_OPS_PER_PAIR} FP32 lane operations per pair (packed f32x2 issue)",
             "frac_at_observed_clock": achieved / (peak * obs_mhz / SM_MAX_MHZ),
-            "probe_pair_mix": peaks["pair_mix_per_s"] / 1e9,
+            "probe_scalar_pair_mix": peaks["pair_mix_per_s"] / 1e9,
             "probe_ffma_per_s": peaks["ffma_per_s"],
             "probe_mufu_per_s": peaks["mufu_rsqrt_per_s"],
         },
@@ -397,10 +400,10 @@ def run_ours(args):
 ADJOINT_ISSUE_PER_PAIR = 31  # 30 FP32 + 1 MUFU (adjoint pair, see the kernel notes)
 DD_ISSUE_PER_PAIR = 104      # double-single pair term + per-term TwoSum (FP32 instructions)
 JERK_ISSUE_PER_PAIR = 31     # 27 FP32 + 1 MUFU + 3 for the potential (force-jerk-potential pair)
-# symmetric form: 16 FP32 + 1 MUFU per unordered pair, plus the warp
-# reduce-scatter (27 SHFL + 27 FADD per 8 j records per lane, i.e. 54 / (8 K)
-# per unordered pair at K particles per thread; K = 8 by default)
-SYM_ISSUE_PER_UNORDERED_PAIR = 17 + 54 / 64
+# symmetric form (packed f32x2 issue): 16 FP32 lane operations per unordered
+# pair, plus per j record and lane 3 FADD joining the two packed halves and
+# 27/8 FADD of the warp reduce-scatter, over K = 8 pairs
+SYM_LANE_OPS_PER_UNORDERED_PAIR = 16 + (3 + 27 / 8) / 8
 
 
 def _events_ms(torch, fn, reps, stream):
@@ -591,7 +594,7 @@ def measure_rows(args, cn, torch, device, peak):
     t0 = time.perf_counter()
     ra, _ = oracle.force(p, p, eps2, rows=r, potential=False)
     dt = time.perf_counter() - t0
-    sym_roof = 2.0 * lane_rate / SYM_ISSUE_PER_UNORDERED_PAIR
+    sym_roof = 2.0 * lane_rate / SYM_LANE_OPS_PER_UNORDERED_PAIR
     rows["symmetric131072"] = {
         "pairs_per_s": float(n) * n / (ms / 1e3), "ms": ms,
         "frac": float(n) * n / (ms / 1e3) / sym_roof, "roofline_pairs_per_s": sym_roof,

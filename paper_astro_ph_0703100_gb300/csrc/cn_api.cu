@@ -248,9 +248,9 @@ cn_tune sym_default_tune(int64_t n, int sms) {
     double rate;
   };
   static const Shape shapes[] = {
-      {8, 256, 256, 3, 1, 3.12e12}, {8, 128, 256, 4, 3, 3.03e12}, {8, 64, 128, 4, 8, 2.90e12},
-      {4, 128, 256, 4, 3, 2.81e12}, {4, 64, 128, 4, 8, 2.56e12},  {2, 64, 64, 4, 8, 1.80e12},
-      {1, 64, 64, 4, 9, 1.10e12}};
+      {8, 256, 256, 3, 1, 3.56e12}, {8, 128, 256, 4, 3, 3.22e12}, {8, 64, 128, 4, 8, 3.05e12},
+      {4, 128, 256, 4, 3, 2.87e12}, {4, 64, 128, 4, 8, 2.64e12},  {2, 64, 64, 4, 8, 1.86e12},
+      {1, 64, 64, 4, 9, 0.93e12}};
   cn_tune best{};
   double best_t = 0.0;
   for (const Shape& sh : shapes) {
@@ -303,10 +303,11 @@ cn_tune default_tune(int variant, int64_t n_i, int64_t n_j) {
     t.i_per_thread = 4;
     t.j_tile = 256;
   } else if (n >= 32768) {
-    // measured optimum at N = 131072: FP32 K = 8 x 128 threads, DD K = 2 x 256 threads;
-    // the adjoint's 32-byte j records keep its stages at 256 records (4 CTAs per SM)
+    // measured optimum at N = 131072: FP32 K = 8 x 256 threads (packed form),
+    // DD K = 2 x 256 threads; the adjoint's 32-byte j records keep its stages
+    // at 256 records (4 CTAs per SM)
     t.i_per_thread = adj ? 2 : (dd ? 2 : 8);
-    t.threads = dd ? 256 : 128;
+    t.threads = (dd || f32) ? 256 : 128;
     t.j_tile = adj ? 256 : 1024;
   } else if (n >= 4096) {
     t.i_per_thread = 2;  // measured at N = 16384: K = 2 x 128 threads x 256 records
@@ -781,13 +782,13 @@ cn_status build_group_plan(const std::vector<Group>& groups, bool lists, int64_t
   if (!tune && !registered_tune(dev, variant, key_i, n_i_total)) {
     // i-tile fitted to the group sizes: every group is cut into whole i-tiles,
     // so a tile larger than the typical group leaves lanes idle. Among
-    // K = 4, 2, 1 particles per thread (128 threads) take the one with the
-    // least evaluated-but-padded work, weighted by the relative pair rate
-    // of each K.
-    const int ks[3] = {4, 2, 1};
-    const double rate[3] = {1.0, 0.93, 0.78};
+    // K = 8, 4, 2, 1 particles per thread (128 threads) take the one with
+    // the least evaluated-but-padded work, weighted by the relative pair
+    // rate of each K (measured on the 512-cluster ensemble).
+    const int ks[4] = {8, 4, 2, 1};
+    const double rate[4] = {1.0, 0.987, 0.974, 0.85};
     double best = -1.0;
-    for (int c = 0; c < 3; ++c) {
+    for (int c = 0; c < 4; ++c) {
       const int64_t it = static_cast<int64_t>(ks[c]) * 128;
       double padded = 0.0;
       for (const Group& gr : groups) padded += static_cast<double>(ceil_div(gr.ni, it) * it) * static_cast<double>(gr.nj);

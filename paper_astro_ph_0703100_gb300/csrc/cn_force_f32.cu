@@ -4,9 +4,14 @@
 namespace cn {
 namespace {
 
+// K >= 2 without the split-j lanes runs the packed (f32x2) policy: the
+// same results, fewer issued instructions per pair.
 template <int K, bool POT, bool GUARD, bool BATCHED, bool SPLITJ = false>
 const void* fn() {
-  return reinterpret_cast<const void*>(&pair_kernel<F32Policy<K, POT, GUARD, SPLITJ>, K, BATCHED>);
+  if constexpr (K >= 2 && !SPLITJ)
+    return reinterpret_cast<const void*>(&pair_kernel<F32x2Policy<K, POT, GUARD>, K, BATCHED>);
+  else
+    return reinterpret_cast<const void*>(&pair_kernel<F32Policy<K, POT, GUARD, SPLITJ>, K, BATCHED>);
 }
 
 template <bool POT, bool GUARD, bool BATCHED>

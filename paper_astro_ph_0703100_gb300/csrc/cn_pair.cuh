@@ -234,6 +234,125 @@ struct F32Policy {
   }
 };
 
+// Packed FP32 form of the same pair term: two i-particles per 64-bit
+// register pair, every FP32 operation issued as one f32x2 instruction
+// (add / mul / fma .rn.f32x2) and the rsqrt as two MUFU operations. Each
+// lane-level operation, and the order of operations, is the scalar
+// pair_f32's, so the results are bitwise the same; the warp instructions
+// per pair drop from 12 FP32 + 1 MUFU to 6 packed + 1 MUFU (+ 4 moves per
+// j record to duplicate it), which leaves the FP32 pipe (12 lane operations
+// per pair) as the bound instead of the issue slot. The i coordinates are
+// held negated so that x_j - x_i is one packed add.
+__device__ __forceinline__ float2 dup2(float v) { return make_float2(v, v); }
+
+template <int K, bool POT, bool GUARD>
+__device__ __forceinline__ void pair_f32x2(const float4 pj, const float2 (&nxi)[K / 2][3], float2 e2,
+                                           float2 (&part)[K / 2][POT ? 4 : 3]) {
+  const float2 jx = dup2(pj.x), jy = dup2(pj.y), jz = dup2(pj.z), jm = dup2(pj.w);
+#pragma unroll
+  for (int p = 0; p < K / 2; ++p) {
+    const float2 dx = __fadd2_rn(jx, nxi[p][0]);
+    const float2 dy = __fadd2_rn(jy, nxi[p][1]);
+    const float2 dz = __fadd2_rn(jz, nxi[p][2]);
+    float2 s, d2 = dup2(0.f);
+    if constexpr (POT) {
+      d2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+      s = __fadd2_rn(d2, e2);
+    } else {
+      s = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, e2)));
+    }
+    float2 r = make_float2(rsqrt_mufu(s.x), rsqrt_mufu(s.y));
+    if constexpr (GUARD) {
+      r.x = (s.x > 0.f) ? r.x : 0.f;
+      r.y = (s.y > 0.f) ? r.y : 0.f;
+    }
+    const float2 mr = __fmul2_rn(jm, r);
+    const float2 q = __fmul2_rn(mr, __fmul2_rn(r, r));
+    part[p][0] = __ffma2_rn(q, dx, part[p][0]);
+    part[p][1] = __ffma2_rn(q, dy, part[p][1]);
+    part[p][2] = __ffma2_rn(q, dz, part[p][2]);
+    if constexpr (POT)
+      part[p][3] = __fadd2_rn(part[p][3], make_float2(d2.x != 0.f ? mr.x : 0.f, d2.y != 0.f ? mr.y : 0.f));
+  }
+}
+
+// Plain FP32 with packed arithmetic (K even): the F32Policy's results,
+// two i-particles per register pair.
+template <int K, bool POT, bool GUARD>
+struct F32x2Policy {
+  static_assert(K % 2 == 0, "the packed form holds i-particles in pairs");
+  static constexpr int NC = POT ? 4 : 3;
+  static constexpr int kSlotF4 = 1;
+  static constexpr int kSums = 4;
+  static constexpr int kJRec = 1;
+  static constexpr bool kSplitJ = false;
+  static constexpr int kMinBlocks = K >= 4 ? 1 : 2;  // K = 4 spills under a 128-register cap
+  float2 nxi[K / 2][3];
+  float2 run[K / 2][NC];
+
+  __device__ __forceinline__ static float& half(float2& v, int k) { return (k & 1) ? v.y : v.x; }
+  __device__ __forceinline__ static float half(const float2& v, int k) { return (k & 1) ? v.y : v.x; }
+
+  __device__ __forceinline__ void load_i(const PairArgs& a, int64_t gi, bool valid, int k) {
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (valid) v = __ldg(a.pos_i + gi);
+    half(nxi[k >> 1][0], k) = -v.x;
+    half(nxi[k >> 1][1], k) = -v.y;
+    half(nxi[k >> 1][2], k) = -v.z;
+  }
+
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int p = 0; p < K / 2; ++p)
+#pragma unroll
+      for (int c = 0; c < NC; ++c) run[p][c] = dup2(0.f);
+  }
+
+  __device__ __forceinline__ void tile(const float4* js, int T, float eps2, int64_t /*self_off*/, bool /*diag*/,
+                                       int /*row*/, int /*rows*/, int /*sub*/, int /*jl*/) {
+    float2 part[K / 2][NC];
+#pragma unroll
+    for (int p = 0; p < K / 2; ++p)
+#pragma unroll
+      for (int c = 0; c < NC; ++c) part[p][c] = dup2(0.f);
+    const float2 e2 = dup2(eps2);
+#pragma unroll 1
+    for (int j = 0; j < T; j += 16) {
+#pragma unroll
+      for (int jj = 0; jj < 16; ++jj) pair_f32x2<K, POT, GUARD>(js[j + jj], nxi, e2, part);
+    }
+#pragma unroll
+    for (int p = 0; p < K / 2; ++p)
+#pragma unroll
+      for (int c = 0; c < NC; ++c) run[p][c] = __fadd2_rn(run[p][c], part[p][c]);
+  }
+
+  __device__ __forceinline__ void reduce_lanes(int /*jl*/) {}
+
+  __device__ __forceinline__ void store_final(const PairArgs& a, int64_t i, int k) const {
+    float* acc = static_cast<float*>(a.acc_out) + 3 * i;
+    acc[0] = half(run[k >> 1][0], k);
+    acc[1] = half(run[k >> 1][1], k);
+    acc[2] = half(run[k >> 1][2], k);
+    if constexpr (POT) {
+      if (a.pot_out) static_cast<float*>(a.pot_out)[i] = -half(run[k >> 1][3], k);
+    }
+  }
+
+  __device__ __forceinline__ void store_partial(float4* slot, int il, int /*i_tile*/, int k) const {
+    slot[il] = make_float4(half(run[k >> 1][0], k), half(run[k >> 1][1], k), half(run[k >> 1][2], k),
+                           POT ? half(run[k >> 1][NC - 1], k) : 0.f);
+  }
+
+  __device__ static __forceinline__ void add_partial(const float4 (&v)[kSlotF4], double (&s)[kSums]) {
+    F32Policy<K, POT, GUARD>::add_partial(v, s);
+  }
+
+  __device__ static __forceinline__ void store_merged(const PairArgs& a, int64_t i, const double (&s)[kSums]) {
+    F32Policy<K, POT, GUARD>::store_merged(a, i, s);
+  }
+};
+
 // Compensated ("split-precision") form. Every quantity of the pair term is
 // carried as a double-single (hi, lo) pair of FP32 numbers and every FP32
 // rounding is recovered exactly, with TwoSum for sums and an FMA for

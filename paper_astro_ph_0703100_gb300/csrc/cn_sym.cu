@@ -17,6 +17,12 @@
 // j-side sums to slot (J, I) of a [tiles][n_pad] float4 array; a second
 // kernel adds the slots of each particle in partner order in FP64 - a
 // deterministic result with no atomics on data.
+//
+// The i-particles of a thread are held in pairs and the pair terms are
+// evaluated with packed f32x2 instructions (two i-particles per 64-bit
+// register pair; the rsqrt stays two MUFU operations): 8 packed FP32
+// instructions and 2 MUFU per two unordered pairs. The two halves of a
+// thread's j-side sum are added before the warp reduction.
 #include "cn_device.cuh"
 #include "cn_kernels.h"
 
@@ -91,7 +97,12 @@ __global__ void __launch_bounds__(NTMAX, sym_min_blocks(NTMAX)) sym_kernel(const
   // lane permutation of a batch: lane visits j = t ^ perm
   const int perm = (((lane >> 4) & 1) << 2) | (((lane >> 3) & 1) << 1) | ((lane >> 2) & 1);
 
-  float xi[K][3], mi[K], acc[K][3];
+  // i-particles in pairs (packed f32x2 arithmetic, as in the plain kernel's
+  // packed form): negated coordinates, masses and their negatives
+  static_assert(K == 1 || K % 2 == 0, "K is 1 or even");
+  constexpr int P = (K + 1) / 2;
+  float2 nxi[P][3], mi[P], nmi[P], acc[P][3];
+  auto half = [](float2& v, int k) -> float& { return (k & 1) ? v.y : v.x; };
   int32_t cur_I = -1;
   for (int64_t u = ub; u < ue; ++u) {
     int32_t I, J;
@@ -99,19 +110,26 @@ __global__ void __launch_bounds__(NTMAX, sym_min_blocks(NTMAX)) sym_kernel(const
     const bool diag = (I == J);
     if (I != cur_I) {
 #pragma unroll
+      for (int p = 0; p < P; ++p)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) nxi[p][c] = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int p = 0; p < P; ++p) mi[p] = nmi[p] = make_float2(0.f, 0.f);
+#pragma unroll
       for (int k = 0; k < K; ++k) {
         const int64_t p = static_cast<int64_t>(I) * B + k * NT + tid;
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
         if (p < a.n) v = __ldg(a.pos + p);
-        xi[k][0] = v.x;
-        xi[k][1] = v.y;
-        xi[k][2] = v.z;
-        mi[k] = v.w;
+        half(nxi[k >> 1][0], k) = -v.x;
+        half(nxi[k >> 1][1], k) = -v.y;
+        half(nxi[k >> 1][2], k) = -v.z;
+        half(mi[k >> 1], k) = v.w;
+        half(nmi[k >> 1], k) = -v.w;
       }
       cur_I = I;
     }
 #pragma unroll
-    for (int k = 0; k < K; ++k) acc[k][0] = acc[k][1] = acc[k][2] = 0.f;
+    for (int p = 0; p < P; ++p) acc[p][0] = acc[p][1] = acc[p][2] = make_float2(0.f, 0.f);
     if (!diag)
       for (int e = tid; e < NW * B * 3; e += NT) jrows[e] = 0.f;
     __syncthreads();
@@ -152,23 +170,31 @@ __global__ void __launch_bounds__(NTMAX, sym_min_blocks(NTMAX)) sym_kernel(const
       live = __all_sync(0xffffffffu, live);
       if (live) {
         const float4* js = ring + static_cast<size_t>(slot) * JS;
-        const float eps2 = a.eps2;
+        const float2 e2 = make_float2(a.eps2, a.eps2);
         if (diag) {
 #pragma unroll 1
           for (int j = 0; j < JS; j += 8) {
 #pragma unroll
             for (int jj = 0; jj < 8; ++jj) {
               const float4 pj = js[j + jj];
+              const float2 jx = make_float2(pj.x, pj.x), jy = make_float2(pj.y, pj.y);
+              const float2 jz = make_float2(pj.z, pj.z), jm = make_float2(pj.w, pj.w);
 #pragma unroll
-              for (int k = 0; k < K; ++k) {
-                const float dx = pj.x - xi[k][0], dy = pj.y - xi[k][1], dz = pj.z - xi[k][2];
-                const float s = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
-                float r = rsqrt_mufu(s);
-                if constexpr (GUARD) r = (s > 0.f) ? r : 0.f;
-                const float q = (pj.w * r) * (r * r);
-                acc[k][0] = fmaf(q, dx, acc[k][0]);
-                acc[k][1] = fmaf(q, dy, acc[k][1]);
-                acc[k][2] = fmaf(q, dz, acc[k][2]);
+              for (int p = 0; p < P; ++p) {
+                const float2 dx = __fadd2_rn(jx, nxi[p][0]);
+                const float2 dy = __fadd2_rn(jy, nxi[p][1]);
+                const float2 dz = __fadd2_rn(jz, nxi[p][2]);
+                const float2 s = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, e2)));
+                float2 r = make_float2(rsqrt_mufu(s.x), rsqrt_mufu(s.y));
+                if constexpr (GUARD) {
+                  r.x = (s.x > 0.f) ? r.x : 0.f;
+                  r.y = (s.y > 0.f) ? r.y : 0.f;
+                }
+                if constexpr (K == 1) r.y = 0.f;  // the unused half of the pair
+                const float2 q = __fmul2_rn(jm, __fmul2_rn(r, __fmul2_rn(r, r)));
+                acc[p][0] = __ffma2_rn(q, dx, acc[p][0]);
+                acc[p][1] = __ffma2_rn(q, dy, acc[p][1]);
+                acc[p][2] = __ffma2_rn(q, dz, acc[p][2]);
               }
             }
           }
@@ -181,26 +207,34 @@ __global__ void __launch_bounds__(NTMAX, sym_min_blocks(NTMAX)) sym_kernel(const
 #pragma unroll
             for (int t = 0; t < kSymBatch; ++t) {
               const float4 pj = js[j + (t ^ perm)];
-              float cx = 0.f, cy = 0.f, cz = 0.f;
+              const float2 jx = make_float2(pj.x, pj.x), jy = make_float2(pj.y, pj.y);
+              const float2 jz = make_float2(pj.z, pj.z), jm = make_float2(pj.w, pj.w);
+              float2 cx = make_float2(0.f, 0.f), cy = cx, cz = cx;
 #pragma unroll
-              for (int k = 0; k < K; ++k) {
-                const float dx = pj.x - xi[k][0], dy = pj.y - xi[k][1], dz = pj.z - xi[k][2];
-                const float s = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
-                float r = rsqrt_mufu(s);
-                if constexpr (GUARD) r = (s > 0.f) ? r : 0.f;
-                const float r3 = r * (r * r);
-                const float qi = pj.w * r3;  // m_j r^-3 onto particle i
-                const float qj = mi[k] * r3;  // m_i r^-3 onto particle j (opposite sign)
-                acc[k][0] = fmaf(qi, dx, acc[k][0]);
-                acc[k][1] = fmaf(qi, dy, acc[k][1]);
-                acc[k][2] = fmaf(qi, dz, acc[k][2]);
-                cx = fmaf(-qj, dx, cx);
-                cy = fmaf(-qj, dy, cy);
-                cz = fmaf(-qj, dz, cz);
+              for (int p = 0; p < P; ++p) {
+                const float2 dx = __fadd2_rn(jx, nxi[p][0]);
+                const float2 dy = __fadd2_rn(jy, nxi[p][1]);
+                const float2 dz = __fadd2_rn(jz, nxi[p][2]);
+                const float2 s = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, e2)));
+                float2 r = make_float2(rsqrt_mufu(s.x), rsqrt_mufu(s.y));
+                if constexpr (GUARD) {
+                  r.x = (s.x > 0.f) ? r.x : 0.f;
+                  r.y = (s.y > 0.f) ? r.y : 0.f;
+                }
+                if constexpr (K == 1) r.y = 0.f;  // the unused half of the pair
+                const float2 r3 = __fmul2_rn(r, __fmul2_rn(r, r));
+                const float2 qi = __fmul2_rn(jm, r3);      // m_j r^-3 onto particle i
+                const float2 qj = __fmul2_rn(nmi[p], r3);  // -m_i r^-3 onto particle j
+                acc[p][0] = __ffma2_rn(qi, dx, acc[p][0]);
+                acc[p][1] = __ffma2_rn(qi, dy, acc[p][1]);
+                acc[p][2] = __ffma2_rn(qi, dz, acc[p][2]);
+                cx = __ffma2_rn(qj, dx, cx);
+                cy = __ffma2_rn(qj, dy, cy);
+                cz = __ffma2_rn(qj, dz, cz);
               }
-              c[t][0] = cx;
-              c[t][1] = cy;
-              c[t][2] = cz;
+              c[t][0] = cx.x + cx.y;
+              c[t][1] = cy.x + cy.y;
+              c[t][2] = cz.x + cz.y;
             }
             // reduce-scatter over the warp: after the three halving steps
             // lane l holds, in c[0], the sum over the 8 lanes that share
@@ -238,7 +272,8 @@ __global__ void __launch_bounds__(NTMAX, sym_min_blocks(NTMAX)) sym_kernel(const
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       const int64_t p = static_cast<int64_t>(I) * B + k * NT + tid;
-      a.slots[static_cast<size_t>(J) * a.n_pad + p] = make_float4(acc[k][0], acc[k][1], acc[k][2], 0.f);
+      a.slots[static_cast<size_t>(J) * a.n_pad + p] =
+          make_float4(half(acc[k >> 1][0], k), half(acc[k >> 1][1], k), half(acc[k >> 1][2], k), 0.f);
     }
     if (!diag) {
       for (int jl = tid; jl < B; jl += NT) {
