@@ -397,9 +397,13 @@ def run_ours(args):
     return line
 
 
-ADJOINT_ISSUE_PER_PAIR = 31  # 30 FP32 + 1 MUFU (adjoint pair, see the kernel notes)
-DD_ISSUE_PER_PAIR = 104      # double-single pair term + per-term TwoSum (FP32 instructions)
-JERK_ISSUE_PER_PAIR = 31     # 27 FP32 + 1 MUFU + 3 for the potential (force-jerk-potential pair)
+# FP32 lane operations per pair of the packed (f32x2) adjoint and
+# force-jerk-potential kernels: the FP32 pipe is their bound, as for the
+# plain kernel. The compensated kernel issues scalar FP32 instructions only
+# (MUFU negligible), so its bound is the issue slot at 104 per pair.
+ADJOINT_LANE_OPS_PER_PAIR = 30
+DD_ISSUE_PER_PAIR = 104
+JERK_POT_LANE_OPS_PER_PAIR = 29  # 27 + 1 (d^2 then + eps2) + 1 (potential sum)
 # symmetric form (packed f32x2 issue): 16 FP32 lane operations per unordered
 # pair, plus per j record and lane 3 FADD joining the two packed halves and
 # 27/8 FADD of the warp reduce-scatter, over K = 8 pairs
@@ -576,8 +580,8 @@ def measure_rows(args, cn, torch, device, peak):
     dt = time.perf_counter() - t0
     rows["hermite_jerk131072"] = {
         "pairs_per_s": float(n) * n / (ms / 1e3), "ms": ms,
-        "frac": float(n) * n / (ms / 1e3) / (lane_rate / JERK_ISSUE_PER_PAIR),
-        "roofline_pairs_per_s": lane_rate / JERK_ISSUE_PER_PAIR,
+        "frac": float(n) * n / (ms / 1e3) / (lane_rate / JERK_POT_LANE_OPS_PER_PAIR),
+        "roofline_pairs_per_s": lane_rate / JERK_POT_LANE_OPS_PER_PAIR,
         "emax_acc": oracle.e_max(a_h.cpu().numpy()[r], ra), "emax_jerk": oracle.e_max(j_h.cpu().numpy()[r], rj),
         "cpu_baseline": {"value": r.size * n / dt, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
                          "sample": "512 seeded rows"}}
@@ -651,8 +655,8 @@ def measure_rows(args, cn, torch, device, peak):
     gph, gmh = gp.cpu().numpy().astype(np.float64), gm.cpu().numpy().astype(np.float64)
     rows["c5_adjoint65536"] = {
         "pairs_per_s": float(n) * n / (ms / 1e3), "ms": ms,
-        "frac": float(n) * n / (ms / 1e3) / (lane_rate / ADJOINT_ISSUE_PER_PAIR),
-        "roofline_pairs_per_s": lane_rate / ADJOINT_ISSUE_PER_PAIR,
+        "frac": float(n) * n / (ms / 1e3) / (lane_rate / ADJOINT_LANE_OPS_PER_PAIR),
+        "roofline_pairs_per_s": lane_rate / ADJOINT_LANE_OPS_PER_PAIR,
         "emax_grad_pos": oracle.e_max(gph[r], rp),
         "max_rel_grad_mass": float(np.max(np.abs(gmh[r] - rm)) / np.max(np.abs(rm))),
         "cpu_baseline": {"value": r.size * n / dt, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",

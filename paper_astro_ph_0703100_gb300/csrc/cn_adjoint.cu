@@ -4,9 +4,14 @@
 namespace cn {
 namespace {
 
+// K >= 2 runs the packed (f32x2) policy: the same results, fewer issued
+// instructions per pair.
 template <int K, bool GUARD>
 const void* fn() {
-  return reinterpret_cast<const void*>(&pair_kernel<AdjointPolicy<K, GUARD>, K, false>);
+  if constexpr (K >= 2)
+    return reinterpret_cast<const void*>(&pair_kernel<AdjointX2Policy<K, GUARD>, K, false>);
+  else
+    return reinterpret_cast<const void*>(&pair_kernel<AdjointPolicy<K, GUARD>, K, false>);
 }
 
 const void* select(int k, bool guard) {

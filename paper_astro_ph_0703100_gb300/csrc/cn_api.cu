@@ -302,12 +302,28 @@ cn_tune default_tune(int variant, int64_t n_i, int64_t n_j) {
   if (variant == cn::kBatched || variant == cn::kBatchedPot) {
     t.i_per_thread = 4;
     t.j_tile = 256;
+  } else if (f32 && n > 4096) {
+    // packed FP32, measured at N = 8192 .. 131072: K = 2 x 128 threads with
+    // 1024-record j-tiles up to N ~ 16K, K = 4 x 256 with 512-record tiles
+    // around 32K - 64K, K = 8 x 256 with 1024-record tiles above
+    if (n < 24576) {
+      t.i_per_thread = 2;
+      t.j_tile = 1024;
+    } else if (n < 98304) {
+      t.i_per_thread = 4;
+      t.threads = 256;
+      t.j_tile = 512;
+    } else {
+      t.i_per_thread = 8;
+      t.threads = 256;
+      t.j_tile = 1024;
+    }
   } else if (n >= 32768) {
-    // measured optimum at N = 131072: FP32 K = 8 x 256 threads (packed form),
-    // DD K = 2 x 256 threads; the adjoint's 32-byte j records keep its stages
-    // at 256 records (4 CTAs per SM)
-    t.i_per_thread = adj ? 2 : (dd ? 2 : 8);
-    t.threads = (dd || f32) ? 256 : 128;
+    // measured optima (packed forms): FP32 K = 8 x 256 threads at N = 131072,
+    // DD K = 2 x 256, adjoint (N = 65536) and force-jerk (N = 131072)
+    // K = 4 x 256 with j-tiles of 256 two-record j entries
+    t.i_per_thread = adj ? 4 : (dd ? 2 : 8);
+    t.threads = 256;
     t.j_tile = adj ? 256 : 1024;
   } else if (n >= 4096) {
     t.i_per_thread = 2;  // measured at N = 16384: K = 2 x 128 threads x 256 records

@@ -778,6 +778,276 @@ struct JerkPolicy {
   }
 };
 
+// ------------------------------------------------------------------ packed adjoint and jerk
+// The adjoint and force-jerk pair terms with two i-particles per register
+// pair (f32x2 issue), K even. Lane-level operations and their order are the
+// scalar forms'; negated terms are formed exactly by negated operands (the
+// i records are held negated, -3 instead of 3), and the adjoint's mass sum,
+// a sum of -g (w_p . d) terms, is accumulated with the opposite sign and
+// negated when stored (round-to-nearest commutes with negation), so the
+// results are bitwise those of the scalar policies.
+template <int K, bool GUARD, bool SELF>
+__device__ __forceinline__ void pair_adjoint_x2(const float4 pj, const float4 wp, const float2 (&nxk)[K / 2][3],
+                                                const float2 (&mk)[K / 2], const float2 (&nwk)[K / 2][3], float2 e2,
+                                                int j, const int (&self_j)[K], float2 (&part)[K / 2][4]) {
+  const float2 jx = dup2(pj.x), jy = dup2(pj.y), jz = dup2(pj.z), jm = dup2(pj.w);
+  const float2 wx = dup2(wp.x), wy = dup2(wp.y), wz = dup2(wp.z), m3 = dup2(-3.0f);
+#pragma unroll
+  for (int p = 0; p < K / 2; ++p) {
+    const float2 dx = __fadd2_rn(jx, nxk[p][0]);
+    const float2 dy = __fadd2_rn(jy, nxk[p][1]);
+    const float2 dz = __fadd2_rn(jz, nxk[p][2]);
+    const float2 s = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, e2)));
+    float2 r = make_float2(rsqrt_mufu(s.x), rsqrt_mufu(s.y));
+    if constexpr (GUARD) {
+      r.x = (s.x > 0.f) ? r.x : 0.f;
+      r.y = (s.y > 0.f) ? r.y : 0.f;
+    }
+    if constexpr (SELF) {
+      r.x = (j == self_j[2 * p]) ? 0.f : r.x;
+      r.y = (j == self_j[2 * p + 1]) ? 0.f : r.y;
+    }
+    const float2 r2 = __fmul2_rn(r, r);
+    const float2 g = __fmul2_rn(r2, r);
+    const float2 nh3 = __fmul2_rn(g, __fmul2_rn(m3, r2));  // -3 g r^2
+    const float2 ux = __ffma2_rn(mk[p], wx, __fmul2_rn(jm, nwk[p][0]));
+    const float2 uy = __ffma2_rn(mk[p], wy, __fmul2_rn(jm, nwk[p][1]));
+    const float2 uz = __ffma2_rn(mk[p], wz, __fmul2_rn(jm, nwk[p][2]));
+    const float2 nc = __fmul2_rn(nh3, __ffma2_rn(dx, ux, __ffma2_rn(dy, uy, __fmul2_rn(dz, uz))));
+    part[p][0] = __ffma2_rn(nc, dx, __ffma2_rn(g, ux, part[p][0]));
+    part[p][1] = __ffma2_rn(nc, dy, __ffma2_rn(g, uy, part[p][1]));
+    part[p][2] = __ffma2_rn(nc, dz, __ffma2_rn(g, uz, part[p][2]));
+    part[p][3] = __ffma2_rn(g, __ffma2_rn(wx, dx, __ffma2_rn(wy, dy, __fmul2_rn(wz, dz))), part[p][3]);
+  }
+}
+
+template <int K, bool GUARD>
+struct AdjointX2Policy {
+  static_assert(K % 2 == 0, "the packed form holds i-particles in pairs");
+  static constexpr int kSlotF4 = 1;
+  static constexpr int kSums = 4;
+  static constexpr int kJRec = 2;
+  static constexpr bool kSplitJ = false;
+  static constexpr int kMinBlocks = K >= 4 ? 1 : 2;
+  __device__ __forceinline__ void reduce_lanes(int) {}
+  float2 nxk[K / 2][3];
+  float2 mk[K / 2];
+  float2 nwk[K / 2][3];
+  float2 run[K / 2][4];  // component 3 holds -(dL/dm)
+
+  __device__ __forceinline__ static float& half(float2& v, int k) { return (k & 1) ? v.y : v.x; }
+  __device__ __forceinline__ static float half(const float2& v, int k) { return (k & 1) ? v.y : v.x; }
+
+  __device__ __forceinline__ void load_i(const PairArgs& a, int64_t gi, bool valid, int k) {
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (valid) {
+      v = __ldg(a.pos_i + gi);
+      w = __ldg(a.pos_i2 + gi);
+    }
+    half(nxk[k >> 1][0], k) = -v.x;
+    half(nxk[k >> 1][1], k) = -v.y;
+    half(nxk[k >> 1][2], k) = -v.z;
+    half(mk[k >> 1], k) = v.w;
+    half(nwk[k >> 1][0], k) = -w.x;
+    half(nwk[k >> 1][1], k) = -w.y;
+    half(nwk[k >> 1][2], k) = -w.z;
+  }
+
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int p = 0; p < K / 2; ++p)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) run[p][c] = dup2(0.f);
+  }
+
+  __device__ __forceinline__ void tile(const float4* js, int T, float eps2, int64_t self_off, bool diag, int row,
+                                       int rows, int /*sub*/, int /*jl*/) {
+    const float4* jw = js + T;
+    float2 part[K / 2][4];
+#pragma unroll
+    for (int p = 0; p < K / 2; ++p)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) part[p][c] = dup2(0.f);
+    int self_j[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int64_t sj = static_cast<int64_t>(k * rows + row) - self_off;
+      self_j[k] = (sj >= 0 && sj < T) ? static_cast<int>(sj) : -1;
+    }
+    const float2 e2 = dup2(eps2);
+    if (!diag) {
+#pragma unroll 1
+      for (int j = 0; j < T; j += 8) {
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj)
+          pair_adjoint_x2<K, GUARD, false>(js[j + jj], jw[j + jj], nxk, mk, nwk, e2, j + jj, self_j, part);
+      }
+    } else {
+#pragma unroll 1
+      for (int j = 0; j < T; j += 8) {
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj)
+          pair_adjoint_x2<K, GUARD, true>(js[j + jj], jw[j + jj], nxk, mk, nwk, e2, j + jj, self_j, part);
+      }
+    }
+#pragma unroll
+    for (int p = 0; p < K / 2; ++p)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) run[p][c] = __fadd2_rn(run[p][c], part[p][c]);
+  }
+
+  __device__ __forceinline__ void store_final(const PairArgs& a, int64_t i, int k) const {
+    float* g = static_cast<float*>(a.acc_out) + 3 * i;
+    g[0] = half(run[k >> 1][0], k);
+    g[1] = half(run[k >> 1][1], k);
+    g[2] = half(run[k >> 1][2], k);
+    static_cast<float*>(a.pot_out)[i] = -half(run[k >> 1][3], k);
+  }
+
+  __device__ __forceinline__ void store_partial(float4* slot, int il, int /*i_tile*/, int k) const {
+    slot[il] = make_float4(half(run[k >> 1][0], k), half(run[k >> 1][1], k), half(run[k >> 1][2], k),
+                           -half(run[k >> 1][3], k));
+  }
+
+  __device__ static __forceinline__ void add_partial(const float4 (&v)[kSlotF4], double (&s)[kSums]) {
+    AdjointPolicy<K, GUARD>::add_partial(v, s);
+  }
+
+  __device__ static __forceinline__ void store_merged(const PairArgs& a, int64_t i, const double (&s)[kSums]) {
+    AdjointPolicy<K, GUARD>::store_merged(a, i, s);
+  }
+};
+
+template <int K, bool POT, bool GUARD>
+__device__ __forceinline__ void pair_jerk_x2(const float4 pj, const float4 vj, const float2 (&nxi)[K / 2][3],
+                                             const float2 (&nvi)[K / 2][3], float2 e2, float2 (&part)[K / 2][7]) {
+  const float2 jx = dup2(pj.x), jy = dup2(pj.y), jz = dup2(pj.z), jm = dup2(pj.w);
+  const float2 ux = dup2(vj.x), uy = dup2(vj.y), uz = dup2(vj.z), m3 = dup2(-3.0f);
+#pragma unroll
+  for (int p = 0; p < K / 2; ++p) {
+    const float2 dx = __fadd2_rn(jx, nxi[p][0]);
+    const float2 dy = __fadd2_rn(jy, nxi[p][1]);
+    const float2 dz = __fadd2_rn(jz, nxi[p][2]);
+    const float2 wx = __fadd2_rn(ux, nvi[p][0]);
+    const float2 wy = __fadd2_rn(uy, nvi[p][1]);
+    const float2 wz = __fadd2_rn(uz, nvi[p][2]);
+    float2 s, d2 = dup2(0.f);
+    if constexpr (POT) {
+      d2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+      s = __fadd2_rn(d2, e2);
+    } else {
+      s = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, e2)));
+    }
+    float2 r = make_float2(rsqrt_mufu(s.x), rsqrt_mufu(s.y));
+    if constexpr (GUARD) {
+      r.x = (s.x > 0.f) ? r.x : 0.f;
+      r.y = (s.y > 0.f) ? r.y : 0.f;
+    }
+    const float2 r2 = __fmul2_rn(r, r);
+    const float2 mr = __fmul2_rn(jm, r);
+    const float2 q = __fmul2_rn(mr, r2);
+    const float2 nb = __fmul2_rn(__fmul2_rn(m3, r2), __ffma2_rn(dx, wx, __ffma2_rn(dy, wy, __fmul2_rn(dz, wz))));
+    const float2 nqb = __fmul2_rn(q, nb);  // -q b
+    part[p][0] = __ffma2_rn(q, dx, part[p][0]);
+    part[p][1] = __ffma2_rn(q, dy, part[p][1]);
+    part[p][2] = __ffma2_rn(q, dz, part[p][2]);
+    part[p][3] = __ffma2_rn(nqb, dx, __ffma2_rn(q, wx, part[p][3]));
+    part[p][4] = __ffma2_rn(nqb, dy, __ffma2_rn(q, wy, part[p][4]));
+    part[p][5] = __ffma2_rn(nqb, dz, __ffma2_rn(q, wz, part[p][5]));
+    if constexpr (POT)
+      part[p][6] = __fadd2_rn(part[p][6], make_float2(d2.x != 0.f ? mr.x : 0.f, d2.y != 0.f ? mr.y : 0.f));
+  }
+}
+
+template <int K, bool POT, bool GUARD>
+struct JerkX2Policy {
+  static_assert(K % 2 == 0, "the packed form holds i-particles in pairs");
+  static constexpr int kSlotF4 = 2;
+  static constexpr int kSums = 7;
+  static constexpr int kJRec = 2;
+  static constexpr bool kSplitJ = false;
+  static constexpr int kMinBlocks = 1;
+  static constexpr int NC = POT ? 7 : 6;
+  __device__ __forceinline__ void reduce_lanes(int) {}
+  float2 nxi[K / 2][3];
+  float2 nvi[K / 2][3];
+  float2 run[K / 2][7];
+
+  __device__ __forceinline__ static float& half(float2& v, int k) { return (k & 1) ? v.y : v.x; }
+  __device__ __forceinline__ static float half(const float2& v, int k) { return (k & 1) ? v.y : v.x; }
+
+  __device__ __forceinline__ void load_i(const PairArgs& a, int64_t gi, bool valid, int k) {
+    float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (valid) {
+      p = __ldg(a.pos_i + gi);
+      v = __ldg(a.pos_i2 + gi);
+    }
+    half(nxi[k >> 1][0], k) = -p.x;
+    half(nxi[k >> 1][1], k) = -p.y;
+    half(nxi[k >> 1][2], k) = -p.z;
+    half(nvi[k >> 1][0], k) = -v.x;
+    half(nvi[k >> 1][1], k) = -v.y;
+    half(nvi[k >> 1][2], k) = -v.z;
+  }
+
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int p = 0; p < K / 2; ++p)
+#pragma unroll
+      for (int c = 0; c < 7; ++c) run[p][c] = dup2(0.f);
+  }
+
+  __device__ __forceinline__ void tile(const float4* js, int T, float eps2, int64_t /*self_off*/, bool /*diag*/,
+                                       int /*row*/, int /*rows*/, int /*sub*/, int /*jl*/) {
+    const float4* jv = js + T;
+    float2 part[K / 2][7];
+#pragma unroll
+    for (int p = 0; p < K / 2; ++p)
+#pragma unroll
+      for (int c = 0; c < 7; ++c) part[p][c] = dup2(0.f);
+    const float2 e2 = dup2(eps2);
+#pragma unroll 1
+    for (int j = 0; j < T; j += 4) {
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) pair_jerk_x2<K, POT, GUARD>(js[j + jj], jv[j + jj], nxi, nvi, e2, part);
+    }
+#pragma unroll
+    for (int p = 0; p < K / 2; ++p)
+#pragma unroll
+      for (int c = 0; c < NC; ++c) run[p][c] = __fadd2_rn(run[p][c], part[p][c]);
+  }
+
+  __device__ __forceinline__ void store_final(const PairArgs& a, int64_t i, int k) const {
+    float* acc = static_cast<float*>(a.acc_out) + 3 * i;
+    float* jk = static_cast<float*>(a.jerk_out) + 3 * i;
+    acc[0] = half(run[k >> 1][0], k);
+    acc[1] = half(run[k >> 1][1], k);
+    acc[2] = half(run[k >> 1][2], k);
+    jk[0] = half(run[k >> 1][3], k);
+    jk[1] = half(run[k >> 1][4], k);
+    jk[2] = half(run[k >> 1][5], k);
+    if constexpr (POT) {
+      if (a.pot_out) static_cast<float*>(a.pot_out)[i] = -half(run[k >> 1][6], k);
+    }
+  }
+
+  __device__ __forceinline__ void store_partial(float4* slot, int il, int i_tile, int k) const {
+    slot[il] = make_float4(half(run[k >> 1][0], k), half(run[k >> 1][1], k), half(run[k >> 1][2], k),
+                           half(run[k >> 1][3], k));
+    slot[i_tile + il] = make_float4(half(run[k >> 1][4], k), half(run[k >> 1][5], k), half(run[k >> 1][6], k), 0.f);
+  }
+
+  __device__ static __forceinline__ void add_partial(const float4 (&v)[kSlotF4], double (&s)[kSums]) {
+    JerkPolicy<K, POT, GUARD>::add_partial(v, s);
+  }
+
+  __device__ static __forceinline__ void store_merged(const PairArgs& a, int64_t i, const double (&s)[kSums]) {
+    JerkPolicy<K, POT, GUARD>::store_merged(a, i, s);
+  }
+};
+
 // ------------------------------------------------------------------ kernel
 // Register budget per policy: Policy::kMinBlocks 256-thread CTAs must fit
 // on an SM (2: up to 128 registers per thread; 1: up to 255).
