@@ -179,17 +179,26 @@ CN_API cn_status cn_force_noalloc(int64_t n_i, const float *pos_i, int64_t n_j, 
                                   float *acc_out, float *pot_out, cn_stream stream);
 
 /*
- * Accelerations of n particles under each other's gravity (i set = j set)
- * evaluating every unordered pair once (Newton's third law: the pair term
- * is added to one particle and subtracted, with the other mass, from the
- * other). Not in the paper, whose kernel evaluates every ordered pair; about
- * 16 FP32 instructions and one MUFU per unordered pair plus a warp
- * reduce-scatter of the j-side sums, against 2 x 13 for the two ordered
+ * Accelerations of Eq. 1 for n particles under each other's gravity (i set
+ * = j set), evaluating every unordered pair once (Newton's third law: the
+ * pair term is added to one particle and subtracted, with the other mass,
+ * from the other). Not in the paper, whose kernel evaluates every ordered
+ * pair: 16 FP32 lane operations and one MUFU per unordered pair plus a warp
+ * reduce-scatter of the j-side sums, against 2 x 12 for the two ordered
  * pairs. Results are accumulated per (tile, partner tile) and merged in
- * FP64 in a fixed order (bitwise reproducible for a given launch shape).
- *   pos_mass : float[n][4]; acc_out : float[n][3]
- * Uses a library workspace of n_tiles x n_pad x 16 bytes (268 MB at
- * n = 131072 with the default 1024-particle tiles).
+ * FP64 in a fixed order (bitwise reproducible for a given launch shape);
+ * accuracy as cn_force.
+ *   pos_mass : float[n][4] device records (x, y, z, m), 16-byte aligned
+ *   eps2     : softening squared, finite and >= 0 (0: coincident pairs
+ *              contribute nothing)
+ *   acc_out  : float[n][3] device, 4-byte aligned, must not overlap pos_mass
+ * Asynchronous on `stream`; n == 0 is a no-op. Errors: CN_ERR_INVALID_ARG
+ * (n < 0, bad eps2, NULL or overlapping buffers, a tune with j_lanes),
+ * CN_ERR_MISALIGNED, CN_ERR_CUDA (launch), CN_ERR_WORKSPACE (below).
+ * Uses a library workspace of n_tiles x n_pad x 16 bytes, about 16 N^2 / B
+ * for tiles of B particles (134 MB at N = 131072 with the default
+ * 2048-particle tiles, 8.6 GB at N = 2^20); returns CN_ERR_WORKSPACE when
+ * the device cannot hold it (cn_force has no such growth).
  */
 CN_API cn_status cn_force_symmetric(int64_t n, const float *pos_mass, float eps2, float *acc_out, cn_stream stream);
 

@@ -184,6 +184,15 @@ cn_status library_workspace(cudaStream_t s, size_t ctrl_need, size_t data_need, 
   return CN_OK;
 }
 
+// Bytes of the data region the library already holds for stream s.
+size_t library_data_bytes(cudaStream_t s) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  std::lock_guard<std::mutex> lock(g_mu);
+  auto it = g_ws.find({dev, s});
+  return it == g_ws.end() ? 0 : it->second.data_bytes;
+}
+
 // Frees the library workspace of a stream that is about to be destroyed.
 void release_library_workspace(cudaStream_t s) {
   int dev = 0;
@@ -711,9 +720,15 @@ cn_status symmetric_common(int64_t n, const float* pos_mass, float eps2, float* 
   a.wait_ns = g_wait_ns.load();
   const int64_t slots = static_cast<int64_t>(p.ctas_per_sm > 0 ? std::min(p.ctas_per_sm, occ) : occ) * d->sms;
   const int grid = static_cast<int>(std::min<int64_t>(slots, a.units));
+  // the slot array grows as N^2 / B (8.6 GB at N = 2^20, 137 GB at 2^22):
+  // refuse clearly when the device cannot hold it
+  const size_t slot_bytes = static_cast<size_t>(T) * static_cast<size_t>(a.n_pad) * 16;
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && slot_bytes > free_b + library_data_bytes(s))
+    return fail(CN_ERR_WORKSPACE, "symmetric form: the per-tile slot array does not fit in device memory "
+                                  "(it grows as N^2 / tile); use cn_force for this N");
   char *ctrl = nullptr, *data = nullptr;
-  if ((st = library_workspace(s, kCtrlBytes, static_cast<size_t>(T) * a.n_pad * 16, &ctrl, &data)) != CN_OK)
-    return st;
+  if ((st = library_workspace(s, kCtrlBytes, slot_bytes, &ctrl, &data)) != CN_OK) return st;
   a.slots = reinterpret_cast<float4*>(data);
   if (inject("launch")) return fail(CN_ERR_CUDA, "kernel launch: injected launch failure");
   e = cn::launch_sym(a, guard ? 1 : p.k, guard, p.threads, grid, smem, s);
