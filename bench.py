@@ -798,7 +798,9 @@ def main(argv=None):
     ap.add_argument("--autotune", action="store_true", help="autotune the headline launch shapes first")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-rows", action="store_true", help="skip the other workloads (C1, C2 small, C3, C4, C5)")
-    ap.add_argument("--cpu-budget", type=float, default=10.0, help="seconds of oracle work for cpu_baseline")
+    ap.add_argument("--cpu-budget", type=float, default=20.0,
+                    help="target seconds of oracle work for cpu_baseline (sized from a short probe that runs slower "
+                         "than the sample: about 10 s are spent)")
     ap.add_argument("--ref-rows", type=int, default=256, help="oracle rows per step of --impl reference")
     ap.add_argument("--only", choices=("f32", "dd", "adjoint", "batched", "jerk", "sym", "lists"),
                     help="time one kernel family alone (profiling mode; prints its own JSON)")
