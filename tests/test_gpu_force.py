@@ -68,6 +68,25 @@ def test_c2_large_sampled_rows_autotuned(n):
     cn.cn_tune_set("f32", n, n, None)
 
 
+def test_c2_131072_default_shape_sampled():
+    """The benchmark's own launch configuration (the default shape, no
+    autotuning) at N = 131072 on 4096 sampled rows, twice in a row."""
+    cn = lib()
+    torch = torch_cuda()
+    n = 131072
+    p = synth.plummer(n, n)
+    eps2 = float(np.float32(synth.plummer_eps(n)) ** 2)
+    t = dev_tensor(p)
+    cn.cn_tune_set("f32", n, n, None)
+    a1, _ = cn.cn_force(t, t, eps2)
+    a2, _ = cn.cn_force(t, t, eps2)
+    torch.cuda.synchronize()
+    assert torch.equal(a1, a2)
+    rows = synth.sample_rows(n, 4096, seed=n + 2)
+    ref, _ = oracle.force(p, p, eps2, rows=rows, potential=False)
+    assert e_max(a1.cpu().numpy()[rows], ref) <= TOL_F32
+
+
 SHAPES = [
     (1, 1), (1, 7), (7, 1), (31, 33), (33, 31), (257, 1000), (1000, 777), (3000, 5001), (4097, 2049),
 ]
@@ -242,4 +261,5 @@ def test_dd_c3_hernquist_million_sampled():
     edd, e32 = e_max(add[rows], ref), e_max(a32[rows], ref)
     print(f"C3 E_max: compensated {edd:.3e}, plain FP32 {e32:.3e}")
     assert edd <= TOL_DD
+    assert e32 <= TOL_F32
     assert edd < e32
