@@ -367,6 +367,7 @@ def run_ours(args):
             "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {SM_MAX_MHZ:.0f} MHz / "
                           f"{FP32_LANE_OPS_PER_PAIR} FP32 lane operations per pair (packed f32x2 issue)",
             "frac_at_observed_clock": achieved / (peak * obs_mhz / SM_MAX_MHZ),
+            "frac_of_probe_ffma_rate": achieved * FP32_LANE_OPS_PER_PAIR / peaks["ffma_per_s"],
             "probe_scalar_pair_mix": peaks["pair_mix_per_s"] / 1e9,
             "probe_ffma_per_s": peaks["ffma_per_s"],
             "probe_mufu_per_s": peaks["mufu_rsqrt_per_s"],
@@ -460,6 +461,7 @@ def measure_rows(args, cn, torch, device, peak):
                          "sample": "all 1024 rows"}}
 
     # C2 small sizes: N = 2048 (all rows checked) and 16384 (4096 rows)
+    paper_gflops = {2048: 173.0, 16384: 246.0}  # 8800GTX, Table 3 (context only)
     for n, n_rows in ((2048, 2048), (16384, 4096)):
         p = synth.plummer(n, n)
         eps2 = float(np.float32(synth.plummer_eps(n)) ** 2)
@@ -476,6 +478,8 @@ def measure_rows(args, cn, torch, device, peak):
             "pairs_per_s": float(n) * n / (us_dev / 1e6), "us_per_eval_device": us_dev,
             "us_per_call_direct": 1e3 * ms,
             "frac": float(n) * n / (us_dev / 1e6) / peak, "launch_shape": cn.cn_tune_get("f32", n, n),
+            "gflops_at_38": float(n) * n / (us_dev / 1e6) * FLOP_PER_PAIR / 1e9,
+            "paper_gflops_8800gtx": paper_gflops[n],
             "emax": oracle.e_max(acc.cpu().numpy()[r], ref),
             "cpu_baseline": {"value": r.size * n / dt, "unit": UNIT, "cores": oracle.max_threads(),
                              "kind": "oracle", "sample": f"{r.size} of {n} rows"}}
