@@ -294,14 +294,15 @@ cn_tune default_tune(int variant, int64_t n_i, int64_t n_j) {
   t.stages = 4;
   t.threads = 128;
   t.j_lanes = 1;
-  if (f32 && n_i <= 4096) {
-    // small systems (measured at N = 1024 .. 4096): 16 lanes per i-particle
-    // (8 at N = 4096) and, where it fits, the whole j set in one single-stage
-    // tile, so that each CTA covers whole i-tiles and nothing is merged
-    const int jl = n_i <= 2048 ? 16 : 8;
-    t.i_per_thread = 1;
+  if (f32 && n_i <= 8192) {
+    // small systems (measured at N = 1024 .. 8192, packed form): lane groups
+    // of 32 (16 at N = 4096) share two i-particles and, where it fits, the
+    // whole j set sits in one single-stage tile, so that each CTA covers
+    // whole i-tiles and nothing is merged
+    const int jl = (n_i > 2048 && n_i <= 4096) ? 16 : 32;
+    t.i_per_thread = 2;
     t.j_lanes = jl;
-    t.threads = n_i <= 2048 ? 128 : 256;
+    t.threads = n_i <= 1024 ? 128 : 256;
     const int64_t unit = 8 * jl;
     t.j_tile = static_cast<int32_t>(std::min<int64_t>(round_up(std::max<int64_t>(n_j, 1), unit), 4096));
     t.stages = n_j <= t.j_tile ? 1 : 3;
@@ -312,7 +313,7 @@ cn_tune default_tune(int variant, int64_t n_i, int64_t n_j) {
     t.i_per_thread = 4;
     t.j_tile = 256;
   } else if (f32 && n > 4096) {
-    // packed FP32, measured at N = 8192 .. 131072: K = 2 x 128 threads with
+    // packed FP32, measured at N = 16384 .. 131072: K = 2 x 128 threads with
     // 1024-record j-tiles up to N ~ 16K, K = 4 x 256 with 512-record tiles
     // around 32K - 64K, K = 8 x 256 with 1024-record tiles above
     if (n < 24576) {
@@ -359,7 +360,7 @@ cn_status check_tune(int variant, const cn_tune& t) {
   if (t.j_lanes > 1) {
     if (variant != cn::kF32 && variant != cn::kF32Pot)
       return fail(CN_ERR_INVALID_ARG, "j_lanes > 1 is offered for the plain FP32 single-system form only");
-    if (t.i_per_thread > 1) return fail(CN_ERR_INVALID_ARG, "j_lanes > 1 needs i_per_thread = 1");
+    if (t.i_per_thread > 2) return fail(CN_ERR_INVALID_ARG, "j_lanes > 1 needs i_per_thread = 1 or 2");
     if (t.j_tile && t.j_tile % (8 * t.j_lanes))
       return fail(CN_ERR_INVALID_ARG, "with j_lanes > 1, j_tile must be a multiple of 8 x j_lanes");
   }
@@ -420,7 +421,8 @@ cn_status resolve_plan(int dev, int variant, int64_t n_i, int64_t n_j, bool guar
   p->j_lanes = t.j_lanes > 1 ? t.j_lanes : 1;
   if (p->j_lanes > 1 && variant == cn::kSym) return fail(CN_ERR_INVALID_ARG, "the symmetric form takes no j_lanes");
   if (p->j_lanes > 1) {
-    p->k = 1;
+    // split-j: one i-particle per lane group, or two with the packed form
+    p->k = (p->k == 2 && !guard) ? 2 : 1;
     if (p->j_tile % (8 * p->j_lanes)) return fail(CN_ERR_INVALID_ARG, "j_tile must be a multiple of 8 x j_lanes");
   }
   const size_t smem = variant == cn::kSym
@@ -1340,7 +1342,8 @@ cn_status cn_autotune(int variant, int64_t n_i, const float* pos_i, int64_t n_j,
         for (int64_t jt : {static_cast<int64_t>(512), static_cast<int64_t>(2048), round_up(std::max<int64_t>(n_j, 1), 8 * jl),
                            static_cast<int64_t>(4096)}) {
           if (jt % (8 * jl) || jt > 4096 || jt < 8 * jl) continue;
-          cands.push_back(cn_tune{1, th, static_cast<int32_t>(jt), jt >= n_j ? 1 : 3, 0, 0, jl});
+          for (int k : {1, 2})  // one i-particle per lane group, or two (packed)
+            cands.push_back(cn_tune{k, th, static_cast<int32_t>(jt), jt >= n_j ? 1 : 3, 0, 0, jl});
         }
     }
   }

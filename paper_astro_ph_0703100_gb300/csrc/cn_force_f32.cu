@@ -8,8 +8,8 @@ namespace {
 // same results, fewer issued instructions per pair.
 template <int K, bool POT, bool GUARD, bool BATCHED, bool SPLITJ = false>
 const void* fn() {
-  if constexpr (K >= 2 && !SPLITJ)
-    return reinterpret_cast<const void*>(&pair_kernel<F32x2Policy<K, POT, GUARD>, K, BATCHED>);
+  if constexpr (K >= 2)
+    return reinterpret_cast<const void*>(&pair_kernel<F32x2Policy<K, POT, GUARD, SPLITJ>, K, BATCHED>);
   else
     return reinterpret_cast<const void*>(&pair_kernel<F32Policy<K, POT, GUARD, SPLITJ>, K, BATCHED>);
 }
@@ -30,8 +30,9 @@ const void* by_k(int k) {
 }
 
 const void* select(int k, bool pot, bool guard, bool batched, int j_lanes) {
-  if (j_lanes > 1) {  // split-j kernels: one i-particle per j-lane group, single systems
-    if (k != 1 || batched) return nullptr;
+  if (j_lanes > 1) {  // split-j kernels: one or two i-particles per j-lane group, single systems
+    if (batched || k > 2 || (k == 2 && guard)) return nullptr;
+    if (k == 2) return pot ? fn<2, true, false, false, true>() : fn<2, false, false, false, true>();
     if (pot) return guard ? fn<1, true, true, false, true>() : fn<1, true, false, false, true>();
     return guard ? fn<1, false, true, false, true>() : fn<1, false, false, false, true>();
   }

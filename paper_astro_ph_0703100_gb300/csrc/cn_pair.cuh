@@ -239,8 +239,9 @@ struct F32Policy {
 // (add / mul / fma .rn.f32x2) and the rsqrt as two MUFU operations. Each
 // lane-level operation, and the order of operations, is the scalar
 // pair_f32's, so the results are bitwise the same; the warp instructions
-// per pair drop from 12 FP32 + 1 MUFU to 6 packed + 1 MUFU (+ 4 moves per
-// j record to duplicate it), which leaves the FP32 pipe (12 lane operations
+// per pair drop from 12 FP32 + 1 MUFU to 6 packed + 1 MUFU (the broadcast j
+// record feeds the packed instructions without extra moves: 7.18 measured
+// per pair, LDS included), which leaves the FP32 pipe (12 lane operations
 // per pair) as the bound instead of the issue slot. The i coordinates are
 // held negated so that x_j - x_i is one packed add.
 __device__ __forceinline__ float2 dup2(float v) { return make_float2(v, v); }
@@ -277,16 +278,19 @@ __device__ __forceinline__ void pair_f32x2(const float4 pj, const float2 (&nxi)[
 }
 
 // Plain FP32 with packed arithmetic (K even): the F32Policy's results,
-// two i-particles per register pair.
-template <int K, bool POT, bool GUARD>
+// two i-particles per register pair. SPLITJ: as in F32Policy, groups of
+// j_lanes lanes share the thread's i-particles, each lane taking every
+// j_lanes-th j record, combined by an xor butterfly at segment ends.
+template <int K, bool POT, bool GUARD, bool SPLITJ = false>
 struct F32x2Policy {
   static_assert(K % 2 == 0, "the packed form holds i-particles in pairs");
   static constexpr int NC = POT ? 4 : 3;
   static constexpr int kSlotF4 = 1;
   static constexpr int kSums = 4;
   static constexpr int kJRec = 1;
-  static constexpr bool kSplitJ = false;
-  static constexpr int kMinBlocks = K >= 4 ? 1 : 2;  // K = 4 spills under a 128-register cap
+  static constexpr bool kSplitJ = SPLITJ;
+  // K = 4 (and the split-j form with the potential) spill under a 128-register cap
+  static constexpr int kMinBlocks = (K >= 4 || SPLITJ) ? 1 : 2;
   float2 nxi[K / 2][3];
   float2 run[K / 2][NC];
 
@@ -309,17 +313,26 @@ struct F32x2Policy {
   }
 
   __device__ __forceinline__ void tile(const float4* js, int T, float eps2, int64_t /*self_off*/, bool /*diag*/,
-                                       int /*row*/, int /*rows*/, int /*sub*/, int /*jl*/) {
+                                       int /*row*/, int /*rows*/, int sub, int jl) {
     float2 part[K / 2][NC];
 #pragma unroll
     for (int p = 0; p < K / 2; ++p)
 #pragma unroll
       for (int c = 0; c < NC; ++c) part[p][c] = dup2(0.f);
     const float2 e2 = dup2(eps2);
+    if constexpr (SPLITJ) {
+      // this lane's j records: sub, sub + jl, ... (j_tile is a multiple of 8 jl)
 #pragma unroll 1
-    for (int j = 0; j < T; j += 16) {
+      for (int j = sub; j < T; j += 8 * jl) {
 #pragma unroll
-      for (int jj = 0; jj < 16; ++jj) pair_f32x2<K, POT, GUARD>(js[j + jj], nxi, e2, part);
+        for (int jj = 0; jj < 8; ++jj) pair_f32x2<K, POT, GUARD>(js[j + jj * jl], nxi, e2, part);
+      }
+    } else {
+#pragma unroll 1
+      for (int j = 0; j < T; j += 16) {
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) pair_f32x2<K, POT, GUARD>(js[j + jj], nxi, e2, part);
+      }
     }
 #pragma unroll
     for (int p = 0; p < K / 2; ++p)
@@ -327,7 +340,18 @@ struct F32x2Policy {
       for (int c = 0; c < NC; ++c) run[p][c] = __fadd2_rn(run[p][c], part[p][c]);
   }
 
-  __device__ __forceinline__ void reduce_lanes(int /*jl*/) {}
+  // sums the running sums of the j_lanes lanes of each group (xor butterfly)
+  __device__ __forceinline__ void reduce_lanes(int jl) {
+    for (int off = jl >> 1; off > 0; off >>= 1) {
+#pragma unroll
+      for (int p = 0; p < K / 2; ++p)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          run[p][c].x += __shfl_xor_sync(0xffffffffu, run[p][c].x, off);
+          run[p][c].y += __shfl_xor_sync(0xffffffffu, run[p][c].y, off);
+        }
+    }
+  }
 
   __device__ __forceinline__ void store_final(const PairArgs& a, int64_t i, int k) const {
     float* acc = static_cast<float*>(a.acc_out) + 3 * i;

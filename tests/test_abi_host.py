@@ -129,7 +129,7 @@ def test_batch_plan_validation(lib):
     assert lib.cn_tune_set(0, 1024, 1024, ctypes.byref(t)) == 1
     t = cn_tune(1, 128, 256, 4, 0, 0, 3)  # j_lanes must be a power of two
     assert lib.cn_tune_set(0, 1024, 1024, ctypes.byref(t)) == 1
-    t = cn_tune(2, 128, 256, 4, 0, 0, 8)  # j_lanes > 1 needs one i-particle per thread
+    t = cn_tune(4, 128, 256, 4, 0, 0, 8)  # j_lanes > 1 needs one or two i-particles per thread
     assert lib.cn_tune_set(0, 1024, 1024, ctypes.byref(t)) == 1
     t = cn_tune(1, 128, 96, 4, 0, 0, 8)  # j_tile not a multiple of 8 x j_lanes
     assert lib.cn_tune_set(0, 1024, 1024, ctypes.byref(t)) == 1

@@ -103,6 +103,9 @@ TUNES = [
     {"i_per_thread": 1, "threads": 64, "j_tile": 64, "stages": 3, "j_lanes": 4},
     {"i_per_thread": 1, "threads": 256, "j_tile": 128, "stages": 4, "j_lanes": 16, "chunk_units": 2},
     {"i_per_thread": 1, "threads": 128, "j_tile": 128, "stages": 1, "j_lanes": 16},
+    # packed split-j: two i-particles per lane group
+    {"i_per_thread": 2, "threads": 128, "j_tile": 256, "stages": 2, "j_lanes": 32},
+    {"i_per_thread": 2, "threads": 256, "j_tile": 128, "stages": 4, "j_lanes": 16, "chunk_units": 2},
     {"i_per_thread": 4, "threads": 128, "j_tile": 64, "stages": 1},
 ]
 

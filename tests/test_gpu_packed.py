@@ -53,6 +53,29 @@ def test_plain_packed_equals_scalar(potential):
             assert np.array_equal(p1, pk), k
 
 
+@pytest.mark.parametrize("potential", [False, True])
+@pytest.mark.parametrize("j_lanes", [8, 16, 32])
+def test_splitj_packed_equals_scalar(potential, j_lanes):
+    """Split-j shapes: lanes of a group take every j_lanes-th j record; the
+    packed form holds two i-particles per group."""
+    cn = lib()
+    torch = torch_cuda()
+    p = dev_tensor(synth.plummer(N, 82))
+    v = "f32_pot" if potential else "f32"
+
+    def run():
+        a, pot = cn.cn_force(p, p, 1e-3, potential=potential)
+        torch.cuda.synchronize()
+        return a.cpu().numpy(), (pot.cpu().numpy() if pot is not None else None)
+
+    shape = dict(_shape(1, threads=128), j_lanes=j_lanes)
+    a1, p1 = _with_tune(cn, [v], shape, run)
+    a2, p2 = _with_tune(cn, [v], dict(shape, i_per_thread=2), run)
+    assert np.array_equal(a1, a2)
+    if potential:
+        assert np.array_equal(p1, p2)
+
+
 def test_adjoint_packed_equals_scalar():
     cn = lib()
     torch = torch_cuda()
