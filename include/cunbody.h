@@ -92,10 +92,12 @@ typedef struct cn_tune {
     int32_t stages;       /* shared-memory ring depth: 1 .. 8 (1: one tile in flight at a time)   */
     int32_t ctas_per_sm;  /* resident CTAs per SM to launch (0 = occupancy maximum)               */
     int32_t chunk_units;  /* 0 = static schedule (equal share per CTA); > 0 = dynamic queue chunks
-                             of this many (i-tile x j-tile) units                                 */
-    int32_t j_lanes;      /* plain FP32 single-system form only: lanes sharing one i-particle
-                             (1, 2, 4, ..., 32; needs i_per_thread = 1 and j_tile a multiple of
-                             8 x j_lanes); their partial sums are combined by warp shuffles       */
+                             of this many (i-tile x j-tile) units. Symmetric form: tile rows per
+                             band (0 = one band while its slots fit in 2 GiB, else bands)       */
+    int32_t j_lanes;      /* plain FP32 single-system form only: lanes sharing the thread's
+                             i-particles (1, 2, 4, ..., 32; needs i_per_thread = 1 or 2 and
+                             j_tile a multiple of 8 x j_lanes); their partial sums are combined
+                             by warp shuffles                                                    */
 } cn_tune;
 
 /* ------------------------------------------------------------------ force */
@@ -195,10 +197,13 @@ CN_API cn_status cn_force_noalloc(int64_t n_i, const float *pos_i, int64_t n_j, 
  * Asynchronous on `stream`; n == 0 is a no-op. Errors: CN_ERR_INVALID_ARG
  * (n < 0, bad eps2, NULL or overlapping buffers, a tune with j_lanes),
  * CN_ERR_MISALIGNED, CN_ERR_CUDA (launch), CN_ERR_WORKSPACE (below).
- * Uses a library workspace of n_tiles x n_pad x 16 bytes, about 16 N^2 / B
+ * Uses a library workspace of per-(tile, partner) slots: 16 N^2 / B bytes
  * for tiles of B particles (134 MB at N = 131072 with the default
- * 2048-particle tiles, 8.6 GB at N = 2^20); returns CN_ERR_WORKSPACE when
- * the device cannot hold it (cn_force has no such growth).
+ * 2048-particle tiles) while that fits in 2 GiB; above, the tile rows are
+ * processed in bands of w rows (about 32 w N + 24 N bytes, w chosen to fit
+ * 2 GiB, or set by the tune's chunk_units), one kernel and one merge per
+ * band, with bitwise the same result. CN_ERR_WORKSPACE when even one band
+ * cannot be held.
  */
 CN_API cn_status cn_force_symmetric(int64_t n, const float *pos_mass, float eps2, float *acc_out, cn_stream stream);
 

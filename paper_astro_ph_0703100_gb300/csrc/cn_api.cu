@@ -3,6 +3,7 @@
 // plans, host-memory forms, tuning and status.
 #include "cunbody.h"
 #include "cn_kernels.h"
+#include "cn_sym.h"
 
 #include <algorithm>
 #include <atomic>
@@ -54,6 +55,7 @@ namespace {
 constexpr size_t kCtrlBytes = 4096;  // queue words and spare control space at the head of a workspace
 constexpr uint64_t kDefaultWaitNs = 2000000000ull;
 constexpr size_t kMaxSmem = 227 * 1024;
+constexpr size_t kSymSlotCap = static_cast<size_t>(2) << 30;  // symmetric-form slot memory before banding
 
 thread_local std::string g_last_error;
 std::atomic<uint64_t> g_wait_ns{kDefaultWaitNs};
@@ -708,33 +710,66 @@ cn_status symmetric_common(int64_t n, const float* pos_mass, float eps2, float* 
   cudaError_t e = cn::occupancy_sym(p.k, guard, p.threads, smem, &occ);
   if (e != cudaSuccess) return fail_cuda(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
   if (occ <= 0) return fail(CN_ERR_INVALID_ARG, "launch shape does not fit on one SM");
+  // Slots: one [T][n_pad] array (16 T n_pad bytes, ~16 N^2 / B) when it fits
+  // in kSymSlotCap, else bands of w tile rows: [T][w B] i-side and [w][n_pad]
+  // j-side slots plus FP64 running sums, ~32 w N + 24 N bytes. The tune's
+  // chunk_units, when set, fixes the rows per band.
+  const int64_t n_pad = T * B;
+  int64_t w = T;
+  if (p.chunk_units > 0)
+    w = std::min<int64_t>(p.chunk_units, T);
+  else if (static_cast<double>(T) * static_cast<double>(n_pad) * 16.0 > static_cast<double>(kSymSlotCap))
+    w = std::max<int64_t>(1, std::min<int64_t>(T, static_cast<int64_t>(kSymSlotCap / (32 * static_cast<size_t>(n_pad)))));
+  const bool banded = w < T;
+  const size_t islot_b = static_cast<size_t>(T) * static_cast<size_t>(banded ? w * B : n_pad) * 16;
+  const size_t jslot_b = banded ? align_up(static_cast<size_t>(w) * static_cast<size_t>(n_pad) * 16, 256) : 0;
+  const size_t acc64_b = banded ? static_cast<size_t>(n) * 24 : 0;
+  const size_t need = align_up(islot_b, 256) + jslot_b + acc64_b;
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && need > free_b + library_data_bytes(s))
+    return fail(CN_ERR_WORKSPACE, "symmetric form: the slot arrays do not fit in device memory");
+  char *ctrl = nullptr, *data = nullptr;
+  if ((st = library_workspace(s, kCtrlBytes, need, &ctrl, &data)) != CN_OK) return st;
   cn::SymArgs a{};
+  a.pos = reinterpret_cast<const float4*>(pos_mass);
+  a.slots_i = reinterpret_cast<float4*>(data);
+  a.slots_j = banded ? reinterpret_cast<float4*>(data + align_up(islot_b, 256)) : a.slots_i;
+  a.status = d->status;
   a.n = n;
-  a.n_pad = T * B;
+  a.n_pad = n_pad;
+  a.ld_i = banded ? w * B : n_pad;
   a.n_tiles = static_cast<int32_t>(T);
-  a.units = T * (T + 1) / 2;
   a.sub_tile = p.j_tile;
   a.stages = p.stages;
   a.eps2 = eps2;
-  a.pos = reinterpret_cast<const float4*>(pos_mass);
-  a.acc_out = acc_out;
-  a.status = d->status;
   a.wait_ns = g_wait_ns.load();
+  cn::SymMerge m{};
+  m.slots_i = a.slots_i;
+  m.slots_j = a.slots_j;
+  m.acc64 = banded ? reinterpret_cast<double*>(data + align_up(islot_b, 256) + jslot_b) : nullptr;
+  m.acc_out = acc_out;
+  m.n = n;
+  m.n_pad = n_pad;
+  m.ld_i = a.ld_i;
+  m.tile = static_cast<int32_t>(B);
+  m.n_tiles = static_cast<int32_t>(T);
   const int64_t slots = static_cast<int64_t>(p.ctas_per_sm > 0 ? std::min(p.ctas_per_sm, occ) : occ) * d->sms;
-  const int grid = static_cast<int>(std::min<int64_t>(slots, a.units));
-  // the slot array grows as N^2 / B (8.6 GB at N = 2^20, 137 GB at 2^22):
-  // refuse clearly when the device cannot hold it
-  const size_t slot_bytes = static_cast<size_t>(T) * static_cast<size_t>(a.n_pad) * 16;
-  size_t free_b = 0, total_b = 0;
-  if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && slot_bytes > free_b + library_data_bytes(s))
-    return fail(CN_ERR_WORKSPACE, "symmetric form: the per-tile slot array does not fit in device memory "
-                                  "(it grows as N^2 / tile); use cn_force for this N");
-  char *ctrl = nullptr, *data = nullptr;
-  if ((st = library_workspace(s, kCtrlBytes, slot_bytes, &ctrl, &data)) != CN_OK) return st;
-  a.slots = reinterpret_cast<float4*>(data);
-  if (inject("launch")) return fail(CN_ERR_CUDA, "kernel launch: injected launch failure");
-  e = cn::launch_sym(a, guard ? 1 : p.k, guard, p.threads, grid, smem, s);
-  return e == cudaSuccess ? CN_OK : fail_cuda(e, "symmetric kernel launch");
+  auto row_start = [T](int64_t r) { return r * T - r * (r - 1) / 2; };  // first unit of tile row r
+  for (int64_t r0 = 0; r0 < T; r0 += w) {
+    const int64_t r1 = std::min(T, r0 + w);
+    a.row0 = static_cast<int32_t>(r0);
+    a.unit_base = row_start(r0);
+    a.units = row_start(r1) - row_start(r0);
+    m.row0 = static_cast<int32_t>(r0);
+    m.row1 = static_cast<int32_t>(r1);
+    m.first = r0 == 0;
+    m.last = r1 == T;
+    const int grid = static_cast<int>(std::min<int64_t>(slots, a.units));
+    if (inject("launch")) return fail(CN_ERR_CUDA, "kernel launch: injected launch failure");
+    e = cn::launch_sym(a, m, guard ? 1 : p.k, guard, p.threads, grid, smem, s);
+    if (e != cudaSuccess) return fail_cuda(e, "symmetric kernel launch");
+  }
+  return CN_OK;
 }
 
 cn_status run_batched(const cn_batch_plan* plan, const float* pos_i, const float* pos_j, float* acc_out,

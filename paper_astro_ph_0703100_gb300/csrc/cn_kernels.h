@@ -59,22 +59,6 @@ struct PairArgs {
   uint64_t wait_ns;       // bound on every barrier wait
 };
 
-// Symmetric (each unordered pair once) evaluation of an i set equal to the j set.
-struct SymArgs {
-  const float4* pos;  // [n] (x, y, z, m)
-  float4* slots;      // [n_tiles][n_pad] partial sums: slot (tile P, partner Q) at Q * n_pad + p
-  float* acc_out;     // [n][3]
-  int* status;
-  int64_t n;
-  int64_t n_pad;      // n_tiles * tile
-  int64_t units;      // n_tiles * (n_tiles + 1) / 2
-  int32_t n_tiles;
-  int32_t sub_tile;   // j records per ring stage (divides the tile, multiple of 8)
-  int32_t stages;
-  float eps2;
-  uint64_t wait_ns;
-};
-
 // Tuning knobs of one launch (mirrors cn_tune of the public header).
 struct Plan {
   int k = 4;              // i-particles per thread
@@ -97,7 +81,7 @@ enum Variant : int {
   kBatchedPot = 6,
   kJerk = 7,
   kJerkPot = 8,
-  kSym = 9,
+  kSym = 9,  // symmetric form (cn_sym.h)
 };
 
 // Kernel selection, occupancy and launch (defined in the per-variant
@@ -111,9 +95,6 @@ cudaError_t launch_adjoint(const PairArgs& a, const Plan& p, bool guard, int gri
 cudaError_t occupancy_adjoint(const Plan& p, bool guard, size_t smem, int* ctas);
 cudaError_t launch_pack_w(const float* w, float4* wrec, int64_t n, cudaStream_t s);
 cudaError_t launch_jerk(const PairArgs& a, const Plan& p, bool pot, bool guard, int grid, cudaStream_t s);
-size_t sym_smem_bytes(int threads, int k, int sub_tile, int stages);
-cudaError_t occupancy_sym(int k, bool guard, int threads, size_t smem, int* ctas);
-cudaError_t launch_sym(const SymArgs& a, int k, bool guard, int threads, int grid, size_t smem, cudaStream_t s);
 cudaError_t occupancy_jerk(const Plan& p, bool pot, bool guard, size_t smem, int* ctas);
 cudaError_t launch_energy(int64_t n, const float4* pos_mass, const float* pot_f, const double* pot_d,
                           double* partials, int* counter, double* w_out, cudaStream_t s);

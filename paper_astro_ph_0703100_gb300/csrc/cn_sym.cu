@@ -16,7 +16,10 @@
 // one-sided loop. Every unit writes its i-side sums to slot (I, J) and its
 // j-side sums to slot (J, I) of a [tiles][n_pad] float4 array; a second
 // kernel adds the slots of each particle in partner order in FP64 - a
-// deterministic result with no atomics on data.
+// deterministic result with no atomics on data. That array grows as N^2 / B;
+// when it would be too large the rows of tiles are processed in bands, each
+// band merged into FP64 running sums in the same partner order, so the
+// result is bitwise the same.
 //
 // The i-particles of a thread are held in pairs and the pair terms are
 // evaluated with packed f32x2 instructions (two i-particles per 64-bit
@@ -24,7 +27,7 @@
 // instructions and 2 MUFU per two unordered pairs. The two halves of a
 // thread's j-side sum are added before the warp reduction.
 #include "cn_device.cuh"
-#include "cn_kernels.h"
+#include "cn_sym.h"
 
 namespace cn {
 
@@ -89,8 +92,8 @@ __global__ void __launch_bounds__(NTMAX, sym_min_blocks(NTMAX)) sym_kernel(const
 
   const int64_t U = a.units;
   const int64_t G = gridDim.x;
-  const int64_t ub = (static_cast<int64_t>(blockIdx.x) * U) / G;
-  const int64_t ue = (static_cast<int64_t>(blockIdx.x + 1) * U) / G;
+  const int64_t ub = a.unit_base + (static_cast<int64_t>(blockIdx.x) * U) / G;
+  const int64_t ue = a.unit_base + (static_cast<int64_t>(blockIdx.x + 1) * U) / G;
   const uint32_t n_loads = static_cast<uint32_t>((ue - ub) * subs);
   const uint32_t D = S > 2 ? static_cast<uint32_t>(S - 2) : static_cast<uint32_t>(S - 1);
   uint32_t issued = 0, consumed = 0;
@@ -271,8 +274,8 @@ __global__ void __launch_bounds__(NTMAX, sym_min_blocks(NTMAX)) sym_kernel(const
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      const int64_t p = static_cast<int64_t>(I) * B + k * NT + tid;
-      a.slots[static_cast<size_t>(J) * a.n_pad + p] =
+      const int64_t p = static_cast<int64_t>(I - a.row0) * B + k * NT + tid;
+      a.slots_i[static_cast<size_t>(J) * a.ld_i + p] =
           make_float4(half(acc[k >> 1][0], k), half(acc[k >> 1][1], k), half(acc[k >> 1][2], k), 0.f);
     }
     if (!diag) {
@@ -285,7 +288,7 @@ __global__ void __launch_bounds__(NTMAX, sym_min_blocks(NTMAX)) sym_kernel(const
           sz += r[2];
         }
         const int64_t p = static_cast<int64_t>(J) * B + jl;
-        a.slots[static_cast<size_t>(I) * a.n_pad + p] = make_float4(sx, sy, sz, 0.f);
+        a.slots_j[static_cast<size_t>(I - a.row0) * a.n_pad + p] = make_float4(sx, sy, sz, 0.f);
       }
     }
     __syncthreads();
@@ -300,21 +303,45 @@ __global__ void __launch_bounds__(NTMAX, sym_min_blocks(NTMAX)) sym_kernel(const
   }
 }
 
-// acc[p] = sum over partner tiles Q (in order) of slots[Q][p], in FP64.
-__global__ void sym_merge_kernel(const float4* __restrict__ slots, int64_t n, int64_t n_pad, int32_t n_tiles,
-                                 float* __restrict__ acc) {
+// Per-particle merge of one band (see SymMerge): partners in ascending
+// order, FP64 sums carried across bands.
+__global__ void sym_merge_kernel(const SymMerge m) {
   const int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-  if (p >= n) return;
+  if (p >= m.n) return;
   double sx = 0.0, sy = 0.0, sz = 0.0;
-  for (int32_t q = 0; q < n_tiles; ++q) {
-    const float4 v = __ldcs(slots + static_cast<size_t>(q) * n_pad + p);
+  if (!m.first) {
+    sx = m.acc64[3 * p + 0];
+    sy = m.acc64[3 * p + 1];
+    sz = m.acc64[3 * p + 2];
+  }
+  const int32_t P = static_cast<int32_t>(p / m.tile);
+  // j-side: units (I, P) of the band with I < P
+  const int32_t jend = P < m.row1 ? P : m.row1;
+  for (int32_t q = m.row0; q < jend; ++q) {
+    const float4 v = __ldcs(m.slots_j + static_cast<size_t>(q - m.row0) * m.n_pad + p);
     sx += v.x;
     sy += v.y;
     sz += v.z;
   }
-  acc[3 * p + 0] = static_cast<float>(sx);
-  acc[3 * p + 1] = static_cast<float>(sy);
-  acc[3 * p + 2] = static_cast<float>(sz);
+  // i-side: units (P, Q) with Q >= P, when P is one of the band's rows
+  if (P >= m.row0 && P < m.row1) {
+    const int64_t pl = p - static_cast<int64_t>(m.row0) * m.tile;
+    for (int32_t q = P; q < m.n_tiles; ++q) {
+      const float4 v = __ldcs(m.slots_i + static_cast<size_t>(q) * m.ld_i + pl);
+      sx += v.x;
+      sy += v.y;
+      sz += v.z;
+    }
+  }
+  if (m.last) {
+    m.acc_out[3 * p + 0] = static_cast<float>(sx);
+    m.acc_out[3 * p + 1] = static_cast<float>(sy);
+    m.acc_out[3 * p + 2] = static_cast<float>(sz);
+  } else {
+    m.acc64[3 * p + 0] = sx;
+    m.acc64[3 * p + 1] = sy;
+    m.acc64[3 * p + 2] = sz;
+  }
 }
 
 template <int K, bool GUARD>
@@ -351,7 +378,8 @@ cudaError_t occupancy_sym(int k, bool guard, int threads, size_t smem, int* ctas
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, f, threads, smem);
 }
 
-cudaError_t launch_sym(const SymArgs& a, int k, bool guard, int threads, int grid, size_t smem, cudaStream_t s) {
+cudaError_t launch_sym(const SymArgs& a, const SymMerge& m, int k, bool guard, int threads, int grid, size_t smem,
+                       cudaStream_t s) {
   const void* f = sym_select(k, guard, threads);
   if (!f) return cudaErrorInvalidValue;
   cudaError_t e = prepare_kernel(f, smem);
@@ -360,8 +388,8 @@ cudaError_t launch_sym(const SymArgs& a, int k, bool guard, int threads, int gri
   e = cudaLaunchKernel(f, dim3(grid), dim3(threads), args, smem, s);
   if (e != cudaSuccess) return e;
   const int mt = 256;
-  const int64_t mb = (a.n + mt - 1) / mt;
-  sym_merge_kernel<<<static_cast<unsigned>(mb), mt, 0, s>>>(a.slots, a.n, a.n_pad, a.n_tiles, a.acc_out);
+  const int64_t mb = (m.n + mt - 1) / mt;
+  sym_merge_kernel<<<static_cast<unsigned>(mb), mt, 0, s>>>(m);
   return cudaGetLastError();
 }
 

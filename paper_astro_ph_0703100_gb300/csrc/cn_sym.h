@@ -1,0 +1,60 @@
+// Symmetric (each unordered pair once) evaluation of an i set equal to the
+// j set: launch arguments and entry points of cn_sym.cu.
+#pragma once
+
+#include "cn_kernels.h"
+
+namespace cn {
+
+// One launch covers the tile rows I in [row0, row0 + band) of the upper
+// triangle of tile pairs (I <= J), i.e. units unit_base .. unit_base + units
+// - 1 of the row-major numbering. Unit (I, J) writes its i-side sums (tile
+// I, partner J) to slots_i[J * ld_i + p - row0 * tile] and its j-side sums
+// (tile J, partner I) to slots_j[(I - row0) * n_pad + p]. With one band
+// covering every row, slots_i == slots_j and ld_i == n_pad: one
+// [n_tiles][n_pad] array with slot (tile P, partner Q) at Q * n_pad + p.
+struct SymArgs {
+  const float4* pos;  // [n] (x, y, z, m)
+  float4* slots_i;
+  float4* slots_j;
+  int* status;
+  int64_t n;
+  int64_t n_pad;      // n_tiles * tile
+  int64_t ld_i;       // row stride of slots_i (particles of the band's tiles)
+  int64_t unit_base;  // first unit of the launch (row-major over I <= J)
+  int64_t units;      // units of the launch
+  int32_t n_tiles;
+  int32_t row0;       // first tile row of the launch
+  int32_t sub_tile;   // j records per ring stage (divides the tile, multiple of 8)
+  int32_t stages;
+  float eps2;
+  uint64_t wait_ns;
+};
+
+// Per-particle merge of one band: adds, in FP64 and in ascending partner
+// order, the band's j-side slots (partners I in [row0, row1), I < P) and,
+// for particles of the band's own tiles, their i-side slots (partners
+// Q >= P) to the running sums (acc64, or zero for the first band); the last
+// band writes the FP32 accelerations, the others store the FP64 sums.
+struct SymMerge {
+  const float4* slots_i;
+  const float4* slots_j;
+  double* acc64;     // [n][3], NULL with a single band
+  float* acc_out;    // [n][3]
+  int64_t n;
+  int64_t n_pad;
+  int64_t ld_i;
+  int32_t tile;
+  int32_t n_tiles;
+  int32_t row0;
+  int32_t row1;
+  int32_t first;
+  int32_t last;
+};
+
+size_t sym_smem_bytes(int threads, int k, int sub_tile, int stages);
+cudaError_t occupancy_sym(int k, bool guard, int threads, size_t smem, int* ctas);
+cudaError_t launch_sym(const SymArgs& a, const SymMerge& m, int k, bool guard, int threads, int grid, size_t smem,
+                       cudaStream_t s);
+
+}  // namespace cn

@@ -90,6 +90,30 @@ def test_symmetric_deterministic_and_matches_plain_form():
     assert e_max(plain.cpu().numpy(), ref) <= TOL
 
 
+@pytest.mark.parametrize("rows", [1, 2, 3])
+def test_symmetric_bands_bitwise_equal_one_band(rows):
+    """Banded evaluation (chunk_units = tile rows per band) merges partners in
+    the same order in FP64, so it reproduces the one-band result bit for bit."""
+    cn = lib()
+    torch = torch_cuda()
+    n = 5000
+    p = synth.hernquist(n, 9)
+    d = dev_tensor(p)
+    shape = {"i_per_thread": 2, "threads": 64, "j_tile": 64, "stages": 3}
+    cn.cn_tune_set("symmetric", n, n, shape)
+    try:
+        one = cn.cn_force_symmetric(d, 1e-4)
+        cn.cn_tune_set("symmetric", n, n, dict(shape, chunk_units=rows))
+        banded = cn.cn_force_symmetric(d, 1e-4)
+        torch.cuda.synchronize()
+    finally:
+        cn.cn_tune_set("symmetric", n, n, None)
+    assert cn.cn_get_device_status() == 0
+    assert torch.equal(one, banded)
+    ref, _ = oracle.force(p, p, 1e-4, potential=False)
+    assert e_max(banded.cpu().numpy(), ref) <= TOL
+
+
 def test_symmetric_empty():
     cn = lib()
     torch = torch_cuda()
@@ -115,5 +139,18 @@ def test_symmetric_plummer_131072_sampled():
     eps2 = float(np.float32(synth.plummer_eps(n)) ** 2)
     a = run(cn, p, eps2)
     rows = synth.sample_rows(n, 512, 7)
+    ref, _ = oracle.force(p, p, eps2, rows=rows, potential=False)
+    assert e_max(a[rows], ref) <= TOL
+
+
+def test_symmetric_million_automatic_bands_sampled():
+    """N = 2^20: the one-band slot array (8.6 GB) exceeds the 2 GiB budget, so
+    the rows run in bands; sampled rows against the oracle."""
+    cn = lib()
+    n = 1 << 20
+    p = synth.plummer(n, 20)
+    eps2 = float(np.float32(synth.plummer_eps(n)) ** 2)
+    a = run(cn, p, eps2)
+    rows = synth.sample_rows(n, 256, 21)
     ref, _ = oracle.force(p, p, eps2, rows=rows, potential=False)
     assert e_max(a[rows], ref) <= TOL
