@@ -101,10 +101,10 @@ __global__ void __launch_bounds__(NTMAX, sym_min_blocks(NTMAX)) sym_kernel(const
   const int perm = (((lane >> 4) & 1) << 2) | (((lane >> 3) & 1) << 1) | ((lane >> 2) & 1);
 
   // i-particles in pairs (packed f32x2 arithmetic, as in the plain kernel's
-  // packed form): negated coordinates, masses and their negatives
+  // packed form): negated coordinates and negated masses
   static_assert(K == 1 || K % 2 == 0, "K is 1 or even");
   constexpr int P = (K + 1) / 2;
-  float2 nxi[P][3], mi[P], nmi[P], acc[P][3];
+  float2 nxi[P][3], nmi[P], acc[P][3];
   auto half = [](float2& v, int k) -> float& { return (k & 1) ? v.y : v.x; };
   int32_t cur_I = -1;
   for (int64_t u = ub; u < ue; ++u) {
@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(NTMAX, sym_min_blocks(NTMAX)) sym_kernel(const
 #pragma unroll
         for (int c = 0; c < 3; ++c) nxi[p][c] = make_float2(0.f, 0.f);
 #pragma unroll
-      for (int p = 0; p < P; ++p) mi[p] = nmi[p] = make_float2(0.f, 0.f);
+      for (int p = 0; p < P; ++p) nmi[p] = make_float2(0.f, 0.f);
 #pragma unroll
       for (int k = 0; k < K; ++k) {
         const int64_t p = static_cast<int64_t>(I) * B + k * NT + tid;
@@ -126,7 +126,6 @@ __global__ void __launch_bounds__(NTMAX, sym_min_blocks(NTMAX)) sym_kernel(const
         half(nxi[k >> 1][0], k) = -v.x;
         half(nxi[k >> 1][1], k) = -v.y;
         half(nxi[k >> 1][2], k) = -v.z;
-        half(mi[k >> 1], k) = v.w;
         half(nmi[k >> 1], k) = -v.w;
       }
       cur_I = I;
