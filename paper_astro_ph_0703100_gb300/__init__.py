@@ -24,11 +24,22 @@ __all__ = [
     "VARIANT",
     "cn_force",
     "cn_force_ws",
+    "cn_force_noalloc",
     "cn_force_dd",
     "cn_force_dd_ws",
     "cn_workspace_bytes",
     "cn_force_symmetric",
     "BatchPlan",
+    "cn_batch_plan_create",
+    "cn_batch_plan_destroy",
+    "cn_batch_plan_workspace_bytes",
+    "cn_batch_plan_info",
+    "cn_batch_plan_capture",
+    "cn_batch_plan_launch",
+    "cn_list_plan_create",
+    "cn_list_plan_capture",
+    "cn_status_string",
+    "cn_last_error_message",
     "cn_force_batched",
     "ListPlan",
     "cn_force_lists",
@@ -131,6 +142,13 @@ def _force(fn, double, pos_i, pos_mass_j, eps2, acc_out, pot_out, potential, str
 def cn_force(pos_i, pos_mass_j, eps2, acc_out=None, pot_out=None, potential=False, stream=None):
     """FP32 accelerations (n_i, 3) and, if requested, potentials (n_i,)."""
     return _force("cn_force", False, pos_i, pos_mass_j, eps2, acc_out, pot_out, potential, stream)
+
+
+def cn_force_noalloc(pos_i, pos_mass_j, eps2, acc_out=None, pot_out=None, potential=False, stream=None):
+    """cn_force with the library's fixed static device scratch: the library
+    allocates no device memory in the call (outputs not given are PyTorch
+    tensors); calls that overlap in time share the scratch and must not."""
+    return _force("cn_force_noalloc", False, pos_i, pos_mass_j, eps2, acc_out, pot_out, potential, stream)
 
 
 def cn_force_ws(pos_i, pos_mass_j, eps2, workspace, acc_out=None, pot_out=None, potential=False, stream=None):
@@ -337,6 +355,49 @@ def cn_force_lists(plan: ListPlan, pos_i, pos_mass_j, acc_out=None, pot_out=None
 
 
 # ------------------------------------------------------------------ adjoint, energy
+
+# Functions with the names of the plan entry points of the C ABI (the plan
+# objects above hold the handle and call them).
+def cn_batch_plan_create(offsets, eps2, tune=None, potential=False) -> BatchPlan:
+    return BatchPlan(offsets, eps2, tune=tune, potential=potential)
+
+
+def cn_list_plan_create(i_offsets, j_begin, j_count, eps2, tune=None, potential=False) -> ListPlan:
+    return ListPlan(i_offsets, j_begin, j_count, eps2, tune=tune, potential=potential)
+
+
+def cn_batch_plan_destroy(plan) -> None:
+    plan.close()
+
+
+def cn_batch_plan_workspace_bytes(plan) -> int:
+    return plan.workspace_bytes
+
+
+def cn_batch_plan_info(plan):
+    """(i-particles, pair count) of a cluster or list plan."""
+    return (plan.n_total if isinstance(plan, BatchPlan) else plan.n_i), plan.pairs
+
+
+def cn_batch_plan_capture(plan: BatchPlan, pos_mass, acc_out, pot_out=None, workspace=None, stream=None):
+    return plan.capture(pos_mass, acc_out, pot_out=pot_out, workspace=workspace, stream=stream)
+
+
+def cn_list_plan_capture(plan: ListPlan, pos_i, pos_mass_j, acc_out, pot_out=None, workspace=None, stream=None):
+    return plan.capture(pos_i, pos_mass_j, acc_out, pot_out=pot_out, workspace=workspace, stream=stream)
+
+
+def cn_batch_plan_launch(plan, stream=None) -> None:
+    plan.launch(stream)
+
+
+def cn_status_string(status: int) -> str:
+    return load().cn_status_string(int(status)).decode()
+
+
+def cn_last_error_message() -> str:
+    return load().cn_last_error_message().decode()
+
 
 def cn_force_adjoint(pos_mass, eps2, w, grad_pos=None, grad_mass=None, stream=None):
     """dL/dx (n, 3) and dL/dm (n,) for L = sum_i w_i . a_i with i set = j set."""

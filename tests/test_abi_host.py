@@ -152,3 +152,15 @@ def test_binding_fails_loudly_without_library(tmp_path):
             _lib.load(str(tmp_path / "missing.so"))
         finally:
             _lib._lib = _lib._lib_saved
+
+
+def test_binding_has_every_entry_point_by_name():
+    """The Python binding offers each C entry point under the same name."""
+    import re
+
+    import paper_astro_ph_0703100_gb300 as cn
+
+    with open(os.path.join(ROOT, "include", "cunbody.h")) as f:
+        names = re.findall(r"CN_API\s+[\w\s\*]+?\b(cn_\w+)\s*\(", f.read())
+    assert len(names) >= 30
+    assert [n for n in names if not hasattr(cn, n)] == []

@@ -67,3 +67,19 @@ def test_noalloc_rejects_problems_beyond_the_static_scratch():
                             None)
     assert st == 6  # CN_ERR_WORKSPACE
     assert b"static scratch" in L.cn_last_error_message()
+
+
+def test_noalloc_python_binding():
+    """The binding of the same name: outputs given or allocated by PyTorch."""
+    cn = lib()
+    torch = torch_cuda()
+    pi = dev_tensor(synth.plummer(3000, 4))
+    ref, ref_pot = cn.cn_force(pi, pi, 1e-3, potential=True)
+    acc = torch.empty((3000, 3), device="cuda")
+    a1, _ = cn.cn_force_noalloc(pi, pi, 1e-3, acc_out=acc)
+    a2, p2 = cn.cn_force_noalloc(pi, pi, 1e-3, potential=True)
+    torch.cuda.synchronize()
+    assert a1.data_ptr() == acc.data_ptr()
+    assert e_max(a1.cpu().numpy(), ref.cpu().numpy().astype(np.float64)) <= TOL_F32
+    assert e_max(a2.cpu().numpy(), ref.cpu().numpy().astype(np.float64)) <= TOL_F32
+    assert rel_pot_err(p2.cpu().numpy(), ref_pot.cpu().numpy()) <= TOL_F32
