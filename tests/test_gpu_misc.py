@@ -114,3 +114,27 @@ def test_host_fault_injection(monkeypatch):
     acc, _ = cn.cn_force(t, t, 1e-2)
     torch.cuda.synchronize()
     assert torch.isfinite(acc).all()
+
+
+def test_plan_functions_of_the_binding():
+    """The module-level plan functions (the C names) drive the same plans."""
+    cn = lib()
+    torch = torch_cuda()
+    rec, offs, eps2 = synth.ensemble(6, 31, n_lo=100, n_hi=900)
+    t = dev_tensor(rec)
+    plan = cn.cn_batch_plan_create(offs, eps2)
+    n_total, pairs = cn.cn_batch_plan_info(plan)
+    assert n_total == rec.shape[0] and pairs == float((np.diff(offs).astype(float) ** 2).sum())
+    ws = torch.zeros(max(cn.cn_batch_plan_workspace_bytes(plan), 256), dtype=torch.uint8, device="cuda")
+    acc = torch.empty((n_total, 3), device="cuda")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        cn.cn_batch_plan_capture(plan, t, acc, workspace=ws, stream=s)
+        cn.cn_batch_plan_launch(plan, s)
+    torch.cuda.synchronize()
+    ref, _ = cn.cn_force_batched(plan, t)
+    torch.cuda.synchronize()
+    assert torch.equal(acc, ref)
+    cn.cn_batch_plan_destroy(plan)
+    assert cn.cn_status_string(0) and cn.cn_status_string(1) != cn.cn_status_string(0)
+    assert isinstance(cn.cn_last_error_message(), str)
