@@ -53,6 +53,8 @@ def _load():
         lib.oracle_force_rows.argtypes = [ctypes.c_int64, _i64p, _f32p, ctypes.c_int64, _f32p,
                                           ctypes.c_float, _f64p, _f64p]
         lib.oracle_force_rows.restype = None
+        lib.oracle_force_rows_eps_i.argtypes = [ctypes.c_int64, _i64p, _f32p, ctypes.c_int64, _f32p, _f64p, _f64p]
+        lib.oracle_force_rows_eps_i.restype = None
         lib.oracle_potential_energy.argtypes = [ctypes.c_int64, _f32p, _f64p]
         lib.oracle_potential_energy.restype = ctypes.c_double
         lib.oracle_adjoint_rows.argtypes = [ctypes.c_int64, _i64p, ctypes.c_int64, _f32p,
@@ -113,6 +115,29 @@ def force(pos_i, pos_mass_j, eps2, rows=None, potential: bool = True):
     pot = np.zeros(n_rows, dtype=np.float64) if potential else None
     lib.oracle_force_rows(n_rows, _ptr(rp, _i64p), _ptr(pi, _f32p), pj.shape[0], _ptr(pj, _f32p),
                           float(np.float32(eps2)), _ptr(acc, _f64p), _ptr(pot, _f64p))
+    return acc, pot
+
+
+def force_eps_i(pos_eps_i, pos_mass_j, rows=None, potential: bool = True):
+    """Eq. 1 with a softening per i-particle, taken from the 4th component of
+    its record (x, y, z, eps2_i) as in the appendix's force driver.
+
+    Returns ``(acc[n_rows, 3], pot[n_rows] or None)`` as float64.
+    """
+    lib = _load()
+    pi = _rec(pos_eps_i)
+    pj = _rec(pos_mass_j)
+    if rows is None:
+        n_rows, rp = pi.shape[0], None
+    else:
+        rows = np.ascontiguousarray(rows, dtype=np.int64)
+        if rows.size and (rows.min() < 0 or rows.max() >= pi.shape[0]):
+            raise IndexError("row index out of range")
+        n_rows, rp = rows.shape[0], rows
+    acc = np.zeros((n_rows, 3), dtype=np.float64)
+    pot = np.zeros(n_rows, dtype=np.float64) if potential else None
+    lib.oracle_force_rows_eps_i(n_rows, _ptr(rp, _i64p), _ptr(pi, _f32p), pj.shape[0], _ptr(pj, _f32p),
+                                _ptr(acc, _f64p), _ptr(pot, _f64p))
     return acc, pot
 
 

@@ -77,10 +77,40 @@ void oracle_set_threads(int n)
 }
 
 /*
- * Eq. 1 of Section 1.1 (acceleration) plus the potential:
+ * Eq. 1 of Section 1.1 (acceleration) plus the potential for one i-particle
+ * at (xi, yi, zi) with softening eps2:
  *   a_i   =  sum_j m_j (x_j - x_i) / (|x_j - x_i|^2 + eps2)^(3/2)
  *   phi_i = -sum_{j : x_j != x_i} m_j / (|x_j - x_i|^2 + eps2)^(1/2)
- *
+ * out[0..2] = a_i, out[3] = phi_i (when want_pot).
+ */
+static void force_row(double xi, double yi, double zi, double eps2, int64_t n_j, const float *pos_mass_j,
+                      int want_pot, double out[4])
+{
+    nsum ax = {0, 0}, ay = {0, 0}, az = {0, 0}, ph = {0, 0};
+    for (int64_t j = 0; j < n_j; ++j) {
+        const double dx = (double)pos_mass_j[4 * j + 0] - xi;
+        const double dy = (double)pos_mass_j[4 * j + 1] - yi;
+        const double dz = (double)pos_mass_j[4 * j + 2] - zi;
+        const double mj = pos_mass_j[4 * j + 3];
+        const double s = dx * dx + dy * dy + dz * dz + eps2;
+        if (s == 0.0)
+            continue;
+        const double root = sqrt(s);
+        const double f = mj / (s * root); /* m_j / s^(3/2) */
+        nsum_add(&ax, f * dx);
+        nsum_add(&ay, f * dy);
+        nsum_add(&az, f * dz);
+        if (want_pot && !(dx == 0.0 && dy == 0.0 && dz == 0.0))
+            nsum_add(&ph, -mj / root);
+    }
+    out[0] = nsum_value(&ax);
+    out[1] = nsum_value(&ay);
+    out[2] = nsum_value(&az);
+    out[3] = nsum_value(&ph);
+}
+
+/*
+ * Eq. 1 for the listed i-particles with one softening for all pairs.
  * rows: indices of the i-particles to evaluate (NULL means 0 .. n_rows-1).
  * pos_i: FP32 [*, 4] records (the 4th component is ignored).
  * pos_mass_j: FP32 [n_j, 4] records (x, y, z, m).
@@ -95,31 +125,38 @@ void oracle_force_rows(int64_t n_rows, const int64_t *rows, const float *pos_i,
 #pragma omp parallel for schedule(dynamic, 16)
     for (r = 0; r < n_rows; ++r) {
         const int64_t i = rows ? rows[r] : r;
-        const double xi = pos_i[4 * i + 0];
-        const double yi = pos_i[4 * i + 1];
-        const double zi = pos_i[4 * i + 2];
-        nsum ax = {0, 0}, ay = {0, 0}, az = {0, 0}, ph = {0, 0};
-        for (int64_t j = 0; j < n_j; ++j) {
-            const double dx = (double)pos_mass_j[4 * j + 0] - xi;
-            const double dy = (double)pos_mass_j[4 * j + 1] - yi;
-            const double dz = (double)pos_mass_j[4 * j + 2] - zi;
-            const double mj = pos_mass_j[4 * j + 3];
-            const double s = dx * dx + dy * dy + dz * dz + eps2;
-            if (s == 0.0)
-                continue;
-            const double root = sqrt(s);
-            const double f = mj / (s * root); /* m_j / s^(3/2) */
-            nsum_add(&ax, f * dx);
-            nsum_add(&ay, f * dy);
-            nsum_add(&az, f * dz);
-            if (pot && !(dx == 0.0 && dy == 0.0 && dz == 0.0))
-                nsum_add(&ph, -mj / root);
-        }
-        acc[3 * r + 0] = nsum_value(&ax);
-        acc[3 * r + 1] = nsum_value(&ay);
-        acc[3 * r + 2] = nsum_value(&az);
+        double out[4];
+        force_row(pos_i[4 * i + 0], pos_i[4 * i + 1], pos_i[4 * i + 2], eps2, n_j, pos_mass_j, pot != NULL, out);
+        acc[3 * r + 0] = out[0];
+        acc[3 * r + 1] = out[1];
+        acc[3 * r + 2] = out[2];
         if (pot)
-            pot[r] = nsum_value(&ph);
+            pot[r] = out[3];
+    }
+}
+
+/*
+ * Eq. 1 with a softening per i-particle: the i record of the appendix's
+ * force driver is (x, y, z, eps2) (IDIM = 4, the driver fills the 4th slot
+ * with eps2), and the force pipeline adds that i-particle's eps2 to the
+ * squared distance of each of its pairs. pos_eps_i: FP32 [*, 4] records
+ * (x, y, z, eps2_i); everything else as oracle_force_rows.
+ */
+void oracle_force_rows_eps_i(int64_t n_rows, const int64_t *rows, const float *pos_eps_i,
+                             int64_t n_j, const float *pos_mass_j, double *acc, double *pot)
+{
+    int64_t r;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (r = 0; r < n_rows; ++r) {
+        const int64_t i = rows ? rows[r] : r;
+        double out[4];
+        force_row(pos_eps_i[4 * i + 0], pos_eps_i[4 * i + 1], pos_eps_i[4 * i + 2], (double)pos_eps_i[4 * i + 3],
+                  n_j, pos_mass_j, pot != NULL, out);
+        acc[3 * r + 0] = out[0];
+        acc[3 * r + 1] = out[1];
+        acc[3 * r + 2] = out[2];
+        if (pot)
+            pot[r] = out[3];
     }
 }
 

@@ -96,12 +96,14 @@ def test_empty_sets():
 # ---------------------------------------------------------------- brute force
 
 def _decimal_force(p, eps2, prec=50):
+    """eps2: one softening for every pair, or one per i-particle."""
     ctx = decimal.Context(prec=prec)
     D = decimal.Decimal
     n = p.shape[0]
-    e2 = D(float(np.float32(eps2)))
+    e2s = np.broadcast_to(np.asarray(eps2, dtype=np.float32), (n,))
     out = []
     for i in range(n):
+        e2 = D(float(e2s[i]))
         acc = [D(0), D(0), D(0)]
         pot = D(0)
         for j in range(n):
@@ -128,6 +130,37 @@ def test_bruteforce_50_digits(n, seed, eps2):
     p[:, 3] = rng.uniform(0.1, 2.0, size=n).astype(np.float32)
     a, phi = oracle.force(p, p, eps2)
     ref = _decimal_force(p, eps2)
+    for i in range(n):
+        assert a[i] == pytest.approx(ref[i][0], rel=1e-14, abs=1e-14 * np.abs(ref[i][0]).max())
+        assert phi[i] == pytest.approx(ref[i][1], rel=1e-14)
+
+
+def test_eps_i_two_body_closed_form():
+    """Softening per i-particle (the i record's 4th slot): each particle of a
+    3-4-5 pair feels its own softened distance, sqrt(25 + 144) = 13 and 5."""
+    m1, m2 = 0.5, 0.75
+    pj = rec([[1.0, -2.0, 0.5], [4.0, 2.0, 0.5]], [m1, m2])
+    pi = pj.copy()
+    pi[:, 3] = [144.0, 0.0]
+    a, phi = oracle.force_eps_i(pi, pj)
+    assert a[0] == pytest.approx([m2 * 3 / 2197, m2 * 4 / 2197, 0.0], rel=1e-15, abs=0)
+    assert phi[0] == pytest.approx(-m2 / 13, rel=1e-15)
+    assert a[1] == pytest.approx([-m1 * 3 / 125, -m1 * 4 / 125, 0.0], rel=1e-15, abs=0)
+    assert phi[1] == pytest.approx(-m1 / 5, rel=1e-15)
+
+
+@pytest.mark.parametrize("n,seed", [(6, 17), (8, 19)])
+def test_eps_i_bruteforce_50_digits(n, seed):
+    rng = np.random.default_rng(seed)
+    pj = np.empty((n, 4), dtype=np.float32)
+    pj[:, :3] = rng.normal(size=(n, 3)).astype(np.float32)
+    pj[:, 3] = rng.uniform(0.1, 2.0, size=n).astype(np.float32)
+    eps2 = rng.uniform(0.0, 0.5, size=n).astype(np.float32)
+    eps2[0] = 0.0
+    pi = pj.copy()
+    pi[:, 3] = eps2
+    a, phi = oracle.force_eps_i(pi, pj)
+    ref = _decimal_force(pj, eps2)
     for i in range(n):
         assert a[i] == pytest.approx(ref[i][0], rel=1e-14, abs=1e-14 * np.abs(ref[i][0]).max())
         assert phi[i] == pytest.approx(ref[i][1], rel=1e-14)
