@@ -81,7 +81,9 @@ typedef enum cn_variant {
     CN_VARIANT_BATCHED_POT = 6, /* cn_force_batched with potential */
     CN_VARIANT_JERK = 7,        /* cn_force_jerk without potential */
     CN_VARIANT_JERK_POT = 8,    /* cn_force_jerk with potential    */
-    CN_VARIANT_SYMMETRIC = 9    /* cn_force_symmetric              */
+    CN_VARIANT_SYMMETRIC = 9,   /* cn_force_symmetric              */
+    CN_VARIANT_F32_EPS_I = 10,  /* cn_force_eps_i without potential */
+    CN_VARIANT_F32_EPS_I_POT = 11 /* cn_force_eps_i with potential */
 } cn_variant;
 
 /* Launch shape of the pair kernels. Zero in a field means "library default". */
@@ -179,6 +181,23 @@ CN_API size_t cn_workspace_bytes(int variant, int64_t n_i, int64_t n_j);
  */
 CN_API cn_status cn_force_noalloc(int64_t n_i, const float *pos_i, int64_t n_j, const float *pos_mass_j, float eps2,
                                   float *acc_out, float *pot_out, cn_stream stream);
+
+/*
+ * cn_force with a softening per i-particle, as in the appendix's force
+ * pipeline, whose i record is (x, y, z, eps2) (IDIM = 4): every pair (i, j)
+ * uses the squared softening eps2_i of its i-particle.
+ *   pos_eps_i  : float[n_i][4] device records (x, y, z, eps2_i), 16-byte
+ *                aligned; each eps2_i finite and >= 0 (not checked: the
+ *                values are on the device). A pair with s = 0 (eps2_i = 0
+ *                and coincident points) contributes nothing.
+ *   pos_mass_j, acc_out, pot_out, stream: as cn_force.
+ * Same kernels and launch shapes as cn_force (tuned under
+ * CN_VARIANT_F32_EPS_I / _POT), always with the s = 0 guard; with every
+ * eps2_i equal to one value the results are bitwise those of cn_force.
+ * Errors as cn_force.
+ */
+CN_API cn_status cn_force_eps_i(int64_t n_i, const float *pos_eps_i, int64_t n_j, const float *pos_mass_j,
+                                float *acc_out, float *pot_out, cn_stream stream);
 
 /*
  * Accelerations of Eq. 1 for n particles under each other's gravity (i set

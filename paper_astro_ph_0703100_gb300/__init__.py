@@ -25,6 +25,7 @@ __all__ = [
     "cn_force",
     "cn_force_ws",
     "cn_force_noalloc",
+    "cn_force_eps_i",
     "cn_force_dd",
     "cn_force_dd_ws",
     "cn_workspace_bytes",
@@ -74,6 +75,8 @@ VARIANT = {
     "jerk": 7,
     "jerk_pot": 8,
     "symmetric": 9,
+    "f32_eps_i": 10,
+    "f32_eps_i_pot": 11,
 }
 
 
@@ -142,6 +145,22 @@ def _force(fn, double, pos_i, pos_mass_j, eps2, acc_out, pot_out, potential, str
 def cn_force(pos_i, pos_mass_j, eps2, acc_out=None, pot_out=None, potential=False, stream=None):
     """FP32 accelerations (n_i, 3) and, if requested, potentials (n_i,)."""
     return _force("cn_force", False, pos_i, pos_mass_j, eps2, acc_out, pot_out, potential, stream)
+
+
+def cn_force_eps_i(pos_eps_i, pos_mass_j, acc_out=None, pot_out=None, potential=False, stream=None):
+    """FP32 accelerations (and potentials) with each i-particle's softening
+    eps2_i taken from the 4th slot of its record (x, y, z, eps2_i)."""
+    torch = _torch()
+    _records(pos_eps_i, "pos_eps_i")
+    _records(pos_mass_j, "pos_mass_j")
+    n_i, n_j = pos_eps_i.shape[0], pos_mass_j.shape[0]
+    acc = _out(acc_out, (n_i, 3), torch.float32, pos_eps_i.device, "acc_out")
+    pot = None
+    if potential or pot_out is not None:
+        pot = _out(pot_out, (n_i,), torch.float32, pos_eps_i.device, "pot_out")
+    check(load().cn_force_eps_i(n_i, _ptr(pos_eps_i), n_j, _ptr(pos_mass_j), _ptr(acc), _ptr(pot),
+                                _stream_handle(stream)), "cn_force_eps_i")
+    return acc, pot
 
 
 def cn_force_noalloc(pos_i, pos_mass_j, eps2, acc_out=None, pot_out=None, potential=False, stream=None):

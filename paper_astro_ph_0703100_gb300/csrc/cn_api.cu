@@ -292,7 +292,8 @@ cn_tune default_tune(int variant, int64_t n_i, int64_t n_j) {
   const bool dd = variant == cn::kDD || variant == cn::kDDPot;
   // the adjoint and the force-jerk form stream two 16-byte records per j
   const bool adj = variant == cn::kAdjoint || variant == cn::kJerk || variant == cn::kJerkPot;
-  const bool f32 = variant == cn::kF32 || variant == cn::kF32Pot;
+  const bool f32 = variant == cn::kF32 || variant == cn::kF32Pot || variant == cn::kF32EpsI ||
+                   variant == cn::kF32EpsIPot;
   t.stages = 4;
   t.threads = 128;
   t.j_lanes = 1;
@@ -360,7 +361,7 @@ cn_status check_tune(int variant, const cn_tune& t) {
   if (t.j_lanes < 0 || t.j_lanes > 32 || (t.j_lanes & (t.j_lanes - 1)))
     return fail(CN_ERR_INVALID_ARG, "j_lanes must be 0 or a power of two up to 32");
   if (t.j_lanes > 1) {
-    if (variant != cn::kF32 && variant != cn::kF32Pot)
+    if (variant != cn::kF32 && variant != cn::kF32Pot && variant != cn::kF32EpsI && variant != cn::kF32EpsIPot)
       return fail(CN_ERR_INVALID_ARG, "j_lanes > 1 is offered for the plain FP32 single-system form only");
     if (t.i_per_thread > 2) return fail(CN_ERR_INVALID_ARG, "j_lanes > 1 needs i_per_thread = 1 or 2");
     if (t.j_tile && t.j_tile % (8 * t.j_lanes))
@@ -475,6 +476,8 @@ cn_status occupancy(int dev, int variant, bool guard, const Plan& p, size_t smem
     case cn::kBatchedPot: e = cn::occupancy_f32(p, true, guard, true, smem, &c); break;
     case cn::kJerk: e = cn::occupancy_jerk(p, false, guard, smem, &c); break;
     case cn::kJerkPot: e = cn::occupancy_jerk(p, true, guard, smem, &c); break;
+    case cn::kF32EpsI: e = cn::occupancy_f32(p, false, true, false, smem, &c, true); break;
+    case cn::kF32EpsIPot: e = cn::occupancy_f32(p, true, true, false, smem, &c, true); break;
     default: return fail(CN_ERR_INVALID_ARG, "unknown variant");
   }
   if (e != cudaSuccess) return fail_cuda(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
@@ -574,12 +577,15 @@ cn_status check_records(const float* p, int64_t n, const char* name) {
 }
 
 // ------------------------------------------------------------------ single-system force
+// eps_i: the softening of each pair is its i-particle's, from the 4th slot
+// of its record (eps2 is not used); the kernels then always take the s = 0
+// guard.
 cn_status force_common(bool dd, int64_t n_i, const float* pos_i, int64_t n_j, const float* pos_mass_j,
                        float eps2, void* acc_out, void* pot_out, void* ws, size_t ws_bytes, bool lib_ws,
-                       cudaStream_t s) {
+                       cudaStream_t s, bool eps_i = false) {
   if (n_i < 0 || n_j < 0) return fail(CN_ERR_INVALID_ARG, "n_i and n_j must be >= 0");
   cn_status st;
-  if ((st = check_eps2(eps2)) != CN_OK) return st;
+  if (!eps_i && (st = check_eps2(eps2)) != CN_OK) return st;
   if ((st = check_records(pos_i, n_i, "pos_i")) != CN_OK) return st;
   if ((st = check_records(pos_mass_j, n_j, "pos_mass_j")) != CN_OK) return st;
   const size_t elt = dd ? sizeof(double) : sizeof(float);
@@ -603,10 +609,12 @@ cn_status force_common(bool dd, int64_t n_i, const float* pos_i, int64_t n_j, co
     return CN_OK;
   }
   const bool pot = pot_out != nullptr;
-  const bool guard = needs_guard(eps2);
-  const int variant = dd ? (pot ? cn::kDDPot : cn::kDD) : (pot ? cn::kF32Pot : cn::kF32);
+  const bool guard = eps_i || needs_guard(eps2);
+  const int variant = eps_i ? (pot ? cn::kF32EpsIPot : cn::kF32EpsI)
+                            : (dd ? (pot ? cn::kDDPot : cn::kDD) : (pot ? cn::kF32Pot : cn::kF32));
   Plan p;
-  if ((st = resolve_plan(dev, variant, n_i, n_j, guard, nullptr, &p)) != CN_OK) return st;
+  // the per-particle kernels are guarded in every shape, so K is not restricted to 1
+  if ((st = resolve_plan(dev, variant, n_i, n_j, guard && !eps_i, nullptr, &p)) != CN_OK) return st;
   Geometry g;
   if ((st = single_geometry(dev, *d, variant, guard, p, n_i, n_j, &g)) != CN_OK) return st;
   char *ctrl = nullptr, *data = nullptr;
@@ -620,7 +628,7 @@ cn_status force_common(bool dd, int64_t n_i, const float* pos_i, int64_t n_j, co
   a.n_j = n_j;
   a.eps2 = eps2;
   if (inject("launch")) return fail(CN_ERR_CUDA, "kernel launch: injected launch failure");
-  e = dd ? cn::launch_dd(a, p, pot, guard, g.grid, s) : cn::launch_f32(a, p, pot, guard, false, g.grid, s);
+  e = dd ? cn::launch_dd(a, p, pot, guard, g.grid, s) : cn::launch_f32(a, p, pot, guard, false, g.grid, s, eps_i);
   if (e != cudaSuccess) return fail_cuda(e, "pair kernel launch");
   return CN_OK;
 }
@@ -1049,6 +1057,12 @@ cn_status cn_force(int64_t n_i, const float* pos_i, int64_t n_j, const float* po
                       reinterpret_cast<cudaStream_t>(stream));
 }
 
+cn_status cn_force_eps_i(int64_t n_i, const float* pos_eps_i, int64_t n_j, const float* pos_mass_j, float* acc_out,
+                         float* pot_out, cn_stream stream) {
+  return force_common(false, n_i, pos_eps_i, n_j, pos_mass_j, 0.f, acc_out, pot_out, nullptr, 0, true,
+                      reinterpret_cast<cudaStream_t>(stream), true);
+}
+
 cn_status cn_force_ws(int64_t n_i, const float* pos_i, int64_t n_j, const float* pos_mass_j, float eps2,
                       float* acc_out, float* pot_out, void* workspace, size_t ws_bytes, cn_stream stream) {
   return force_common(false, n_i, pos_i, n_j, pos_mass_j, eps2, acc_out, pot_out, workspace, ws_bytes, false,
@@ -1068,8 +1082,8 @@ cn_status cn_force_dd_ws(int64_t n_i, const float* pos_i, int64_t n_j, const flo
 }
 
 size_t cn_workspace_bytes(int variant, int64_t n_i, int64_t n_j) {
-  if (n_i <= 0 || n_j <= 0 || variant < cn::kF32 || variant > cn::kJerkPot || variant == cn::kBatched ||
-      variant == cn::kBatchedPot)
+  if (n_i <= 0 || n_j <= 0 || variant < cn::kF32 || variant > cn::kF32EpsIPot || variant == cn::kBatched ||
+      variant == cn::kBatchedPot || variant == cn::kSym)
     return 0;
   int dev = 0;
   DeviceInfo* d = nullptr;
@@ -1304,7 +1318,7 @@ cn_status cn_force_host_f64(const double* xj, const double* mj, const double* xi
 }
 
 cn_status cn_tune_get(int variant, int64_t n_i, int64_t n_j, cn_tune* out) {
-  if (!out || variant < cn::kF32 || variant > cn::kSym || n_i < 0 || n_j < 0)
+  if (!out || variant < cn::kF32 || variant > cn::kF32EpsIPot || n_i < 0 || n_j < 0)
     return fail(CN_ERR_INVALID_ARG, "bad variant, size or NULL output");
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -1323,7 +1337,7 @@ cn_status cn_tune_get(int variant, int64_t n_i, int64_t n_j, cn_tune* out) {
 }
 
 cn_status cn_tune_set(int variant, int64_t n_i, int64_t n_j, const cn_tune* tune) {
-  if (variant < cn::kF32 || variant > cn::kSym || n_i < 0 || n_j < 0)
+  if (variant < cn::kF32 || variant > cn::kF32EpsIPot || n_i < 0 || n_j < 0)
     return fail(CN_ERR_INVALID_ARG, "bad variant or size");
   if (tune) {
     cn_status st = check_tune(variant, *tune);

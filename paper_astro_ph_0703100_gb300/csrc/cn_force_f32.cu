@@ -4,14 +4,32 @@
 namespace cn {
 namespace {
 
-// K >= 2 without the split-j lanes runs the packed (f32x2) policy: the
-// same results, fewer issued instructions per pair.
-template <int K, bool POT, bool GUARD, bool BATCHED, bool SPLITJ = false>
+// K >= 2 runs the packed (f32x2) policy: the same results, fewer issued
+// instructions per pair.
+template <int K, bool POT, bool GUARD, bool BATCHED, bool SPLITJ = false, bool EPSI = false>
 const void* fn() {
   if constexpr (K >= 2)
-    return reinterpret_cast<const void*>(&pair_kernel<F32x2Policy<K, POT, GUARD, SPLITJ>, K, BATCHED>);
+    return reinterpret_cast<const void*>(&pair_kernel<F32x2Policy<K, POT, GUARD, SPLITJ, EPSI>, K, BATCHED>);
   else
-    return reinterpret_cast<const void*>(&pair_kernel<F32Policy<K, POT, GUARD, SPLITJ>, K, BATCHED>);
+    return reinterpret_cast<const void*>(&pair_kernel<F32Policy<K, POT, GUARD, SPLITJ, EPSI>, K, BATCHED>);
+}
+
+// Softening per i-particle (the i record's 4th slot): always guarded, since
+// any particle's eps2 may be 0; single systems, split-j up to two particles.
+template <bool POT>
+const void* epsi(int k, int j_lanes) {
+  if (j_lanes > 1) {
+    if (k == 1) return fn<1, POT, true, false, true, true>();
+    if (k == 2) return fn<2, POT, true, false, true, true>();
+    return nullptr;
+  }
+  switch (k) {
+    case 1: return fn<1, POT, true, false, false, true>();
+    case 2: return fn<2, POT, true, false, false, true>();
+    case 4: return fn<4, POT, true, false, false, true>();
+    case 8: return fn<8, POT, true, false, false, true>();
+    default: return nullptr;
+  }
 }
 
 template <bool POT, bool GUARD, bool BATCHED>
@@ -29,7 +47,8 @@ const void* by_k(int k) {
   }
 }
 
-const void* select(int k, bool pot, bool guard, bool batched, int j_lanes) {
+const void* select(int k, bool pot, bool guard, bool batched, int j_lanes, bool eps_i) {
+  if (eps_i) return batched ? nullptr : (pot ? epsi<true>(k, j_lanes) : epsi<false>(k, j_lanes));
   if (j_lanes > 1) {  // split-j kernels: one or two i-particles per j-lane group, single systems
     if (batched || k > 2 || (k == 2 && guard)) return nullptr;
     if (k == 2) return pot ? fn<2, true, false, false, true>() : fn<2, false, false, false, true>();
@@ -46,8 +65,8 @@ const void* select(int k, bool pot, bool guard, bool batched, int j_lanes) {
 
 }  // namespace
 
-cudaError_t occupancy_f32(const Plan& p, bool pot, bool guard, bool batched, size_t smem, int* ctas) {
-  const void* f = select(p.k, pot, guard, batched, p.j_lanes);
+cudaError_t occupancy_f32(const Plan& p, bool pot, bool guard, bool batched, size_t smem, int* ctas, bool eps_i) {
+  const void* f = select(p.k, pot, guard, batched, p.j_lanes, eps_i);
   if (!f) return cudaErrorInvalidValue;
   cudaError_t e = prepare_kernel(f, smem);
   if (e != cudaSuccess) return e;
@@ -55,8 +74,8 @@ cudaError_t occupancy_f32(const Plan& p, bool pot, bool guard, bool batched, siz
 }
 
 cudaError_t launch_f32(const PairArgs& a, const Plan& p, bool pot, bool guard, bool batched, int grid,
-                       cudaStream_t s) {
-  const void* f = select(p.k, pot, guard, batched, p.j_lanes);
+                       cudaStream_t s, bool eps_i) {
+  const void* f = select(p.k, pot, guard, batched, p.j_lanes, eps_i);
   if (!f) return cudaErrorInvalidValue;
   const size_t smem = ring_smem_bytes(p);
   cudaError_t e = prepare_kernel(f, smem);

@@ -82,13 +82,16 @@ enum Variant : int {
   kJerk = 7,
   kJerkPot = 8,
   kSym = 9,  // symmetric form (cn_sym.h)
+  kF32EpsI = 10,     // softening per i-particle (the i record's 4th slot)
+  kF32EpsIPot = 11,
 };
 
 // Kernel selection, occupancy and launch (defined in the per-variant
 // translation units).
 cudaError_t launch_f32(const PairArgs& a, const Plan& p, bool pot, bool guard, bool batched, int grid,
-                       cudaStream_t s);
-cudaError_t occupancy_f32(const Plan& p, bool pot, bool guard, bool batched, size_t smem, int* ctas);
+                       cudaStream_t s, bool eps_i = false);
+cudaError_t occupancy_f32(const Plan& p, bool pot, bool guard, bool batched, size_t smem, int* ctas,
+                          bool eps_i = false);
 cudaError_t launch_dd(const PairArgs& a, const Plan& p, bool pot, bool guard, int grid, cudaStream_t s);
 cudaError_t occupancy_dd(const Plan& p, bool pot, bool guard, size_t smem, int* ctas);
 cudaError_t launch_adjoint(const PairArgs& a, const Plan& p, bool guard, int grid, cudaStream_t s);

@@ -81,21 +81,23 @@ __device__ __forceinline__ int32_t tile_of_unit(const PairArgs& a, int64_t u) {
 // softened squared distance, one MUFU rsqrt, 3 FMUL for m r^-3 and 3 FFMA
 // into the partial. POT adds the pair potential m / r for every pair whose
 // separation is not exactly zero; GUARD zeroes pairs with s == 0 (reachable
-// only for eps2 == 0 and coincident points).
-template <int K, bool POT, bool GUARD>
+// only for eps2 == 0 and coincident points). EPSI: i-particle k's own
+// softening e2i[k] (the i record's 4th slot) replaces eps2.
+template <int K, bool POT, bool GUARD, bool EPSI = false>
 __device__ __forceinline__ void pair_f32(const float4 pj, const float (&xi)[K][3], float eps2,
-                                         float (&part)[K][POT ? 4 : 3]) {
+                                         const float (&e2i)[EPSI ? K : 1], float (&part)[K][POT ? 4 : 3]) {
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     const float dx = pj.x - xi[k][0];
     const float dy = pj.y - xi[k][1];
     const float dz = pj.z - xi[k][2];
+    const float e2 = EPSI ? e2i[EPSI ? k : 0] : eps2;
     float s, d2 = 0.f;
     if constexpr (POT) {
       d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-      s = d2 + eps2;
+      s = d2 + e2;
     } else {
-      s = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+      s = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, e2)));
     }
     float r = rsqrt_mufu(s);
     if constexpr (GUARD) r = (s > 0.f) ? r : 0.f;
@@ -135,8 +137,8 @@ __device__ __forceinline__ void pair_f32(const float4 pj, const float (&xi)[K][3
 // `sub` of a group taking j records sub, sub + j_lanes, ... of each tile;
 // the group's sums are combined by a fixed xor butterfly of warp shuffles
 // at the end of each segment (small systems: many threads, no cross-CTA
-// merge).
-template <int K, bool POT, bool GUARD, bool SPLITJ = false>
+// merge). EPSI: each i-particle's softening is its record's 4th slot.
+template <int K, bool POT, bool GUARD, bool SPLITJ = false, bool EPSI = false>
 struct F32Policy {
   static constexpr int NC = POT ? 4 : 3;
   static constexpr int kSlotF4 = 1;  // float4 per i-particle in a workspace slot
@@ -145,6 +147,7 @@ struct F32Policy {
   static constexpr bool kSplitJ = SPLITJ;
   static constexpr int kMinBlocks = K >= 8 ? 1 : 2;  // 256-thread CTAs per SM the register budget must allow
   float xi[K][3];
+  float e2i[EPSI ? K : 1];
   float run[K][NC];
 
   __device__ __forceinline__ void load_i(const PairArgs& a, int64_t gi, bool valid, int k) {
@@ -153,6 +156,7 @@ struct F32Policy {
     xi[k][0] = v.x;
     xi[k][1] = v.y;
     xi[k][2] = v.z;
+    if constexpr (EPSI) e2i[k] = v.w;
   }
 
   __device__ __forceinline__ void zero() {
@@ -174,7 +178,7 @@ struct F32Policy {
 #pragma unroll 1
       for (int j = sub; j < T; j += 8 * jl) {
 #pragma unroll
-        for (int jj = 0; jj < 8; ++jj) pair_f32<K, POT, GUARD>(js[j + jj * jl], xi, eps2, part);
+        for (int jj = 0; jj < 8; ++jj) pair_f32<K, POT, GUARD, EPSI>(js[j + jj * jl], xi, eps2, e2i, part);
       }
     } else {
       // 16 j records per loop trip (j_tile is a multiple of 16): enough
@@ -182,7 +186,7 @@ struct F32Policy {
 #pragma unroll 1
       for (int j = 0; j < T; j += 16) {
 #pragma unroll
-        for (int jj = 0; jj < 16; ++jj) pair_f32<K, POT, GUARD>(js[j + jj], xi, eps2, part);
+        for (int jj = 0; jj < 16; ++jj) pair_f32<K, POT, GUARD, EPSI>(js[j + jj], xi, eps2, e2i, part);
       }
     }
 #pragma unroll
@@ -246,12 +250,13 @@ struct F32Policy {
 // held negated so that x_j - x_i is one packed add.
 __device__ __forceinline__ float2 dup2(float v) { return make_float2(v, v); }
 
-template <int K, bool POT, bool GUARD>
-__device__ __forceinline__ void pair_f32x2(const float4 pj, const float2 (&nxi)[K / 2][3], float2 e2,
-                                           float2 (&part)[K / 2][POT ? 4 : 3]) {
+template <int K, bool POT, bool GUARD, bool EPSI = false>
+__device__ __forceinline__ void pair_f32x2(const float4 pj, const float2 (&nxi)[K / 2][3], float2 e2u,
+                                           const float2 (&e2i)[EPSI ? K / 2 : 1], float2 (&part)[K / 2][POT ? 4 : 3]) {
   const float2 jx = dup2(pj.x), jy = dup2(pj.y), jz = dup2(pj.z), jm = dup2(pj.w);
 #pragma unroll
   for (int p = 0; p < K / 2; ++p) {
+    const float2 e2 = EPSI ? e2i[EPSI ? p : 0] : e2u;
     const float2 dx = __fadd2_rn(jx, nxi[p][0]);
     const float2 dy = __fadd2_rn(jy, nxi[p][1]);
     const float2 dz = __fadd2_rn(jz, nxi[p][2]);
@@ -281,7 +286,7 @@ __device__ __forceinline__ void pair_f32x2(const float4 pj, const float2 (&nxi)[
 // two i-particles per register pair. SPLITJ: as in F32Policy, groups of
 // j_lanes lanes share the thread's i-particles, each lane taking every
 // j_lanes-th j record, combined by an xor butterfly at segment ends.
-template <int K, bool POT, bool GUARD, bool SPLITJ = false>
+template <int K, bool POT, bool GUARD, bool SPLITJ = false, bool EPSI = false>
 struct F32x2Policy {
   static_assert(K % 2 == 0, "the packed form holds i-particles in pairs");
   static constexpr int NC = POT ? 4 : 3;
@@ -292,6 +297,7 @@ struct F32x2Policy {
   // K = 4 (and the split-j form with the potential) spill under a 128-register cap
   static constexpr int kMinBlocks = (K >= 4 || SPLITJ) ? 1 : 2;
   float2 nxi[K / 2][3];
+  float2 e2i[EPSI ? K / 2 : 1];  // per-particle softening (EPSI)
   float2 run[K / 2][NC];
 
   __device__ __forceinline__ static float& half(float2& v, int k) { return (k & 1) ? v.y : v.x; }
@@ -303,6 +309,7 @@ struct F32x2Policy {
     half(nxi[k >> 1][0], k) = -v.x;
     half(nxi[k >> 1][1], k) = -v.y;
     half(nxi[k >> 1][2], k) = -v.z;
+    if constexpr (EPSI) half(e2i[k >> 1], k) = v.w;
   }
 
   __device__ __forceinline__ void zero() {
@@ -325,13 +332,13 @@ struct F32x2Policy {
 #pragma unroll 1
       for (int j = sub; j < T; j += 8 * jl) {
 #pragma unroll
-        for (int jj = 0; jj < 8; ++jj) pair_f32x2<K, POT, GUARD>(js[j + jj * jl], nxi, e2, part);
+        for (int jj = 0; jj < 8; ++jj) pair_f32x2<K, POT, GUARD, EPSI>(js[j + jj * jl], nxi, e2, e2i, part);
       }
     } else {
 #pragma unroll 1
       for (int j = 0; j < T; j += 16) {
 #pragma unroll
-        for (int jj = 0; jj < 16; ++jj) pair_f32x2<K, POT, GUARD>(js[j + jj], nxi, e2, part);
+        for (int jj = 0; jj < 16; ++jj) pair_f32x2<K, POT, GUARD, EPSI>(js[j + jj], nxi, e2, e2i, part);
       }
     }
 #pragma unroll
