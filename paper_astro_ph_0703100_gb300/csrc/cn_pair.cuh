@@ -991,16 +991,29 @@ __device__ __forceinline__ void pair_jerk_x2(const float4 pj, const float4 vj, c
   }
 }
 
-template <int K, bool POT, bool GUARD>
+// SPLITJ (small systems): groups of j_lanes lanes share the thread's
+// i-particles, each lane taking every j_lanes-th j entry, combined by an
+// xor butterfly at segment ends, as in the plain packed form.
+template <int K, bool POT, bool GUARD, bool SPLITJ = false>
 struct JerkX2Policy {
   static_assert(K % 2 == 0, "the packed form holds i-particles in pairs");
   static constexpr int kSlotF4 = 2;
   static constexpr int kSums = 7;
   static constexpr int kJRec = 2;
-  static constexpr bool kSplitJ = false;
+  static constexpr bool kSplitJ = SPLITJ;
   static constexpr int kMinBlocks = 1;
   static constexpr int NC = POT ? 7 : 6;
-  __device__ __forceinline__ void reduce_lanes(int) {}
+  __device__ __forceinline__ void reduce_lanes(int jl) {
+    for (int off = jl >> 1; off > 0; off >>= 1) {
+#pragma unroll
+      for (int p = 0; p < K / 2; ++p)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          run[p][c].x += __shfl_xor_sync(0xffffffffu, run[p][c].x, off);
+          run[p][c].y += __shfl_xor_sync(0xffffffffu, run[p][c].y, off);
+        }
+    }
+  }
   float2 nxi[K / 2][3];
   float2 nvi[K / 2][3];
   float2 run[K / 2][7];
@@ -1031,7 +1044,7 @@ struct JerkX2Policy {
   }
 
   __device__ __forceinline__ void tile(const float4* js, int T, float eps2, int64_t /*self_off*/, bool /*diag*/,
-                                       int /*row*/, int /*rows*/, int /*sub*/, int /*jl*/) {
+                                       int /*row*/, int /*rows*/, int sub, int jl) {
     const float4* jv = js + T;
     float2 part[K / 2][7];
 #pragma unroll
@@ -1039,10 +1052,20 @@ struct JerkX2Policy {
 #pragma unroll
       for (int c = 0; c < 7; ++c) part[p][c] = dup2(0.f);
     const float2 e2 = dup2(eps2);
+    if constexpr (SPLITJ) {
+      // this lane's j entries: sub, sub + jl, ... (j_tile is a multiple of 8 jl)
 #pragma unroll 1
-    for (int j = 0; j < T; j += 4) {
+      for (int j = sub; j < T; j += 4 * jl) {
 #pragma unroll
-      for (int jj = 0; jj < 4; ++jj) pair_jerk_x2<K, POT, GUARD>(js[j + jj], jv[j + jj], nxi, nvi, e2, part);
+        for (int jj = 0; jj < 4; ++jj)
+          pair_jerk_x2<K, POT, GUARD>(js[j + jj * jl], jv[j + jj * jl], nxi, nvi, e2, part);
+      }
+    } else {
+#pragma unroll 1
+      for (int j = 0; j < T; j += 4) {
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) pair_jerk_x2<K, POT, GUARD>(js[j + jj], jv[j + jj], nxi, nvi, e2, part);
+      }
     }
 #pragma unroll
     for (int p = 0; p < K / 2; ++p)

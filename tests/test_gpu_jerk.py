@@ -31,7 +31,10 @@ def run(cn, pi, vi, pj, vj, eps2, potential=True):
 @pytest.mark.parametrize("tune", [None, {"i_per_thread": 1, "threads": 64, "j_tile": 16, "stages": 2},
                                   {"i_per_thread": 2, "threads": 128, "j_tile": 64, "stages": 3},
                                   {"i_per_thread": 4, "threads": 256, "j_tile": 128, "stages": 4, "chunk_units": 3},
-                                  {"i_per_thread": 2, "threads": 128, "j_tile": 256, "stages": 1}])
+                                  {"i_per_thread": 2, "threads": 128, "j_tile": 256, "stages": 1},
+                                  # split-j: lane groups share two i-particles
+                                  {"i_per_thread": 2, "threads": 128, "j_tile": 256, "stages": 2, "j_lanes": 32},
+                                  {"i_per_thread": 2, "threads": 256, "j_tile": 128, "stages": 3, "j_lanes": 8}])
 @pytest.mark.parametrize("shape", [(1, 1), (33, 31), (1000, 777), (4097, 2049)])
 def test_jerk_ragged_and_launch_shapes(shape, tune):
     cn = lib()
