@@ -6,15 +6,17 @@ namespace {
 
 // K >= 2 runs the packed (f32x2) policy: the same results, fewer issued
 // instructions per pair.
-template <int K, bool GUARD>
+template <int K, bool GUARD, bool SPLITJ = false>
 const void* fn() {
   if constexpr (K >= 2)
-    return reinterpret_cast<const void*>(&pair_kernel<AdjointX2Policy<K, GUARD>, K, false>);
+    return reinterpret_cast<const void*>(&pair_kernel<AdjointX2Policy<K, GUARD, SPLITJ>, K, false>);
   else
     return reinterpret_cast<const void*>(&pair_kernel<AdjointPolicy<K, GUARD>, K, false>);
 }
 
-const void* select(int k, bool guard) {
+// j_lanes > 1 (small systems): the packed form with two i-particles per lane group
+const void* select(int k, bool guard, int j_lanes) {
+  if (j_lanes > 1) return (k == 2 && !guard) ? fn<2, false, true>() : nullptr;
   if (guard) return k == 1 ? fn<1, true>() : nullptr;
   switch (k) {
     case 1: return fn<1, false>();
@@ -36,7 +38,7 @@ __global__ void pack_w_kernel(const float* __restrict__ w, float4* __restrict__ 
 }  // namespace
 
 cudaError_t occupancy_adjoint(const Plan& p, bool guard, size_t smem, int* ctas) {
-  const void* f = select(p.k, guard);
+  const void* f = select(p.k, guard, p.j_lanes);
   if (!f) return cudaErrorInvalidValue;
   cudaError_t e = prepare_kernel(f, smem);
   if (e != cudaSuccess) return e;
@@ -44,7 +46,7 @@ cudaError_t occupancy_adjoint(const Plan& p, bool guard, size_t smem, int* ctas)
 }
 
 cudaError_t launch_adjoint(const PairArgs& a, const Plan& p, bool guard, int grid, cudaStream_t s) {
-  const void* f = select(p.k, guard);
+  const void* f = select(p.k, guard, p.j_lanes);
   if (!f) return cudaErrorInvalidValue;
   const size_t smem = adjoint_smem_bytes(p);
   cudaError_t e = prepare_kernel(f, smem);

@@ -311,10 +311,11 @@ cn_tune default_tune(int variant, int64_t n_i, int64_t n_j) {
     t.stages = n_j <= t.j_tile ? 1 : 3;
     return t;
   }
-  if ((variant == cn::kJerk || variant == cn::kJerkPot) && n_i <= 8192) {
-    // small systems, measured at N = 1024 .. 8192 (force + jerk + potential):
-    // packed split-j, two i-particles per lane group of 32 (16 at N = 8192,
-    // 8 at N = 4096), up to 2048 two-record j entries per stage
+  if ((variant == cn::kJerk || variant == cn::kJerkPot || variant == cn::kAdjoint) && n_i <= 8192) {
+    // small systems, measured at N = 1024 .. 8192 (force + jerk + potential,
+    // and the adjoint, with the same optima): packed split-j, two
+    // i-particles per lane group of 32 (16 at N = 8192, 8 at N = 4096), up
+    // to 2048 two-record j entries per stage
     const int jl = n_i <= 2048 ? 32 : (n_i <= 4096 ? 8 : 16);
     t.i_per_thread = 2;
     t.j_lanes = jl;
@@ -373,12 +374,12 @@ cn_status check_tune(int variant, const cn_tune& t) {
   if (t.j_lanes < 0 || t.j_lanes > 32 || (t.j_lanes & (t.j_lanes - 1)))
     return fail(CN_ERR_INVALID_ARG, "j_lanes must be 0 or a power of two up to 32");
   if (t.j_lanes > 1) {
-    const bool jerk = variant == cn::kJerk || variant == cn::kJerkPot;
+    const bool jerk = variant == cn::kJerk || variant == cn::kJerkPot || variant == cn::kAdjoint;
     if (variant != cn::kF32 && variant != cn::kF32Pot && variant != cn::kF32EpsI && variant != cn::kF32EpsIPot && !jerk)
-      return fail(CN_ERR_INVALID_ARG, "j_lanes > 1 is offered for the plain FP32 and force-jerk single-system forms");
+      return fail(CN_ERR_INVALID_ARG, "j_lanes > 1 is offered for the plain FP32, force-jerk and adjoint forms");
     if (t.i_per_thread > 2) return fail(CN_ERR_INVALID_ARG, "j_lanes > 1 needs i_per_thread = 1 or 2");
     if (jerk && t.i_per_thread != 2)
-      return fail(CN_ERR_INVALID_ARG, "the force-jerk form takes j_lanes > 1 with i_per_thread = 2");
+      return fail(CN_ERR_INVALID_ARG, "the force-jerk and adjoint forms take j_lanes > 1 with i_per_thread = 2");
     if (t.j_tile && t.j_tile % (8 * t.j_lanes))
       return fail(CN_ERR_INVALID_ARG, "with j_lanes > 1, j_tile must be a multiple of 8 x j_lanes");
   }
@@ -438,8 +439,8 @@ cn_status resolve_plan(int dev, int variant, int64_t n_i, int64_t n_j, bool guar
   p->chunk_units = t.chunk_units;
   p->j_lanes = t.j_lanes > 1 ? t.j_lanes : 1;
   if (p->j_lanes > 1 && variant == cn::kSym) return fail(CN_ERR_INVALID_ARG, "the symmetric form takes no j_lanes");
-  if (p->j_lanes > 1 && (variant == cn::kJerk || variant == cn::kJerkPot) && guard) {
-    p->j_lanes = 1;  // the guarded force-jerk kernel holds one i-particle per thread, without split-j lanes
+  if (p->j_lanes > 1 && (variant == cn::kJerk || variant == cn::kJerkPot || variant == cn::kAdjoint) && guard) {
+    p->j_lanes = 1;  // the guarded force-jerk and adjoint kernels hold one i-particle per thread, without split-j
     p->k = 1;
   }
   if (p->j_lanes > 1) {

@@ -852,15 +852,28 @@ __device__ __forceinline__ void pair_adjoint_x2(const float4 pj, const float4 wp
   }
 }
 
-template <int K, bool GUARD>
+// SPLITJ (small systems): lane groups share the thread's i-particles, each
+// lane taking every j_lanes-th j entry (the self test compares the entry's
+// index in the tile, so it is unchanged), combined by an xor butterfly.
+template <int K, bool GUARD, bool SPLITJ = false>
 struct AdjointX2Policy {
   static_assert(K % 2 == 0, "the packed form holds i-particles in pairs");
   static constexpr int kSlotF4 = 1;
   static constexpr int kSums = 4;
   static constexpr int kJRec = 2;
-  static constexpr bool kSplitJ = false;
-  static constexpr int kMinBlocks = K >= 4 ? 1 : 2;
-  __device__ __forceinline__ void reduce_lanes(int) {}
+  static constexpr bool kSplitJ = SPLITJ;
+  static constexpr int kMinBlocks = (K >= 4 || SPLITJ) ? 1 : 2;
+  __device__ __forceinline__ void reduce_lanes(int jl) {
+    for (int off = jl >> 1; off > 0; off >>= 1) {
+#pragma unroll
+      for (int p = 0; p < K / 2; ++p)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          run[p][c].x += __shfl_xor_sync(0xffffffffu, run[p][c].x, off);
+          run[p][c].y += __shfl_xor_sync(0xffffffffu, run[p][c].y, off);
+        }
+    }
+  }
   float2 nxk[K / 2][3];
   float2 mk[K / 2];
   float2 nwk[K / 2][3];
@@ -893,8 +906,10 @@ struct AdjointX2Policy {
   }
 
   __device__ __forceinline__ void tile(const float4* js, int T, float eps2, int64_t self_off, bool diag, int row,
-                                       int rows, int /*sub*/, int /*jl*/) {
+                                       int rows, int sub, int jl) {
     const float4* jw = js + T;
+    const int j0 = SPLITJ ? sub : 0;   // this lane's first entry
+    const int js1 = SPLITJ ? jl : 1;   // stride between its entries
     float2 part[K / 2][4];
 #pragma unroll
     for (int p = 0; p < K / 2; ++p)
@@ -909,17 +924,21 @@ struct AdjointX2Policy {
     const float2 e2 = dup2(eps2);
     if (!diag) {
 #pragma unroll 1
-      for (int j = 0; j < T; j += 8) {
+      for (int j = j0; j < T; j += 8 * js1) {
 #pragma unroll
-        for (int jj = 0; jj < 8; ++jj)
-          pair_adjoint_x2<K, GUARD, false>(js[j + jj], jw[j + jj], nxk, mk, nwk, e2, j + jj, self_j, part);
+        for (int jj = 0; jj < 8; ++jj) {
+          const int e = j + jj * js1;
+          pair_adjoint_x2<K, GUARD, false>(js[e], jw[e], nxk, mk, nwk, e2, e, self_j, part);
+        }
       }
     } else {
 #pragma unroll 1
-      for (int j = 0; j < T; j += 8) {
+      for (int j = j0; j < T; j += 8 * js1) {
 #pragma unroll
-        for (int jj = 0; jj < 8; ++jj)
-          pair_adjoint_x2<K, GUARD, true>(js[j + jj], jw[j + jj], nxk, mk, nwk, e2, j + jj, self_j, part);
+        for (int jj = 0; jj < 8; ++jj) {
+          const int e = j + jj * js1;
+          pair_adjoint_x2<K, GUARD, true>(js[e], jw[e], nxk, mk, nwk, e2, e, self_j, part);
+        }
       }
     }
 #pragma unroll

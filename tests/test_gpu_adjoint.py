@@ -48,7 +48,11 @@ def test_adjoint_small_all_particles(n):
 
 
 @pytest.mark.parametrize("tune", [{"i_per_thread": 1, "threads": 64, "j_tile": 32, "stages": 2},
-                                  {"i_per_thread": 4, "threads": 128, "j_tile": 256, "stages": 4}])
+                                  {"i_per_thread": 4, "threads": 128, "j_tile": 256, "stages": 4},
+                                  # split-j: lane groups share two i-particles (self pairs
+                                  # are excluded by the entry's index within the tile)
+                                  {"i_per_thread": 2, "threads": 128, "j_tile": 512, "stages": 3, "j_lanes": 32},
+                                  {"i_per_thread": 2, "threads": 256, "j_tile": 2560, "stages": 1, "j_lanes": 16}])
 def test_adjoint_launch_shapes(tune):
     cn = lib()
     n = 2500
