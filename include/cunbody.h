@@ -96,10 +96,12 @@ typedef struct cn_tune {
     int32_t chunk_units;  /* 0 = static schedule (equal share per CTA); > 0 = dynamic queue chunks
                              of this many (i-tile x j-tile) units. Symmetric form: tile rows per
                              band (0 = one band while its slots fit in 2 GiB, else bands)       */
-    int32_t j_lanes;      /* plain FP32 single-system form only: lanes sharing the thread's
-                             i-particles (1, 2, 4, ..., 32; needs i_per_thread = 1 or 2 and
-                             j_tile a multiple of 8 x j_lanes); their partial sums are combined
-                             by warp shuffles                                                    */
+    int32_t j_lanes;      /* single-system FP32, per-i-softening, force-jerk and adjoint forms:
+                             lanes sharing the thread's i-particles (1, 2, 4, ..., 32; needs
+                             i_per_thread = 1 or 2 - exactly 2 for the force-jerk and adjoint
+                             forms - and j_tile a multiple of 8 x j_lanes); their partial sums
+                             are combined by warp shuffles. Ignored (1) for calls with eps2 = 0
+                             of the force-jerk and adjoint forms                                */
 } cn_tune;
 
 /* ------------------------------------------------------------------ force */
