@@ -119,7 +119,7 @@ __device__ __forceinline__ void pair_f32(const float4 pj, const float (&xi)[K][3
 //                  velocity or a weight record follows)
 //   kSlotF4        float4 words per i-particle in a split tile's partial
 //   kSums          FP64 sums per i-particle in the merge (the result width)
-//   kSplitJ        lanes of a group share one i-particle (reduce_lanes)
+//   kSplitJ        lanes of a group share the thread's i-particles (reduce_lanes)
 //   kMinBlocks     256-thread CTAs per SM its register budget is sized for
 //   load_i         i-particle k's record(s) into registers
 //   zero, tile     clear the running sums; fold one staged j-tile into them
@@ -127,10 +127,11 @@ __device__ __forceinline__ void pair_f32(const float4 pj, const float (&xi)[K][3
 //   store_partial  a split tile's partial to its workspace slot
 //   add_partial    one loaded partial into the FP64 merge sums
 //   store_merged   the merged sums to the outputs
-// Gravity with or without the potential (F32Policy), its compensated form
-// (DDPolicy), the gradient of L = sum_i w_i . a_i (AdjointPolicy) and the
-// force-jerk-potential pipeline (JerkPolicy) all run through the one
-// staging, scheduling and merging loop of pair_kernel.
+// Gravity with or without the potential and with a per-particle softening
+// (F32Policy, packed F32x2Policy), its compensated form (DDPolicy), the
+// gradient of L = sum_i w_i . a_i (AdjointPolicy, AdjointX2Policy) and the
+// force-jerk-potential pipeline (JerkPolicy, JerkX2Policy) all run through
+// the one staging, scheduling and merging loop of pair_kernel.
 //
 // Plain FP32: per-tile FP32 partial folded into an FP32 running sum.
 // SPLITJ: groups of j_lanes consecutive lanes share one i-particle, lane
