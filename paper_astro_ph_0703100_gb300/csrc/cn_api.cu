@@ -286,6 +286,43 @@ cn_tune sym_default_tune(int64_t n, int sms) {
   return best;
 }
 
+// Launch shape of the plain FP32 form for mid-size systems (4096 < n_i <=
+// 20000; measured best shapes there are split-j with lane groups of 4 and
+// two i-particles per group). Few units per resident slot make the static
+// schedule quantise (n_i = 6000 in 564 units over 456 slots takes two
+// rounds), so the j-tile and block size come from the same schedule model
+// as the symmetric form: the busiest SM's CTAs x units per CTA x unit work,
+// at a rate that saturates with about six warps per SM. Resident CTAs per
+// SM follow from 158 registers per thread and the ring's shared memory.
+cn_tune mid_f32_tune(int64_t n_i, int64_t n_j, int sms) {
+  struct Shape {
+    int threads, j_tile, slots_per_sm;
+  };
+  static const Shape shapes[] = {{128, 1024, 3}, {128, 2048, 2}, {128, 4096, 1},
+                                 {256, 1024, 1}, {256, 2048, 1}, {256, 4096, 1}};
+  cn_tune best{};
+  double best_t = 0.0;
+  for (const Shape& sh : shapes) {
+    const int64_t it = sh.threads / 2;  // two i-particles per group of four lanes
+    const int64_t units = ((n_i + it - 1) / it) * ((std::max<int64_t>(n_j, 1) + sh.j_tile - 1) / sh.j_tile);
+    const int64_t g = std::min<int64_t>(static_cast<int64_t>(sh.slots_per_sm) * sms, units);
+    const int64_t per_sm = (g + sms - 1) / sms;
+    const int64_t per_cta = (units + g - 1) / g;
+    const double warps = static_cast<double>(per_sm) * sh.threads / 32.0;
+    const double t = static_cast<double>(per_sm * per_cta) * static_cast<double>(it * sh.j_tile) /
+                     std::min(1.0, warps / 6.0);
+    if (best_t == 0.0 || t < best_t) {
+      best_t = t;
+      best.i_per_thread = 2;
+      best.threads = sh.threads;
+      best.j_tile = sh.j_tile;
+      best.j_lanes = 4;
+      best.stages = n_j <= sh.j_tile ? 1 : 3;
+    }
+  }
+  return best;
+}
+
 cn_tune default_tune(int variant, int64_t n_i, int64_t n_j) {
   cn_tune t{};
   const int64_t n = std::max(n_i, n_j);
@@ -297,12 +334,12 @@ cn_tune default_tune(int variant, int64_t n_i, int64_t n_j) {
   t.stages = 4;
   t.threads = 128;
   t.j_lanes = 1;
-  if (f32 && n_i <= 8192) {
-    // small systems (measured at N = 1024 .. 8192, packed form): lane groups
+  if (f32 && n_i <= 4096) {
+    // small systems (measured at N = 1024 .. 4096, packed form): lane groups
     // of 32 (16 at N = 4096) share two i-particles and, where it fits, the
     // whole j set sits in one single-stage tile, so that each CTA covers
     // whole i-tiles and nothing is merged
-    const int jl = (n_i > 2048 && n_i <= 4096) ? 16 : 32;
+    const int jl = n_i > 2048 ? 16 : 32;
     t.i_per_thread = 2;
     t.j_lanes = jl;
     t.threads = n_i <= 1024 ? 128 : 256;
@@ -311,6 +348,7 @@ cn_tune default_tune(int variant, int64_t n_i, int64_t n_j) {
     t.stages = n_j <= t.j_tile ? 1 : 3;
     return t;
   }
+  if (f32 && n_i <= 20000) return mid_f32_tune(n_i, n_j, 152);
   if ((variant == cn::kJerk || variant == cn::kJerkPot || variant == cn::kAdjoint) && n_i <= 8192) {
     // small systems, measured at N = 1024 .. 8192 (force + jerk + potential,
     // and the adjoint, with the same optima): packed split-j, two
@@ -334,7 +372,8 @@ cn_tune default_tune(int variant, int64_t n_i, int64_t n_j) {
     // around 32K - 64K, K = 8 x 256 with 1024-record tiles above
     if (n < 24576) {
       t.i_per_thread = 2;
-      t.j_tile = 1024;
+      t.threads = 256;
+      t.j_tile = 512;
     } else if (n < 98304) {
       t.i_per_thread = 4;
       t.threads = 256;
@@ -406,6 +445,16 @@ cn_status resolve_plan(int dev, int variant, int64_t n_i, int64_t n_j, bool guar
       if (it != g_devices.end()) sms = it->second.sms;
     }
     if (sms > 0) t = sym_default_tune(std::max(n_i, n_j), sms);
+  }
+  if ((variant == cn::kF32 || variant == cn::kF32Pot || variant == cn::kF32EpsI || variant == cn::kF32EpsIPot) &&
+      n_i > 4096 && n_i <= 20000) {
+    int sms = 0;
+    {
+      std::lock_guard<std::mutex> lock(g_mu);
+      auto it = g_devices.find(dev);
+      if (it != g_devices.end()) sms = it->second.sms;
+    }
+    if (sms > 0) t = mid_f32_tune(n_i, n_j, sms);
   }
   cn_tune chosen{};
   bool have = false;
