@@ -596,8 +596,9 @@ def measure_rows(args, cn, torch, device, peak):
     p, eps2 = workload(131072, 131072)
     n = p.shape[0]
     tp = torch.from_numpy(p).to(device)
-    a_s = cn.cn_force_symmetric(tp, eps2)
+    a_s, pot_s = cn.cn_force_symmetric(tp, eps2, potential=True)
     ms = _events_ms(torch, lambda: cn.cn_force_symmetric(tp, eps2, acc_out=a_s), 10, stream)
+    ms_pot = _events_ms(torch, lambda: cn.cn_force_symmetric(tp, eps2, acc_out=a_s, pot_out=pot_s), 10, stream)
     r = synth.sample_rows(n, 512, seed=13)
     t0 = time.perf_counter()
     ra, _ = oracle.force(p, p, eps2, rows=r, potential=False)
@@ -605,6 +606,8 @@ def measure_rows(args, cn, torch, device, peak):
     sym_roof = 2.0 * lane_rate / SYM_LANE_OPS_PER_UNORDERED_PAIR
     rows["symmetric131072"] = {
         "pairs_per_s": float(n) * n / (ms / 1e3), "ms": ms,
+        "with_potential": {"pairs_per_s": float(n) * n / (ms_pot / 1e3), "ms": ms_pot,
+                           "launch_shape": "K = 8 x 128 threads (four sums per particle in the shared rows)"},
         "frac": float(n) * n / (ms / 1e3) / sym_roof, "roofline_pairs_per_s": sym_roof,
         "launch_shape": cn.cn_tune_get("symmetric", n, n),
         "emax": oracle.e_max(a_s.cpu().numpy()[r], ra),

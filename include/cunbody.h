@@ -215,6 +215,8 @@ CN_API cn_status cn_force_eps_i(int64_t n_i, const float *pos_eps_i, int64_t n_j
  *   eps2     : softening squared, finite and >= 0 (0: coincident pairs
  *              contribute nothing)
  *   acc_out  : float[n][3] device, 4-byte aligned, must not overlap pos_mass
+ *   pot_out  : float[n] potentials or NULL (the pair's -m r to both sides,
+ *              skipping pairs at exactly zero separation, as cn_force)
  * Asynchronous on `stream`; n == 0 is a no-op. Errors: CN_ERR_INVALID_ARG
  * (n < 0, bad eps2, NULL or overlapping buffers, a tune with j_lanes),
  * CN_ERR_MISALIGNED, CN_ERR_CUDA (launch), CN_ERR_WORKSPACE (below).
@@ -226,7 +228,8 @@ CN_API cn_status cn_force_eps_i(int64_t n_i, const float *pos_eps_i, int64_t n_j
  * band, with bitwise the same result. CN_ERR_WORKSPACE when even one band
  * cannot be held.
  */
-CN_API cn_status cn_force_symmetric(int64_t n, const float *pos_mass, float eps2, float *acc_out, cn_stream stream);
+CN_API cn_status cn_force_symmetric(int64_t n, const float *pos_mass, float eps2, float *acc_out, float *pot_out,
+                                    cn_stream stream);
 
 /* ------------------------------------------------------------------ batched */
 

@@ -184,15 +184,19 @@ def cn_force_dd_ws(pos_i, pos_mass_j, eps2, workspace, acc_out=None, pot_out=Non
     return _force("cn_force_dd_ws", True, pos_i, pos_mass_j, eps2, acc_out, pot_out, potential, stream, workspace)
 
 
-def cn_force_symmetric(pos_mass, eps2, acc_out=None, stream=None):
-    """Accelerations of all particles, each unordered pair evaluated once."""
+def cn_force_symmetric(pos_mass, eps2, acc_out=None, pot_out=None, potential=False, stream=None):
+    """Accelerations (n, 3) and, if requested, potentials (n,) of all
+    particles, each unordered pair evaluated once."""
     torch = _torch()
     _records(pos_mass, "pos_mass")
     n = pos_mass.shape[0]
     acc = _out(acc_out, (n, 3), torch.float32, pos_mass.device, "acc_out")
-    check(load().cn_force_symmetric(n, _ptr(pos_mass), float(eps2), _ptr(acc), _stream_handle(stream)),
+    pot = None
+    if potential or pot_out is not None:
+        pot = _out(pot_out, (n,), torch.float32, pos_mass.device, "pot_out")
+    check(load().cn_force_symmetric(n, _ptr(pos_mass), float(eps2), _ptr(acc), _ptr(pot), _stream_handle(stream)),
           "cn_force_symmetric")
-    return acc
+    return acc, pot
 
 
 def cn_workspace_bytes(variant, n_i, n_j) -> int:

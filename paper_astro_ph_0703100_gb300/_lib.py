@@ -45,7 +45,7 @@ SIGNATURES = {
     "cn_force_dd_ws": (c_int, [c_i64, vp, c_i64, vp, c_f32, vp, vp, vp, c_size, vp]),
     "cn_workspace_bytes": (c_size, [c_int, c_i64, c_i64]),
     "cn_force_noalloc": (c_int, [c_i64, vp, c_i64, vp, c_f32, vp, vp, vp]),
-    "cn_force_symmetric": (c_int, [c_i64, vp, c_f32, vp, vp]),
+    "cn_force_symmetric": (c_int, [c_i64, vp, c_f32, vp, vp, vp]),
     "cn_force_eps_i": (c_int, [c_i64, vp, c_i64, vp, vp, vp, vp]),
     "cn_batch_plan_create": (c_int, [c_i32, vp, vp, vp, c_int, ctypes.POINTER(vp)]),
     "cn_batch_plan_destroy": (c_int, [vp]),

@@ -253,7 +253,7 @@ int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 // N = 131072 (ordered pairs / s): they favour large K (fewer warp
 // reductions per pair), while small systems need small tiles to fill the
 // SMs.
-cn_tune sym_default_tune(int64_t n, int sms) {
+cn_tune sym_default_tune(int64_t n, int sms, bool pot) {
   struct Shape {
     int k, threads, j_tile, stages, slots_per_sm;
     double rate;
@@ -265,6 +265,8 @@ cn_tune sym_default_tune(int64_t n, int sms) {
   cn_tune best{};
   double best_t = 0.0;
   for (const Shape& sh : shapes) {
+    // with the potential the rows of j-side sums take four floats per particle
+    if (cn::sym_smem_bytes(sh.threads, sh.k, sh.j_tile, sh.stages, pot) > kMaxSmem) continue;
     const int64_t b = static_cast<int64_t>(sh.k) * sh.threads;
     const int64_t T = (std::max<int64_t>(n, 1) + b - 1) / b;
     const int64_t units = T * (T + 1) / 2;
@@ -362,7 +364,7 @@ cn_tune default_tune(int variant, int64_t n_i, int64_t n_j) {
     t.stages = n_j <= t.j_tile ? 1 : 3;
     return t;
   }
-  if (variant == cn::kSym) return sym_default_tune(n, 152);
+  if (variant == cn::kSym) return sym_default_tune(n, 152, false);
   if (variant == cn::kBatched || variant == cn::kBatchedPot) {
     t.i_per_thread = 4;
     t.j_tile = 256;
@@ -444,7 +446,7 @@ cn_status resolve_plan(int dev, int variant, int64_t n_i, int64_t n_j, bool guar
       auto it = g_devices.find(dev);
       if (it != g_devices.end()) sms = it->second.sms;
     }
-    if (sms > 0) t = sym_default_tune(std::max(n_i, n_j), sms);
+    if (sms > 0) t = sym_default_tune(std::max(n_i, n_j), sms, false);
   }
   if ((variant == cn::kF32 || variant == cn::kF32Pot || variant == cn::kF32EpsI || variant == cn::kF32EpsIPot) &&
       n_i > 4096 && n_i <= 20000) {
@@ -498,7 +500,7 @@ cn_status resolve_plan(int dev, int variant, int64_t n_i, int64_t n_j, bool guar
     if (p->j_tile % (8 * p->j_lanes)) return fail(CN_ERR_INVALID_ARG, "j_tile must be a multiple of 8 x j_lanes");
   }
   const size_t smem = variant == cn::kSym
-                          ? cn::sym_smem_bytes(p->threads, p->k, p->j_tile, p->stages)
+                          ? cn::sym_smem_bytes(p->threads, p->k, p->j_tile, p->stages, false)
                           : (two_records(variant) ? cn::adjoint_smem_bytes(*p) : cn::ring_smem_bytes(*p));
   if (smem > kMaxSmem) return fail(CN_ERR_INVALID_ARG, "the launch shape exceeds the shared memory of one CTA");
   if (variant == cn::kSym && p->i_tile() % p->j_tile) p->j_tile = std::min(p->j_tile, p->i_tile());
@@ -763,28 +765,42 @@ cn_status jerk_common(int64_t n_i, const float* pos_i, const float* vel_i, int64
   return e == cudaSuccess ? CN_OK : fail_cuda(e, "force-jerk kernel launch");
 }
 
-cn_status symmetric_common(int64_t n, const float* pos_mass, float eps2, float* acc_out, cudaStream_t s) {
+cn_status symmetric_common(int64_t n, const float* pos_mass, float eps2, float* acc_out, float* pot_out,
+                           cudaStream_t s) {
   if (n < 0) return fail(CN_ERR_INVALID_ARG, "n must be >= 0");
   cn_status st;
   if ((st = check_eps2(eps2)) != CN_OK) return st;
   if ((st = check_records(pos_mass, n, "pos_mass")) != CN_OK) return st;
   if (n > 0 && !acc_out) return fail(CN_ERR_INVALID_ARG, "acc_out is NULL");
-  if (acc_out && !aligned(acc_out, 4)) return fail(CN_ERR_MISALIGNED, "acc_out must be 4-byte aligned");
-  if (overlaps(acc_out, static_cast<size_t>(n) * 12, pos_mass, static_cast<size_t>(n) * 16))
-    return fail(CN_ERR_INVALID_ARG, "acc_out overlaps pos_mass");
+  if ((acc_out && !aligned(acc_out, 4)) || (pot_out && !aligned(pot_out, 4)))
+    return fail(CN_ERR_MISALIGNED, "outputs must be 4-byte aligned");
+  const size_t nb = static_cast<size_t>(n);
+  if (overlaps(acc_out, nb * 12, pos_mass, nb * 16) || overlaps(pot_out, nb * 4, pos_mass, nb * 16) ||
+      overlaps(acc_out, nb * 12, pot_out, nb * 4))
+    return fail(CN_ERR_INVALID_ARG, "outputs overlap pos_mass or each other");
+  const bool pot = pot_out != nullptr;
   if (n == 0) return CN_OK;
   int dev = 0;
   DeviceInfo* d = nullptr;
   if ((st = current_device(&dev, &d)) != CN_OK) return st;
   const bool guard = needs_guard(eps2);
+  // with the potential the default shape must leave room for four sums per
+  // particle in the shared-memory rows
+  cn_tune pot_tune{};
+  const cn_tune* shape = nullptr;
+  if (pot && !registered_tune(dev, cn::kSym, n, n)) {
+    pot_tune = sym_default_tune(n, d->sms, true);
+    shape = &pot_tune;
+  }
   Plan p;
-  if ((st = resolve_plan(dev, cn::kSym, n, n, guard, nullptr, &p)) != CN_OK) return st;
+  if ((st = resolve_plan(dev, cn::kSym, n, n, guard, shape, &p)) != CN_OK) return st;
   const int64_t B = p.i_tile();
   const int64_t T = ceil_div(n, B);
   if (T > 65535) return fail(CN_ERR_INVALID_ARG, "too many tiles for the symmetric form");
-  const size_t smem = cn::sym_smem_bytes(p.threads, p.k, p.j_tile, p.stages);
+  const size_t smem = cn::sym_smem_bytes(p.threads, p.k, p.j_tile, p.stages, pot);
+  if (smem > kMaxSmem) return fail(CN_ERR_INVALID_ARG, "the launch shape exceeds the shared memory of one CTA");
   int occ = 0;
-  cudaError_t e = cn::occupancy_sym(p.k, guard, p.threads, smem, &occ);
+  cudaError_t e = cn::occupancy_sym(p.k, guard, p.threads, smem, &occ, pot);
   if (e != cudaSuccess) return fail_cuda(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
   if (occ <= 0) return fail(CN_ERR_INVALID_ARG, "launch shape does not fit on one SM");
   // Slots: one [T][n_pad] array (16 T n_pad bytes, ~16 N^2 / B) when it fits
@@ -800,7 +816,7 @@ cn_status symmetric_common(int64_t n, const float* pos_mass, float eps2, float* 
   const bool banded = w < T;
   const size_t islot_b = static_cast<size_t>(T) * static_cast<size_t>(banded ? w * B : n_pad) * 16;
   const size_t jslot_b = banded ? align_up(static_cast<size_t>(w) * static_cast<size_t>(n_pad) * 16, 256) : 0;
-  const size_t acc64_b = banded ? static_cast<size_t>(n) * 24 : 0;
+  const size_t acc64_b = banded ? static_cast<size_t>(n) * 32 : 0;
   const size_t need = align_up(islot_b, 256) + jslot_b + acc64_b;
   size_t free_b = 0, total_b = 0;
   if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && need > free_b + library_data_bytes(s))
@@ -825,6 +841,7 @@ cn_status symmetric_common(int64_t n, const float* pos_mass, float eps2, float* 
   m.slots_j = a.slots_j;
   m.acc64 = banded ? reinterpret_cast<double*>(data + align_up(islot_b, 256) + jslot_b) : nullptr;
   m.acc_out = acc_out;
+  m.pot_out = pot_out;
   m.n = n;
   m.n_pad = n_pad;
   m.ld_i = a.ld_i;
@@ -843,7 +860,7 @@ cn_status symmetric_common(int64_t n, const float* pos_mass, float eps2, float* 
     m.last = r1 == T;
     const int grid = static_cast<int>(std::min<int64_t>(slots, a.units));
     if (inject("launch")) return fail(CN_ERR_CUDA, "kernel launch: injected launch failure");
-    e = cn::launch_sym(a, m, guard ? 1 : p.k, guard, p.threads, grid, smem, s);
+    e = cn::launch_sym(a, m, guard ? 1 : p.k, guard, p.threads, grid, smem, s, pot);
     if (e != cudaSuccess) return fail_cuda(e, "symmetric kernel launch");
   }
   return CN_OK;
@@ -1313,8 +1330,9 @@ cn_status cn_force_jerk(int64_t n_i, const float* pos_i, const float* vel_i, int
                      reinterpret_cast<cudaStream_t>(stream));
 }
 
-cn_status cn_force_symmetric(int64_t n, const float* pos_mass, float eps2, float* acc_out, cn_stream stream) {
-  return symmetric_common(n, pos_mass, eps2, acc_out, reinterpret_cast<cudaStream_t>(stream));
+cn_status cn_force_symmetric(int64_t n, const float* pos_mass, float eps2, float* acc_out, float* pot_out,
+                             cn_stream stream) {
+  return symmetric_common(n, pos_mass, eps2, acc_out, pot_out, reinterpret_cast<cudaStream_t>(stream));
 }
 
 cn_status cn_potential_energy(int64_t n, const float* pos_mass, const float* pot, double* w_out, cn_stream stream) {

@@ -62,8 +62,13 @@ __device__ __forceinline__ void unit_tiles(int64_t u, int32_t T, int32_t* I, int
 // the tile, so larger blocks cannot hold more CTAs anyway.
 constexpr int sym_min_blocks(int nt_max) { return nt_max <= 64 ? 8 : (nt_max <= 128 ? 3 : 1); }
 
-template <int K, bool GUARD, int NTMAX>
+// POT: the potential rides along as a fourth sum (each pair's -m r to both
+// sides, skipping pairs whose separation is exactly zero); the warp
+// reduce-scatter then runs over 32 values per lane and ends with every lane
+// owning one (j record, component) sum.
+template <int K, bool GUARD, int NTMAX, bool POT>
 __global__ void __launch_bounds__(NTMAX, sym_min_blocks(NTMAX)) sym_kernel(const __grid_constant__ SymArgs a) {
+  constexpr int NCJ = POT ? 4 : 3;  // sums per particle
   extern __shared__ __align__(128) unsigned char smem[];
   const int NT = blockDim.x;
   const int tid = threadIdx.x;
@@ -78,7 +83,7 @@ __global__ void __launch_bounds__(NTMAX, sym_min_blocks(NTMAX)) sym_kernel(const
   uint64_t* empty = full + S;
   volatile int* ctl = reinterpret_cast<volatile int*>(smem + 16 * S);  // [0] abort
   float4* ring = reinterpret_cast<float4*>(smem + 256);
-  float* jrows = reinterpret_cast<float*>(ring + static_cast<size_t>(S) * JS);  // [NW][B][3]
+  float* jrows = reinterpret_cast<float*>(ring + static_cast<size_t>(S) * JS);  // [NW][B][NCJ]
 
   if (tid == 0) {
     for (int s = 0; s < S; ++s) {
@@ -104,7 +109,7 @@ __global__ void __launch_bounds__(NTMAX, sym_min_blocks(NTMAX)) sym_kernel(const
   // packed form): negated coordinates and negated masses
   static_assert(K == 1 || K % 2 == 0, "K is 1 or even");
   constexpr int P = (K + 1) / 2;
-  float2 nxi[P][3], nmi[P], acc[P][3];
+  float2 nxi[P][3], nmi[P], acc[P][3], pacc[P];
   auto half = [](float2& v, int k) -> float& { return (k & 1) ? v.y : v.x; };
   int32_t cur_I = -1;
   for (int64_t u = ub; u < ue; ++u) {
@@ -131,9 +136,9 @@ __global__ void __launch_bounds__(NTMAX, sym_min_blocks(NTMAX)) sym_kernel(const
       cur_I = I;
     }
 #pragma unroll
-    for (int p = 0; p < P; ++p) acc[p][0] = acc[p][1] = acc[p][2] = make_float2(0.f, 0.f);
+    for (int p = 0; p < P; ++p) acc[p][0] = acc[p][1] = acc[p][2] = pacc[p] = make_float2(0.f, 0.f);
     if (!diag)
-      for (int e = tid; e < NW * B * 3; e += NT) jrows[e] = 0.f;
+      for (int e = tid; e < NW * B * NCJ; e += NT) jrows[e] = 0.f;
     __syncthreads();
     for (int sub = 0; sub < subs; ++sub) {
       // ---- producer: keep D loads ahead (thread 0)
@@ -181,12 +186,19 @@ __global__ void __launch_bounds__(NTMAX, sym_min_blocks(NTMAX)) sym_kernel(const
               const float4 pj = js[j + jj];
               const float2 jx = make_float2(pj.x, pj.x), jy = make_float2(pj.y, pj.y);
               const float2 jz = make_float2(pj.z, pj.z), jm = make_float2(pj.w, pj.w);
+              const float2 njm = make_float2(-pj.w, -pj.w);
 #pragma unroll
               for (int p = 0; p < P; ++p) {
                 const float2 dx = __fadd2_rn(jx, nxi[p][0]);
                 const float2 dy = __fadd2_rn(jy, nxi[p][1]);
                 const float2 dz = __fadd2_rn(jz, nxi[p][2]);
-                const float2 s = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, e2)));
+                float2 s, d2;
+                if constexpr (POT) {
+                  d2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+                  s = __fadd2_rn(d2, e2);
+                } else {
+                  s = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, e2)));
+                }
                 float2 r = make_float2(rsqrt_mufu(s.x), rsqrt_mufu(s.y));
                 if constexpr (GUARD) {
                   r.x = (s.x > 0.f) ? r.x : 0.f;
@@ -197,27 +209,38 @@ __global__ void __launch_bounds__(NTMAX, sym_min_blocks(NTMAX)) sym_kernel(const
                 acc[p][0] = __ffma2_rn(q, dx, acc[p][0]);
                 acc[p][1] = __ffma2_rn(q, dy, acc[p][1]);
                 acc[p][2] = __ffma2_rn(q, dz, acc[p][2]);
+                if constexpr (POT) {
+                  const float2 rp = make_float2(d2.x != 0.f ? r.x : 0.f, d2.y != 0.f ? r.y : 0.f);
+                  pacc[p] = __ffma2_rn(njm, rp, pacc[p]);
+                }
               }
             }
           }
         } else {
-          float* myrow = jrows + static_cast<size_t>(warp) * B * 3;
+          float* myrow = jrows + static_cast<size_t>(warp) * B * NCJ;
           const int jbase = sub * JS;
 #pragma unroll 1
           for (int j = 0; j < JS; j += kSymBatch) {
-            float c[kSymBatch][3];
+            float c[kSymBatch][NCJ];
 #pragma unroll
             for (int t = 0; t < kSymBatch; ++t) {
               const float4 pj = js[j + (t ^ perm)];
               const float2 jx = make_float2(pj.x, pj.x), jy = make_float2(pj.y, pj.y);
               const float2 jz = make_float2(pj.z, pj.z), jm = make_float2(pj.w, pj.w);
-              float2 cx = make_float2(0.f, 0.f), cy = cx, cz = cx;
+              const float2 njm = make_float2(-pj.w, -pj.w);
+              float2 cx = make_float2(0.f, 0.f), cy = cx, cz = cx, cp = cx;
 #pragma unroll
               for (int p = 0; p < P; ++p) {
                 const float2 dx = __fadd2_rn(jx, nxi[p][0]);
                 const float2 dy = __fadd2_rn(jy, nxi[p][1]);
                 const float2 dz = __fadd2_rn(jz, nxi[p][2]);
-                const float2 s = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, e2)));
+                float2 s, d2;
+                if constexpr (POT) {
+                  d2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+                  s = __fadd2_rn(d2, e2);
+                } else {
+                  s = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, e2)));
+                }
                 float2 r = make_float2(rsqrt_mufu(s.x), rsqrt_mufu(s.y));
                 if constexpr (GUARD) {
                   r.x = (s.x > 0.f) ? r.x : 0.f;
@@ -233,10 +256,16 @@ __global__ void __launch_bounds__(NTMAX, sym_min_blocks(NTMAX)) sym_kernel(const
                 cx = __ffma2_rn(qj, dx, cx);
                 cy = __ffma2_rn(qj, dy, cy);
                 cz = __ffma2_rn(qj, dz, cz);
+                if constexpr (POT) {
+                  const float2 rp = make_float2(d2.x != 0.f ? r.x : 0.f, d2.y != 0.f ? r.y : 0.f);
+                  pacc[p] = __ffma2_rn(njm, rp, pacc[p]);  // -m_j r onto particle i
+                  cp = __ffma2_rn(nmi[p], rp, cp);         // -m_i r onto particle j
+                }
               }
               c[t][0] = cx.x + cx.y;
               c[t][1] = cy.x + cy.y;
               c[t][2] = cz.x + cz.y;
+              if constexpr (POT) c[t][3] = cp.x + cp.y;
             }
             // reduce-scatter over the warp: after the three halving steps
             // lane l holds, in c[0], the sum over the 8 lanes that share
@@ -244,23 +273,36 @@ __global__ void __launch_bounds__(NTMAX, sym_min_blocks(NTMAX)) sym_kernel(const
 #pragma unroll
             for (int t = 0; t < 4; ++t)
 #pragma unroll
-              for (int d = 0; d < 3; ++d) c[t][d] += __shfl_xor_sync(0xffffffffu, c[t + 4][d], 16);
+              for (int d = 0; d < NCJ; ++d) c[t][d] += __shfl_xor_sync(0xffffffffu, c[t + 4][d], 16);
 #pragma unroll
             for (int t = 0; t < 2; ++t)
 #pragma unroll
-              for (int d = 0; d < 3; ++d) c[t][d] += __shfl_xor_sync(0xffffffffu, c[t + 2][d], 8);
+              for (int d = 0; d < NCJ; ++d) c[t][d] += __shfl_xor_sync(0xffffffffu, c[t + 2][d], 8);
 #pragma unroll
-            for (int d = 0; d < 3; ++d) c[0][d] += __shfl_xor_sync(0xffffffffu, c[1][d], 4);
+            for (int d = 0; d < NCJ; ++d) c[0][d] += __shfl_xor_sync(0xffffffffu, c[1][d], 4);
+            if constexpr (POT) {
+              // two more halving steps over the four components: lane bit 1
+              // keeps components {0, 1} or {2, 3}, lane bit 0 one of those
+              const int b1 = (lane >> 1) & 1, b0 = lane & 1;
+              float v0 = b1 ? c[0][2] : c[0][0], v1 = b1 ? c[0][3] : c[0][1];
+              const float o0 = b1 ? c[0][0] : c[0][2], o1 = b1 ? c[0][1] : c[0][3];
+              v0 += __shfl_xor_sync(0xffffffffu, o0, 2);
+              v1 += __shfl_xor_sync(0xffffffffu, o1, 2);
+              float w = b0 ? v1 : v0;
+              w += __shfl_xor_sync(0xffffffffu, b0 ? v0 : v1, 1);
+              myrow[static_cast<size_t>(jbase + j + perm) * 4 + 2 * b1 + b0] += w;
+            } else {
 #pragma unroll
-            for (int d = 0; d < 3; ++d) {
-              c[0][d] += __shfl_xor_sync(0xffffffffu, c[0][d], 2);
-              c[0][d] += __shfl_xor_sync(0xffffffffu, c[0][d], 1);
-            }
-            if ((lane & 3) == 0) {
-              float* dst = myrow + static_cast<size_t>(jbase + j + perm) * 3;
-              dst[0] += c[0][0];
-              dst[1] += c[0][1];
-              dst[2] += c[0][2];
+              for (int d = 0; d < 3; ++d) {
+                c[0][d] += __shfl_xor_sync(0xffffffffu, c[0][d], 2);
+                c[0][d] += __shfl_xor_sync(0xffffffffu, c[0][d], 1);
+              }
+              if ((lane & 3) == 0) {
+                float* dst = myrow + static_cast<size_t>(jbase + j + perm) * 3;
+                dst[0] += c[0][0];
+                dst[1] += c[0][1];
+                dst[2] += c[0][2];
+              }
             }
           }
         }
@@ -274,20 +316,21 @@ __global__ void __launch_bounds__(NTMAX, sym_min_blocks(NTMAX)) sym_kernel(const
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       const int64_t p = static_cast<int64_t>(I - a.row0) * B + k * NT + tid;
-      a.slots_i[static_cast<size_t>(J) * a.ld_i + p] =
-          make_float4(half(acc[k >> 1][0], k), half(acc[k >> 1][1], k), half(acc[k >> 1][2], k), 0.f);
+      a.slots_i[static_cast<size_t>(J) * a.ld_i + p] = make_float4(
+          half(acc[k >> 1][0], k), half(acc[k >> 1][1], k), half(acc[k >> 1][2], k), POT ? half(pacc[k >> 1], k) : 0.f);
     }
     if (!diag) {
       for (int jl = tid; jl < B; jl += NT) {
-        float sx = 0.f, sy = 0.f, sz = 0.f;
+        float sx = 0.f, sy = 0.f, sz = 0.f, sp = 0.f;
         for (int w = 0; w < NW; ++w) {
-          const float* r = jrows + (static_cast<size_t>(w) * B + jl) * 3;
+          const float* r = jrows + (static_cast<size_t>(w) * B + jl) * NCJ;
           sx += r[0];
           sy += r[1];
           sz += r[2];
+          if constexpr (POT) sp += r[3];
         }
         const int64_t p = static_cast<int64_t>(J) * B + jl;
-        a.slots_j[static_cast<size_t>(I - a.row0) * a.n_pad + p] = make_float4(sx, sy, sz, 0.f);
+        a.slots_j[static_cast<size_t>(I - a.row0) * a.n_pad + p] = make_float4(sx, sy, sz, sp);
       }
     }
     __syncthreads();
@@ -307,11 +350,12 @@ __global__ void __launch_bounds__(NTMAX, sym_min_blocks(NTMAX)) sym_kernel(const
 __global__ void sym_merge_kernel(const SymMerge m) {
   const int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (p >= m.n) return;
-  double sx = 0.0, sy = 0.0, sz = 0.0;
+  double sx = 0.0, sy = 0.0, sz = 0.0, sp = 0.0;
   if (!m.first) {
-    sx = m.acc64[3 * p + 0];
-    sy = m.acc64[3 * p + 1];
-    sz = m.acc64[3 * p + 2];
+    sx = m.acc64[4 * p + 0];
+    sy = m.acc64[4 * p + 1];
+    sz = m.acc64[4 * p + 2];
+    sp = m.acc64[4 * p + 3];
   }
   const int32_t P = static_cast<int32_t>(p / m.tile);
   // j-side: units (I, P) of the band with I < P
@@ -321,6 +365,7 @@ __global__ void sym_merge_kernel(const SymMerge m) {
     sx += v.x;
     sy += v.y;
     sz += v.z;
+    sp += v.w;
   }
   // i-side: units (P, Q) with Q >= P, when P is one of the band's rows
   if (P >= m.row0 && P < m.row1) {
@@ -330,47 +375,55 @@ __global__ void sym_merge_kernel(const SymMerge m) {
       sx += v.x;
       sy += v.y;
       sz += v.z;
+      sp += v.w;
     }
   }
   if (m.last) {
     m.acc_out[3 * p + 0] = static_cast<float>(sx);
     m.acc_out[3 * p + 1] = static_cast<float>(sy);
     m.acc_out[3 * p + 2] = static_cast<float>(sz);
+    if (m.pot_out) m.pot_out[p] = static_cast<float>(sp);
   } else {
-    m.acc64[3 * p + 0] = sx;
-    m.acc64[3 * p + 1] = sy;
-    m.acc64[3 * p + 2] = sz;
+    m.acc64[4 * p + 0] = sx;
+    m.acc64[4 * p + 1] = sy;
+    m.acc64[4 * p + 2] = sz;
+    m.acc64[4 * p + 3] = sp;
   }
 }
 
-template <int K, bool GUARD>
+template <int K, bool GUARD, bool POT>
 const void* sym_fn(int threads) {
-  if (threads <= 64) return reinterpret_cast<const void*>(&sym_kernel<K, GUARD, 64>);
-  if (threads <= 128) return reinterpret_cast<const void*>(&sym_kernel<K, GUARD, 128>);
-  return reinterpret_cast<const void*>(&sym_kernel<K, GUARD, 256>);
+  if (threads <= 64) return reinterpret_cast<const void*>(&sym_kernel<K, GUARD, 64, POT>);
+  if (threads <= 128) return reinterpret_cast<const void*>(&sym_kernel<K, GUARD, 128, POT>);
+  return reinterpret_cast<const void*>(&sym_kernel<K, GUARD, 256, POT>);
 }
 
-const void* sym_select(int k, bool guard, int threads) {
+template <bool POT>
+const void* sym_select_pot(int k, bool guard, int threads) {
   if (threads > 256) return nullptr;
-  if (guard) return k == 1 ? sym_fn<1, true>(threads) : nullptr;
+  if (guard) return k == 1 ? sym_fn<1, true, POT>(threads) : nullptr;
   switch (k) {
-    case 1: return sym_fn<1, false>(threads);
-    case 2: return sym_fn<2, false>(threads);
-    case 4: return sym_fn<4, false>(threads);
-    case 8: return sym_fn<8, false>(threads);
+    case 1: return sym_fn<1, false, POT>(threads);
+    case 2: return sym_fn<2, false, POT>(threads);
+    case 4: return sym_fn<4, false, POT>(threads);
+    case 8: return sym_fn<8, false, POT>(threads);
     default: return nullptr;
   }
 }
 
-}  // namespace
-
-size_t sym_smem_bytes(int threads, int k, int sub_tile, int stages) {
-  const size_t b = static_cast<size_t>(threads) * k;
-  return 256 + static_cast<size_t>(stages) * sub_tile * 16 + (threads / 32) * b * 3 * sizeof(float);
+const void* sym_select(int k, bool guard, int threads, bool pot) {
+  return pot ? sym_select_pot<true>(k, guard, threads) : sym_select_pot<false>(k, guard, threads);
 }
 
-cudaError_t occupancy_sym(int k, bool guard, int threads, size_t smem, int* ctas) {
-  const void* f = sym_select(k, guard, threads);
+}  // namespace
+
+size_t sym_smem_bytes(int threads, int k, int sub_tile, int stages, bool pot) {
+  const size_t b = static_cast<size_t>(threads) * k;
+  return 256 + static_cast<size_t>(stages) * sub_tile * 16 + (threads / 32) * b * (pot ? 4 : 3) * sizeof(float);
+}
+
+cudaError_t occupancy_sym(int k, bool guard, int threads, size_t smem, int* ctas, bool pot) {
+  const void* f = sym_select(k, guard, threads, pot);
   if (!f) return cudaErrorInvalidValue;
   cudaError_t e = prepare_kernel(f, smem);
   if (e != cudaSuccess) return e;
@@ -378,8 +431,8 @@ cudaError_t occupancy_sym(int k, bool guard, int threads, size_t smem, int* ctas
 }
 
 cudaError_t launch_sym(const SymArgs& a, const SymMerge& m, int k, bool guard, int threads, int grid, size_t smem,
-                       cudaStream_t s) {
-  const void* f = sym_select(k, guard, threads);
+                       cudaStream_t s, bool pot) {
+  const void* f = sym_select(k, guard, threads, pot);
   if (!f) return cudaErrorInvalidValue;
   cudaError_t e = prepare_kernel(f, smem);
   if (e != cudaSuccess) return e;

@@ -32,15 +32,16 @@ struct SymArgs {
 };
 
 // Per-particle merge of one band: adds, in FP64 and in ascending partner
-// order, the band's j-side slots (partners I in [row0, row1), I < P) and,
+// order, the band's j-side slots (x, y, z and the potential in w) (partners I in [row0, row1), I < P) and,
 // for particles of the band's own tiles, their i-side slots (partners
 // Q >= P) to the running sums (acc64, or zero for the first band); the last
 // band writes the FP32 accelerations, the others store the FP64 sums.
 struct SymMerge {
   const float4* slots_i;
   const float4* slots_j;
-  double* acc64;     // [n][3], NULL with a single band
+  double* acc64;     // [n][4] (acceleration, potential), NULL with a single band
   float* acc_out;    // [n][3]
+  float* pot_out;    // [n] or NULL
   int64_t n;
   int64_t n_pad;
   int64_t ld_i;
@@ -52,9 +53,9 @@ struct SymMerge {
   int32_t last;
 };
 
-size_t sym_smem_bytes(int threads, int k, int sub_tile, int stages);
-cudaError_t occupancy_sym(int k, bool guard, int threads, size_t smem, int* ctas);
+size_t sym_smem_bytes(int threads, int k, int sub_tile, int stages, bool pot);
+cudaError_t occupancy_sym(int k, bool guard, int threads, size_t smem, int* ctas, bool pot);
 cudaError_t launch_sym(const SymArgs& a, const SymMerge& m, int k, bool guard, int threads, int grid, size_t smem,
-                       cudaStream_t s);
+                       cudaStream_t s, bool pot);
 
 }  // namespace cn

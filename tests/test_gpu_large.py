@@ -35,7 +35,7 @@ def test_symmetric_two_million_in_bands():
     n = 1 << 21
     p = synth.plummer(n, 24)
     eps2 = float(np.float32(synth.plummer_eps(n)) ** 2)
-    a = cn.cn_force_symmetric(dev_tensor(p), eps2)
+    a, _ = cn.cn_force_symmetric(dev_tensor(p), eps2)
     torch.cuda.synchronize()
     assert cn.cn_get_device_status() == 0
     rows = synth.sample_rows(n, 128, 25)

@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gpu_common import dev_tensor, e_max, lib, torch_cuda
+from gpu_common import dev_tensor, e_max, lib, rel_pot_err, torch_cuda
 from paper_astro_ph_0703100_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -19,12 +19,12 @@ pytestmark = pytest.mark.gpu
 TOL = 1e-5
 
 
-def run(cn, p, eps2):
+def run(cn, p, eps2, potential=False):
     torch = torch_cuda()
-    a = cn.cn_force_symmetric(dev_tensor(p), eps2)
+    a, pot = cn.cn_force_symmetric(dev_tensor(p), eps2, potential=potential)
     torch.cuda.synchronize()
     assert cn.cn_get_device_status() == 0
-    return a.cpu().numpy()
+    return (a.cpu().numpy(), pot.cpu().numpy()) if potential else a.cpu().numpy()
 
 
 TUNES = [None,
@@ -40,13 +40,36 @@ TUNES = [None,
 def test_symmetric_ragged_and_launch_shapes(n, tune):
     cn = lib()
     p = synth.plummer(n, 50 + n)
+    # with the potential, tiles of 2048 particles need more shared memory than a CTA has
+    with_pot = tune is None or tune["i_per_thread"] * tune["threads"] <= 1024
     cn.cn_tune_set("symmetric", n, n, tune)
     try:
         a = run(cn, p, 1e-3)
+        if with_pot:
+            a2, pot = run(cn, p, 1e-3, potential=True)
     finally:
         cn.cn_tune_set("symmetric", n, n, None)
-    ref, _ = oracle.force(p, p, 1e-3, potential=False)
+    ref, rpot = oracle.force(p, p, 1e-3)
     assert e_max(a, ref) <= TOL
+    if with_pot:
+        assert e_max(a2, ref) <= TOL
+        assert rel_pot_err(pot, rpot) <= TOL
+
+
+def test_symmetric_potential_rejects_oversized_tiles():
+    """An explicit 2048-particle tile cannot hold four sums per particle."""
+    cn = lib()
+    torch = torch_cuda()
+    n = 3000
+    cn.cn_tune_set("symmetric", n, n, {"i_per_thread": 8, "threads": 256, "j_tile": 256, "stages": 3})
+    try:
+        d = dev_tensor(synth.plummer(n, 34))
+        with pytest.raises(cn.CunbodyError):
+            cn.cn_force_symmetric(d, 1e-3, potential=True)
+        a, _ = cn.cn_force_symmetric(d, 1e-3)  # the force alone fits
+        torch.cuda.synchronize()
+    finally:
+        cn.cn_tune_set("symmetric", n, n, None)
 
 
 def test_symmetric_unequal_masses_many_tiles():
@@ -80,8 +103,8 @@ def test_symmetric_deterministic_and_matches_plain_form():
     n = 9000
     p = synth.plummer(n, 12)
     d = dev_tensor(p)
-    a1 = cn.cn_force_symmetric(d, 1e-3)
-    a2 = cn.cn_force_symmetric(d, 1e-3)
+    a1, _ = cn.cn_force_symmetric(d, 1e-3)
+    a2, _ = cn.cn_force_symmetric(d, 1e-3)
     plain, _ = cn.cn_force(d, d, 1e-3)
     torch.cuda.synchronize()
     assert torch.equal(a1, a2)
@@ -102,23 +125,24 @@ def test_symmetric_bands_bitwise_equal_one_band(rows):
     shape = {"i_per_thread": 2, "threads": 64, "j_tile": 64, "stages": 3}
     cn.cn_tune_set("symmetric", n, n, shape)
     try:
-        one = cn.cn_force_symmetric(d, 1e-4)
+        one, pone = cn.cn_force_symmetric(d, 1e-4, potential=True)
         cn.cn_tune_set("symmetric", n, n, dict(shape, chunk_units=rows))
-        banded = cn.cn_force_symmetric(d, 1e-4)
+        banded, pband = cn.cn_force_symmetric(d, 1e-4, potential=True)
         torch.cuda.synchronize()
     finally:
         cn.cn_tune_set("symmetric", n, n, None)
     assert cn.cn_get_device_status() == 0
-    assert torch.equal(one, banded)
-    ref, _ = oracle.force(p, p, 1e-4, potential=False)
+    assert torch.equal(one, banded) and torch.equal(pone, pband)
+    ref, rpot = oracle.force(p, p, 1e-4)
     assert e_max(banded.cpu().numpy(), ref) <= TOL
+    assert rel_pot_err(pband.cpu().numpy(), rpot) <= TOL
 
 
 def test_symmetric_empty():
     cn = lib()
     torch = torch_cuda()
-    a = cn.cn_force_symmetric(torch.empty((0, 4), dtype=torch.float32, device="cuda"), 1e-3)
-    assert a.shape == (0, 3)
+    a, pot = cn.cn_force_symmetric(torch.empty((0, 4), dtype=torch.float32, device="cuda"), 1e-3, potential=True)
+    assert a.shape == (0, 3) and pot.shape == (0,)
 
 
 def test_symmetric_rejects_j_lanes():
@@ -154,3 +178,36 @@ def test_symmetric_million_automatic_bands_sampled():
     rows = synth.sample_rows(n, 256, 21)
     ref, _ = oracle.force(p, p, eps2, rows=rows, potential=False)
     assert e_max(a[rows], ref) <= TOL
+
+
+def test_symmetric_potential_coincident_points_and_zero_softening():
+    """Duplicated positions in different tiles and eps2 = 0: the potential
+    skips pairs at zero separation, the force gets nothing from them."""
+    cn = lib()
+    p = synth.plummer(700, 31)
+    p = np.concatenate([p, p[:90]])
+    for eps2 in (0.0, 1e-3):
+        a, pot = run(cn, p, eps2, potential=True)
+        ref, rpot = oracle.force(p, p, eps2)
+        assert np.all(np.isfinite(a)) and np.all(np.isfinite(pot))
+        assert e_max(a, ref) <= TOL
+        assert rel_pot_err(pot, rpot) <= TOL
+
+
+def test_symmetric_potential_energy_plummer_131072():
+    """W = 1/2 sum m phi from the symmetric potentials at the benchmark size."""
+    cn = lib()
+    torch = torch_cuda()
+    n = 131072
+    p = synth.plummer(n, 32)
+    eps2 = float(np.float32(synth.plummer_eps(n)) ** 2)
+    d = dev_tensor(p)
+    _, pot = cn.cn_force_symmetric(d, eps2, potential=True)
+    _, pot_plain = cn.cn_force(d, d, eps2, potential=True)
+    torch.cuda.synchronize()
+    rows = synth.sample_rows(n, 256, 33)
+    _, rpot = oracle.force(p, p, eps2, rows=rows)
+    assert rel_pot_err(pot.cpu().numpy()[rows], rpot) <= TOL
+    w_sym = float(cn.cn_potential_energy(d, pot).item())
+    w_plain = float(cn.cn_potential_energy(d, pot_plain).item())
+    assert abs(w_sym - w_plain) <= 1e-6 * abs(w_plain)
