@@ -606,8 +606,7 @@ def measure_rows(args, cn, torch, device, peak):
     sym_roof = 2.0 * lane_rate / SYM_LANE_OPS_PER_UNORDERED_PAIR
     rows["symmetric131072"] = {
         "pairs_per_s": float(n) * n / (ms / 1e3), "ms": ms,
-        "with_potential": {"pairs_per_s": float(n) * n / (ms_pot / 1e3), "ms": ms_pot,
-                           "launch_shape": "K = 8 x 128 threads (four sums per particle in the shared rows)"},
+        "with_potential": {"pairs_per_s": float(n) * n / (ms_pot / 1e3), "ms": ms_pot},
         "frac": float(n) * n / (ms / 1e3) / sym_roof, "roofline_pairs_per_s": sym_roof,
         "launch_shape": cn.cn_tune_get("symmetric", n, n),
         "emax": oracle.e_max(a_s.cpu().numpy()[r], ra),

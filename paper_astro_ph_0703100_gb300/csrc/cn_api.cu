@@ -256,12 +256,13 @@ int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 cn_tune sym_default_tune(int64_t n, int sms, bool pot) {
   struct Shape {
     int k, threads, j_tile, stages, slots_per_sm;
-    double rate;
+    double rate, rate_pot;  // saturated effective pairs/s without and with the potential
   };
   static const Shape shapes[] = {
-      {8, 256, 256, 3, 1, 3.56e12}, {8, 128, 256, 4, 3, 3.22e12}, {8, 64, 128, 4, 8, 3.05e12},
-      {4, 128, 256, 4, 3, 2.87e12}, {4, 64, 128, 4, 8, 2.64e12},  {2, 64, 64, 4, 8, 1.86e12},
-      {1, 64, 64, 4, 9, 0.93e12}};
+      {8, 256, 256, 3, 1, 3.56e12, 0.0},     {4, 256, 256, 3, 1, 3.10e12, 2.59e12},
+      {8, 128, 256, 4, 3, 3.22e12, 2.38e12}, {8, 64, 128, 4, 8, 3.05e12, 2.38e12},
+      {4, 128, 256, 4, 3, 2.87e12, 2.33e12}, {4, 64, 128, 4, 8, 2.64e12, 2.10e12},
+      {2, 64, 64, 4, 8, 1.86e12, 1.50e12},   {1, 64, 64, 4, 9, 0.93e12, 0.75e12}};
   cn_tune best{};
   double best_t = 0.0;
   for (const Shape& sh : shapes) {
@@ -274,7 +275,7 @@ cn_tune sym_default_tune(int64_t n, int sms, bool pot) {
     const int64_t per_sm = (g + sms - 1) / sms;
     const int64_t per_cta = (units + g - 1) / g;
     const double warps = static_cast<double>(per_sm) * sh.threads / 32.0;
-    const double sm_rate = sh.rate / sms * std::min(1.0, warps / 6.0);
+    const double sm_rate = (pot ? sh.rate_pot : sh.rate) / sms * std::min(1.0, warps / 6.0);
     const double t = static_cast<double>(per_sm * per_cta) * 2.0 * static_cast<double>(b * b) / sm_rate;
     if (best_t == 0.0 || t < best_t) {
       best_t = t;
