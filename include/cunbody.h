@@ -223,7 +223,7 @@ CN_API cn_status cn_force_eps_i(int64_t n_i, const float *pos_eps_i, int64_t n_j
  * Uses a library workspace of per-(tile, partner) slots: 16 N^2 / B bytes
  * for tiles of B particles (134 MB at N = 131072 with the default
  * 2048-particle tiles) while that fits in 2 GiB; above, the tile rows are
- * processed in bands of w rows (about 32 w N + 24 N bytes, w chosen to fit
+ * processed in bands of w rows (about 32 w N + 32 N bytes, w chosen to fit
  * 2 GiB, or set by the tune's chunk_units), one kernel and one merge per
  * band, with bitwise the same result. CN_ERR_WORKSPACE when even one band
  * cannot be held.

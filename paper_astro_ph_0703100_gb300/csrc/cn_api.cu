@@ -806,7 +806,7 @@ cn_status symmetric_common(int64_t n, const float* pos_mass, float eps2, float* 
   if (occ <= 0) return fail(CN_ERR_INVALID_ARG, "launch shape does not fit on one SM");
   // Slots: one [T][n_pad] array (16 T n_pad bytes, ~16 N^2 / B) when it fits
   // in kSymSlotCap, else bands of w tile rows: [T][w B] i-side and [w][n_pad]
-  // j-side slots plus FP64 running sums, ~32 w N + 24 N bytes. The tune's
+  // j-side slots plus FP64 running sums, ~32 w N + 32 N bytes. The tune's
   // chunk_units, when set, fixes the rows per band.
   const int64_t n_pad = T * B;
   int64_t w = T;
