@@ -21,6 +21,7 @@ from ._lib import CunbodyError, STATUS, cn_tune, check, load
 
 __all__ = [
     "CunbodyError",
+    "STATUS",
     "VARIANT",
     "cn_force",
     "cn_force_ws",
