@@ -347,6 +347,9 @@ __global__ void __launch_bounds__(NTMAX, sym_min_blocks(NTMAX)) sym_kernel(const
 
 // Per-particle merge of one band (see SymMerge): partners in ascending
 // order, FP64 sums carried across bands.
+// POT: the potential (slot word 3) is summed too; without it that word is
+// skipped, since FP64 additions are the merge's slow part on this GPU.
+template <bool POT>
 __global__ void sym_merge_kernel(const SymMerge m) {
   const int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (p >= m.n) return;
@@ -365,7 +368,7 @@ __global__ void sym_merge_kernel(const SymMerge m) {
     sx += v.x;
     sy += v.y;
     sz += v.z;
-    sp += v.w;
+    if constexpr (POT) sp += v.w;
   }
   // i-side: units (P, Q) with Q >= P, when P is one of the band's rows
   if (P >= m.row0 && P < m.row1) {
@@ -375,14 +378,14 @@ __global__ void sym_merge_kernel(const SymMerge m) {
       sx += v.x;
       sy += v.y;
       sz += v.z;
-      sp += v.w;
+      if constexpr (POT) sp += v.w;
     }
   }
   if (m.last) {
     m.acc_out[3 * p + 0] = static_cast<float>(sx);
     m.acc_out[3 * p + 1] = static_cast<float>(sy);
     m.acc_out[3 * p + 2] = static_cast<float>(sz);
-    if (m.pot_out) m.pot_out[p] = static_cast<float>(sp);
+    if constexpr (POT) m.pot_out[p] = static_cast<float>(sp);
   } else {
     m.acc64[4 * p + 0] = sx;
     m.acc64[4 * p + 1] = sy;
@@ -441,7 +444,10 @@ cudaError_t launch_sym(const SymArgs& a, const SymMerge& m, int k, bool guard, i
   if (e != cudaSuccess) return e;
   const int mt = 256;
   const int64_t mb = (m.n + mt - 1) / mt;
-  sym_merge_kernel<<<static_cast<unsigned>(mb), mt, 0, s>>>(m);
+  if (pot)
+    sym_merge_kernel<true><<<static_cast<unsigned>(mb), mt, 0, s>>>(m);
+  else
+    sym_merge_kernel<false><<<static_cast<unsigned>(mb), mt, 0, s>>>(m);
   return cudaGetLastError();
 }
 
