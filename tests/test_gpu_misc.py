@@ -138,3 +138,44 @@ def test_plan_functions_of_the_binding():
     cn.cn_batch_plan_destroy(plan)
     assert cn.cn_status_string(0) and cn.cn_status_string(1) != cn.cn_status_string(0)
     assert isinstance(cn.cn_last_error_message(), str)
+
+
+def test_concurrent_host_threads_on_separate_streams():
+    """Calls from several host threads, each on its own stream (own library
+    workspace): results equal the single-threaded ones bit for bit."""
+    import threading
+
+    cn = lib()
+    torch = torch_cuda()
+    sizes = [3000, 20000, 70000, 131072]
+    data = [dev_tensor(synth.plummer(n, 40 + n)) for n in sizes]
+    eps2 = 1e-3
+    ref = []
+    for d in data:
+        a, _ = cn.cn_force(d, d, eps2)
+        ref.append(a)
+    torch.cuda.synchronize()
+    out = [None] * len(sizes)
+    errors = []
+
+    def work(idx):
+        try:
+            s = torch.cuda.Stream()
+            with torch.cuda.stream(s):
+                for _ in range(3):
+                    a, _ = cn.cn_force(data[idx], data[idx], eps2, stream=s)
+                s.synchronize()
+            out[idx] = a
+        except Exception as e:  # noqa: BLE001 - reported below
+            errors.append(e)
+
+    threads = [threading.Thread(target=work, args=(i,)) for i in range(len(sizes))]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errors, errors
+    torch.cuda.synchronize()
+    assert cn.cn_get_device_status() == 0
+    for a, r in zip(out, ref):
+        assert torch.equal(a, r)
