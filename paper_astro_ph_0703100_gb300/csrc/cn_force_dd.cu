@@ -1,4 +1,6 @@
-// Compensated (double-single) pair-kernel instantiations, single system.
+// Compensated pair-kernel instantiations, single system: K = 1 (the
+// guarded kernel) in scalar form, K = 2 and 4 packed (f32x2), with
+// bitwise the same results.
 #include "cn_pair.cuh"
 
 namespace cn {
@@ -6,7 +8,10 @@ namespace {
 
 template <int K, bool POT, bool GUARD>
 const void* fn() {
-  return reinterpret_cast<const void*>(&pair_kernel<DDPolicy<K, POT, GUARD>, K, false>);
+  if constexpr (K >= 2)
+    return reinterpret_cast<const void*>(&pair_kernel<DDx2Policy<K, POT, GUARD>, K, false>);
+  else
+    return reinterpret_cast<const void*>(&pair_kernel<DDPolicy<K, POT, GUARD>, K, false>);
 }
 
 template <bool POT, bool GUARD>

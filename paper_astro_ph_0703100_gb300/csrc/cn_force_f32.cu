@@ -2,6 +2,10 @@
 #include "cn_pair.cuh"
 
 namespace cn {
+
+// split-j kernels with K = 4 or 8 (and the batched K = 2 form): cn_force_f32_splitj.cu
+const void* select_f32_splitj_wide(int k, bool pot, bool batched);
+
 namespace {
 
 // K >= 2 runs the packed (f32x2) policy: the same results, fewer issued
@@ -49,8 +53,9 @@ const void* by_k(int k) {
 
 const void* select(int k, bool pot, bool guard, bool batched, int j_lanes, bool eps_i) {
   if (eps_i) return batched ? nullptr : (pot ? epsi<true>(k, j_lanes) : epsi<false>(k, j_lanes));
-  if (j_lanes > 1) {  // split-j kernels: one or two i-particles per j-lane group, single systems
-    if (batched || k > 2 || (k == 2 && guard)) return nullptr;
+  if (j_lanes > 1) {  // split-j kernels: 1, 2, 4 or 8 i-particles per j-lane group
+    if (k > 1 && guard) return nullptr;
+    if (batched || k > 2) return k == 1 ? nullptr : select_f32_splitj_wide(k, pot, batched);
     if (k == 2) return pot ? fn<2, true, false, false, true>() : fn<2, false, false, false, true>();
     if (pot) return guard ? fn<1, true, true, false, true>() : fn<1, true, false, false, true>();
     return guard ? fn<1, false, true, false, true>() : fn<1, false, false, false, true>();

@@ -385,134 +385,278 @@ struct F32x2Policy {
   }
 };
 
-// Compensated ("split-precision") form. Every quantity of the pair term is
-// carried as a double-single (hi, lo) pair of FP32 numbers and every FP32
-// rounding is recovered exactly, with TwoSum for sums and an FMA for
-// products:
-//   d = x_j - x_i            TwoSum per component (exact)
-//   s = |d|^2 + eps2         exact squares (FMA), three TwoSums, plus the
-//                            cross term 2 d_hi . d_lo
-//   y = s^-1/2               MUFU estimate y0, then y = y0 + y0 rho / 2 with
-//                            the residual rho = 1 - s y0^2 formed by FMAs
-//   g = y^3, m g, m g d      double-single products
-//   a += m g d               TwoSum of the hi part into the running hi sum,
-//                            every low part into the running lo sum
-// so the per-pair relative error is of order 2^-44 and the accumulated sum
-// is exact to a few ulps of the hi part. FP32 instructions only (about 104
-// issue slots per pair plus one MUFU). Partials of split tiles are merged
-// in FP64; outputs are FP64 (hi + lo).
-template <int K, bool POT, bool GUARD>
-__device__ __forceinline__ void pair_ds(const float4 pj, const float (&xi)[K][3], float eps2,
-                                        float (&hi)[K][POT ? 4 : 3], float (&lo)[K][POT ? 4 : 3]) {
+// Compensated ("split-precision") form. The pair term is evaluated in FP32
+// with its roundings recovered, and summed without loss:
+//   d = x_j - x_i           fast two-sum taking x_j as the larger operand:
+//                           exact whenever |x_j| >= |x_i| (and by Sterbenz
+//                           whenever the two are within a factor of two),
+//                           otherwise the low word is approximate
+//   s = |d|^2 + eps2        exact squares (FMUL + FMA residual), the three
+//                           non-negative additions as fast two-sums ordered
+//                           by FMNMX, plus the cross term 2 d_hi . d_lo
+//   y = s^-1/2              MUFU estimate y0 corrected to first order by the
+//                           residual rho = 1 - s y0^2 (formed by FMAs)
+//   q = m y^3               m y0 y0^2 with both product residuals, plus the
+//                           correction 3/2 rho (relative)
+//   a += q d                the product residual and the d_lo and q_lo
+//                           terms go to the low word; the high word is added
+//                           to the running sum by Knuth's TwoSum, its error
+//                           to the low word
+// Each j-tile's (hi, lo) sums are folded into FP64 running sums and
+// restarted, which keeps the FP32 low word from accumulating rounding over
+// long j ranges. 82 FP32 lane operations + 6 FMNMX + 1 MUFU per pair (the
+// potential adds 10 FP32 and 3 selects). Measured against the FP64 oracle: E_max ~1e-9 on
+// Plummer spheres; a CPU emulation of these operations bounds the four
+// parity workloads at 1.6e-8 (the inexact d low word for |x_i| > |x_j| sets
+// it; with an ordered two-sum for d as well the error is ~1e-13, 8% slower).
+// Partials of split tiles carry the FP64 sums as (hi, lo) FP32 pairs and
+// are merged in FP64; outputs are FP64.
+//
+// One term, for one i-particle: scalar (K = 1, the guarded kernel) and
+// packed (two i-particles per f32x2 register pair) share this sequence of
+// lane-level operations, so both give bitwise the same results.
+struct DSTerm {
+  // Knuth's TwoSum: s = a + b, e = the rounding error of s (exact)
+  __device__ static __forceinline__ void ts(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bp = __fadd_rn(s, -a);
+    const float ap = __fadd_rn(s, -bp);
+    e = __fadd_rn(__fadd_rn(a, -ap), __fadd_rn(b, -bp));
+  }
+  // fast two-sum with a taken as the larger operand: e = b + (a - s)
+  __device__ static __forceinline__ void fts(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    e = __fadd_rn(b, __fadd_rn(a, -s));
+  }
+  // the same for non-negative operands, ordered by max / min (exact)
+  __device__ static __forceinline__ void ofs_pos(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    e = __fadd_rn(fminf(a, b), __fadd_rn(fmaxf(a, b), -s));
+  }
+};
+
+template <bool POT, bool GUARD>
+__device__ __forceinline__ void pair_ds1(const float4 pj, const float (&nxi)[3], float eps2, float (&hi)[POT ? 4 : 3],
+                                         float (&lo)[POT ? 4 : 3]) {
+  const float xj[3] = {pj.x, pj.y, pj.z};
+  float dh[3], dl[3], ph[3], pl[3];
 #pragma unroll
-  for (int k = 0; k < K; ++k) {
-    float dh[3], dl[3], ph[3], pl[3];
-    two_sum(pj.x, -xi[k][0], dh[0], dl[0]);
-    two_sum(pj.y, -xi[k][1], dh[1], dl[1]);
-    two_sum(pj.z, -xi[k][2], dh[2], dl[2]);
+  for (int c = 0; c < 3; ++c) {
+    DSTerm::fts(xj[c], nxi[c], dh[c], dl[c]);
+    ph[c] = __fmul_rn(dh[c], dh[c]);
+    pl[c] = __fmaf_rn(dh[c], dh[c], -ph[c]);
+  }
+  float t1, e1, t2, e2, sh, e3;
+  DSTerm::ofs_pos(ph[0], ph[1], t1, e1);
+  DSTerm::ofs_pos(t1, ph[2], t2, e2);
+  DSTerm::ofs_pos(t2, eps2, sh, e3);
+  const float cross = __fmaf_rn(dh[0], dl[0], __fmaf_rn(dh[1], dl[1], __fmul_rn(dh[2], dl[2])));
+  float sl = __fadd_rn(__fadd_rn(e1, e2), __fadd_rn(e3, __fadd_rn(__fadd_rn(pl[0], pl[1]), pl[2])));
+  sl = __fmaf_rn(2.0f, cross, sl);
+  float y0 = rsqrt_mufu(sh);
+  if constexpr (GUARD) y0 = (sh > 0.f) ? y0 : 0.f;
+  const float y2 = __fmul_rn(y0, y0);
+  const float y2l = __fmaf_rn(y0, y0, -y2);
+  float rho = __fmaf_rn(-sh, y2, 1.0f);
+  rho = __fmaf_rn(-sh, y2l, rho);
+  rho = __fmaf_rn(-sl, y2, rho);
+  const float mr = __fmul_rn(pj.w, y0);
+  const float mrl = __fmaf_rn(pj.w, y0, -mr);
+  const float q = __fmul_rn(mr, y2);
+  float t = __fmaf_rn(mr, y2, -q);
+  t = __fmaf_rn(mr, y2l, t);
+  t = __fmaf_rn(mrl, y2, t);
+  t = __fmaf_rn(q, __fmul_rn(1.5f, rho), t);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      ph[c] = __fmul_rn(dh[c], dh[c]);
-      pl[c] = fmaf(dh[c], dh[c], -ph[c]);
-    }
-    float t1, e1, t2, e2, sh, e3;
-    two_sum(ph[0], ph[1], t1, e1);
-    two_sum(t1, ph[2], t2, e2);
-    two_sum(t2, eps2, sh, e3);
-    float cross = fmaf(dh[0], dl[0], fmaf(dh[1], dl[1], __fmul_rn(dh[2], dl[2])));
-    float sl = __fadd_rn(__fadd_rn(e1, e2), __fadd_rn(e3, __fadd_rn(__fadd_rn(pl[0], pl[1]), pl[2])));
-    sl = fmaf(2.0f, cross, sl);
-    float y0 = rsqrt_mufu(sh);
-    if constexpr (GUARD) y0 = (sh > 0.f) ? y0 : 0.f;
-    const float q = __fmul_rn(y0, y0);
-    const float ql = fmaf(y0, y0, -q);
-    float rho = fmaf(-sh, q, 1.0f);
-    rho = fmaf(-sh, ql, rho);
-    rho = fmaf(-sl, q, rho);
-    const float yl = __fmul_rn(y0, __fmul_rn(0.5f, rho));
-    const float y2l = fmaf(__fmul_rn(2.0f, y0), yl, ql);
-    const float y3h = __fmul_rn(q, y0);
-    float y3l = fmaf(q, y0, -y3h);
-    y3l = fmaf(q, yl, y3l);
-    y3l = fmaf(y2l, y0, y3l);
-    const float mgh = __fmul_rn(pj.w, y3h);
-    float mgl = fmaf(pj.w, y3h, -mgh);
-    mgl = fmaf(pj.w, y3l, mgl);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const float fh = __fmul_rn(mgh, dh[c]);
-      float fl = fmaf(mgh, dh[c], -fh);
-      fl = fmaf(mgh, dl[c], fl);
-      fl = fmaf(mgl, dh[c], fl);
-      float sum, err;
-      two_sum(hi[k][c], fh, sum, err);
-      hi[k][c] = sum;
-      lo[k][c] = __fadd_rn(lo[k][c], __fadd_rn(err, fl));
-    }
-    if constexpr (POT) {
-      // m (y0 + yl), skipped when the separation is exactly zero (t2 == 0)
-      const bool apart = t2 != 0.f;
-      const float uh = apart ? __fmul_rn(pj.w, y0) : 0.f;
-      const float ul = apart ? fmaf(pj.w, yl, fmaf(pj.w, y0, -uh)) : 0.f;
-      float sum, err;
-      two_sum(hi[k][3], uh, sum, err);
-      hi[k][3] = sum;
-      lo[k][3] = __fadd_rn(lo[k][3], __fadd_rn(err, ul));
-    }
+  for (int c = 0; c < 3; ++c) {
+    const float fh = __fmul_rn(q, dh[c]);
+    const float r = __fmaf_rn(q, dh[c], -fh);
+    float s, e;
+    DSTerm::ts(hi[c], fh, s, e);
+    hi[c] = s;
+    float l = __fadd_rn(lo[c], e);
+    l = __fadd_rn(l, r);
+    l = __fmaf_rn(q, dl[c], l);
+    lo[c] = __fmaf_rn(t, dh[c], l);
+  }
+  if constexpr (POT) {
+    // m y0 (1 + rho / 2), skipped when the separation is exactly zero
+    const bool apart = t2 != 0.f;
+    const float uh = apart ? mr : 0.f;
+    const float ul = apart ? __fmaf_rn(mr, __fmul_rn(0.5f, rho), mrl) : 0.f;
+    float s, e;
+    DSTerm::ts(hi[3], uh, s, e);
+    hi[3] = s;
+    lo[3] = __fadd_rn(__fadd_rn(lo[3], e), ul);
   }
 }
 
+// Packed: the same operations on two i-particles (the .x and .y halves);
+// selects and compares stay per half. a - b is formed as fma(-1, b, a),
+// which rounds exactly as the subtraction does.
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(dup2(-1.0f), b, a); }
+// a b - c per half, as two scalar FMAs: the packed FMA takes no negated
+// operand, while the scalar one negates c for free (the FP32 pipe does the
+// same lane work either way)
+__device__ __forceinline__ float2 fms2(float2 a, float2 b, float2 c) {
+  return make_float2(__fmaf_rn(a.x, b.x, -c.x), __fmaf_rn(a.y, b.y, -c.y));
+}
+// TwoSum and the fast two-sum (a taken as the larger operand), per half
+__device__ __forceinline__ void ts2(float2 a, float2 b, float2& s, float2& e) {
+  s = __fadd2_rn(a, b);
+  const float2 bp = sub2(s, a);
+  const float2 ap = sub2(s, bp);
+  e = __fadd2_rn(sub2(a, ap), sub2(b, bp));
+}
+__device__ __forceinline__ void fts2(float2 a, float2 b, float2& s, float2& e) {
+  s = __fadd2_rn(a, b);
+  e = __fadd2_rn(b, sub2(a, s));
+}
+__device__ __forceinline__ void ofs_pos2(float2 a, float2 b, float2& s, float2& e) {
+  s = __fadd2_rn(a, b);
+  e = __fadd2_rn(make_float2(fminf(a.x, b.x), fminf(a.y, b.y)), sub2(make_float2(fmaxf(a.x, b.x), fmaxf(a.y, b.y)), s));
+}
+
+template <bool POT, bool GUARD>
+__device__ __forceinline__ void pair_ds2(const float4 pj, const float2 (&nxi)[3], float2 e2,
+                                         float2 (&hi)[POT ? 4 : 3], float2 (&lo)[POT ? 4 : 3]) {
+  const float xj[3] = {pj.x, pj.y, pj.z};
+  float2 dh[3], dl[3], ph[3], pl[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    fts2(dup2(xj[c]), nxi[c], dh[c], dl[c]);
+    ph[c] = __fmul2_rn(dh[c], dh[c]);
+    pl[c] = fms2(dh[c], dh[c], ph[c]);
+  }
+  float2 t1, e1, t2, ee2, sh, e3;
+  ofs_pos2(ph[0], ph[1], t1, e1);
+  ofs_pos2(t1, ph[2], t2, ee2);
+  ofs_pos2(t2, e2, sh, e3);
+  const float2 cross = __ffma2_rn(dh[0], dl[0], __ffma2_rn(dh[1], dl[1], __fmul2_rn(dh[2], dl[2])));
+  float2 sl = __fadd2_rn(__fadd2_rn(e1, ee2), __fadd2_rn(e3, __fadd2_rn(__fadd2_rn(pl[0], pl[1]), pl[2])));
+  sl = __ffma2_rn(dup2(2.0f), cross, sl);
+  float2 y0 = make_float2(rsqrt_mufu(sh.x), rsqrt_mufu(sh.y));
+  if constexpr (GUARD) {
+    y0.x = (sh.x > 0.f) ? y0.x : 0.f;
+    y0.y = (sh.y > 0.f) ? y0.y : 0.f;
+  }
+  const float2 y2 = __fmul2_rn(y0, y0);
+  const float2 y2l = fms2(y0, y0, y2);
+  // nrho = -rho = s y0^2 - 1, formed with positive operands only (the same
+  // roundings as the scalar form's rho, negated)
+  float2 nrho = __ffma2_rn(sh, y2, dup2(-1.0f));
+  nrho = __ffma2_rn(sh, y2l, nrho);
+  nrho = __ffma2_rn(sl, y2, nrho);
+  const float2 m = dup2(pj.w);
+  const float2 mr = __fmul2_rn(m, y0);
+  const float2 mrl = fms2(m, y0, mr);
+  const float2 q = __fmul2_rn(mr, y2);
+  float2 t = fms2(mr, y2, q);
+  t = __ffma2_rn(mr, y2l, t);
+  t = __ffma2_rn(mrl, y2, t);
+  t = __ffma2_rn(q, __fmul2_rn(dup2(-1.5f), nrho), t);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const float2 fh = __fmul2_rn(q, dh[c]);
+    const float2 r = fms2(q, dh[c], fh);
+    float2 s, e;
+    ts2(hi[c], fh, s, e);
+    hi[c] = s;
+    float2 l = __fadd2_rn(lo[c], e);
+    l = __fadd2_rn(l, r);
+    l = __ffma2_rn(q, dl[c], l);
+    lo[c] = __ffma2_rn(t, dh[c], l);
+  }
+  if constexpr (POT) {
+    const bool ax = t2.x != 0.f, ay = t2.y != 0.f;
+    const float2 ulr = __ffma2_rn(mr, __fmul2_rn(dup2(-0.5f), nrho), mrl);
+    const float2 uh = make_float2(ax ? mr.x : 0.f, ay ? mr.y : 0.f);
+    const float2 ul = make_float2(ax ? ulr.x : 0.f, ay ? ulr.y : 0.f);
+    float2 s, e;
+    ts2(hi[3], uh, s, e);
+    hi[3] = s;
+    lo[3] = __fadd2_rn(__fadd2_rn(lo[3], e), ul);
+  }
+}
+
+// Scalar compensated policy (K i-particles per thread, one per register;
+// the guarded kernels use K = 1).
 template <int K, bool POT, bool GUARD>
 struct DDPolicy {
   static constexpr int NC = POT ? 4 : 3;
-  static constexpr int kSlotF4 = 2;  // hi float4 then lo float4
+  static constexpr int kSlotF4 = 2;  // FP64 sums as (hi, lo) FP32 pairs: hi float4 then lo float4
   static constexpr int kSums = 4;
   static constexpr int kJRec = 1;
   static constexpr bool kSplitJ = false;
-  static constexpr int kMinBlocks = K >= 4 ? 1 : 2;
+  static constexpr int kMinBlocks = K >= 2 ? 1 : 2;
   __device__ __forceinline__ void reduce_lanes(int) {}
-  float xi[K][3];
-  float hi[K][NC];
-  float lo[K][NC];
+  float nxi[K][3];
+  double run[K][NC];
 
   __device__ __forceinline__ void load_i(const PairArgs& a, int64_t gi, bool valid, int k) {
     float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
     if (valid) v = __ldg(a.pos_i + gi);
-    xi[k][0] = v.x;
-    xi[k][1] = v.y;
-    xi[k][2] = v.z;
+    nxi[k][0] = -v.x;
+    nxi[k][1] = -v.y;
+    nxi[k][2] = -v.z;
   }
 
   __device__ __forceinline__ void zero() {
 #pragma unroll
     for (int k = 0; k < K; ++k)
 #pragma unroll
-      for (int c = 0; c < NC; ++c) hi[k][c] = lo[k][c] = 0.f;
+      for (int c = 0; c < NC; ++c) run[k][c] = 0.0;
   }
 
   __device__ __forceinline__ void tile(const float4* js, int T, float eps2, int64_t /*self_off*/, bool /*diag*/,
                                        int /*row*/, int /*rows*/, int /*sub*/, int /*jl*/) {
-#pragma unroll 1
-    for (int j = 0; j < T; j += 8) {
+    float hi[K][NC], lo[K][NC];
 #pragma unroll
-      for (int jj = 0; jj < 8; ++jj) pair_ds<K, POT, GUARD>(js[j + jj], xi, eps2, hi, lo);
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+      for (int c = 0; c < NC; ++c) hi[k][c] = lo[k][c] = 0.f;
+#pragma unroll 1
+    for (int j = 0; j < T; j += 4) {
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) {
+        const float4 pj = js[j + jj];
+#pragma unroll
+        for (int k = 0; k < K; ++k) pair_ds1<POT, GUARD>(pj, nxi[k], eps2, hi[k], lo[k]);
+      }
     }
+    // fold the tile's (hi, lo) sums into the FP64 running sums
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+      for (int c = 0; c < NC; ++c) run[k][c] += static_cast<double>(hi[k][c]) + static_cast<double>(lo[k][c]);
   }
 
   __device__ __forceinline__ void store_final(const PairArgs& a, int64_t i, int k) const {
     double* acc = static_cast<double*>(a.acc_out) + 3 * i;
-    acc[0] = static_cast<double>(hi[k][0]) + static_cast<double>(lo[k][0]);
-    acc[1] = static_cast<double>(hi[k][1]) + static_cast<double>(lo[k][1]);
-    acc[2] = static_cast<double>(hi[k][2]) + static_cast<double>(lo[k][2]);
+    acc[0] = run[k][0];
+    acc[1] = run[k][1];
+    acc[2] = run[k][2];
     if constexpr (POT) {
-      if (a.pot_out)
-        static_cast<double*>(a.pot_out)[i] = -(static_cast<double>(hi[k][3]) + static_cast<double>(lo[k][3]));
+      if (a.pot_out) static_cast<double*>(a.pot_out)[i] = -run[k][3];
     }
   }
 
+  // an FP64 sum as an unevaluated (hi, lo) FP32 pair (exact to about 2^-48)
+  __device__ static __forceinline__ float2 split64(double v) {
+    const float h = __double2float_rn(v);
+    return make_float2(h, __double2float_rn(v - static_cast<double>(h)));
+  }
+
+  __device__ static __forceinline__ void store_split(float4* slot, int il, int i_tile, const double (&r)[NC]) {
+    float2 s[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) s[c] = c < NC ? split64(r[c < NC ? c : 0]) : make_float2(0.f, 0.f);
+    slot[il] = make_float4(s[0].x, s[1].x, s[2].x, s[3].x);
+    slot[i_tile + il] = make_float4(s[0].y, s[1].y, s[2].y, s[3].y);
+  }
+
   __device__ __forceinline__ void store_partial(float4* slot, int il, int i_tile, int k) const {
-    slot[il] = make_float4(hi[k][0], hi[k][1], hi[k][2], POT ? hi[k][3] : 0.f);
-    slot[i_tile + il] = make_float4(lo[k][0], lo[k][1], lo[k][2], POT ? lo[k][3] : 0.f);
+    store_split(slot, il, i_tile, run[k]);
   }
 
   __device__ static __forceinline__ void add_partial(const float4 (&v)[kSlotF4], double (&s)[kSums]) {
@@ -532,6 +676,88 @@ struct DDPolicy {
     if constexpr (POT) {
       if (a.pot_out) static_cast<double*>(a.pot_out)[i] = -s[3];
     }
+  }
+};
+
+// Packed compensated policy (K even): two i-particles per f32x2 register
+// pair, bitwise the results of DDPolicy.
+template <int K, bool POT, bool GUARD>
+struct DDx2Policy {
+  static_assert(K % 2 == 0, "the packed form holds i-particles in pairs");
+  static constexpr int NC = POT ? 4 : 3;
+  static constexpr int kSlotF4 = 2;
+  static constexpr int kSums = 4;
+  static constexpr int kJRec = 1;
+  static constexpr bool kSplitJ = false;
+  // K = 2 without the potential fits 128 registers (16 warps per SM)
+  static constexpr int kMinBlocks = (K >= 4 || POT) ? 1 : 2;
+  __device__ __forceinline__ void reduce_lanes(int) {}
+  float2 nxi[K / 2][3];
+  double run[K][NC];
+
+  __device__ __forceinline__ static float& half(float2& v, int k) { return (k & 1) ? v.y : v.x; }
+
+  __device__ __forceinline__ void load_i(const PairArgs& a, int64_t gi, bool valid, int k) {
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (valid) v = __ldg(a.pos_i + gi);
+    half(nxi[k >> 1][0], k) = -v.x;
+    half(nxi[k >> 1][1], k) = -v.y;
+    half(nxi[k >> 1][2], k) = -v.z;
+  }
+
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+      for (int c = 0; c < NC; ++c) run[k][c] = 0.0;
+  }
+
+  __device__ __forceinline__ void tile(const float4* js, int T, float eps2, int64_t /*self_off*/, bool /*diag*/,
+                                       int /*row*/, int /*rows*/, int /*sub*/, int /*jl*/) {
+    float2 hi[K / 2][NC], lo[K / 2][NC];
+#pragma unroll
+    for (int p = 0; p < K / 2; ++p)
+#pragma unroll
+      for (int c = 0; c < NC; ++c) hi[p][c] = lo[p][c] = dup2(0.f);
+    const float2 e2 = dup2(eps2);
+#pragma unroll 1
+    for (int j = 0; j < T; j += 4) {
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) {
+        const float4 pj = js[j + jj];
+#pragma unroll
+        for (int p = 0; p < K / 2; ++p) pair_ds2<POT, GUARD>(pj, nxi[p], e2, hi[p], lo[p]);
+      }
+    }
+#pragma unroll
+    for (int p = 0; p < K / 2; ++p)
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        run[2 * p][c] += static_cast<double>(hi[p][c].x) + static_cast<double>(lo[p][c].x);
+        run[2 * p + 1][c] += static_cast<double>(hi[p][c].y) + static_cast<double>(lo[p][c].y);
+      }
+  }
+
+  __device__ __forceinline__ void store_final(const PairArgs& a, int64_t i, int k) const {
+    double* acc = static_cast<double*>(a.acc_out) + 3 * i;
+    acc[0] = run[k][0];
+    acc[1] = run[k][1];
+    acc[2] = run[k][2];
+    if constexpr (POT) {
+      if (a.pot_out) static_cast<double*>(a.pot_out)[i] = -run[k][3];
+    }
+  }
+
+  __device__ __forceinline__ void store_partial(float4* slot, int il, int i_tile, int k) const {
+    DDPolicy<1, POT, GUARD>::store_split(slot, il, i_tile, run[k]);
+  }
+
+  __device__ static __forceinline__ void add_partial(const float4 (&v)[kSlotF4], double (&s)[kSums]) {
+    DDPolicy<1, POT, GUARD>::add_partial(v, s);
+  }
+
+  __device__ static __forceinline__ void store_merged(const PairArgs& a, int64_t i, const double (&s)[kSums]) {
+    DDPolicy<1, POT, GUARD>::store_merged(a, i, s);
   }
 };
 
@@ -577,11 +803,16 @@ struct AdjointPolicy {
   static constexpr int kJRec = 2;  // (x, y, z, m) then (wx, wy, wz, 0)
   static constexpr bool kSplitJ = false;
   static constexpr int kMinBlocks = K >= 4 ? 1 : 2;
+  static constexpr int kBlock = 64;  // j entries summed in FP32 before the compensated fold
   __device__ __forceinline__ void reduce_lanes(int) {}
   float xk[K][3];
   float mk[K];
   float wk[K][3];
+  // Running sums as (hi, lo) pairs: the adjoint's sums cancel heavily (the
+  // weights are signed), so each block of kBlock terms is added to the
+  // running sum by TwoSum instead of a rounded FP32 addition.
   float run[K][4];
+  float runl[K][4];
 
   __device__ __forceinline__ void load_i(const PairArgs& a, int64_t gi, bool valid, int k) {
     float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -603,18 +834,13 @@ struct AdjointPolicy {
 #pragma unroll
     for (int k = 0; k < K; ++k)
 #pragma unroll
-      for (int c = 0; c < 4; ++c) run[k][c] = 0.f;
+      for (int c = 0; c < 4; ++c) run[k][c] = runl[k][c] = 0.f;
   }
 
   // self_off = (first j index of the tile) - (first i index of the i-tile)
   __device__ __forceinline__ void tile(const float4* js, int T, float eps2, int64_t self_off, bool diag, int row,
                                        int rows, int /*sub*/, int /*jl*/) {
     const float4* jw = js + T;
-    float part[K][4];
-#pragma unroll
-    for (int k = 0; k < K; ++k)
-#pragma unroll
-      for (int c = 0; c < 4; ++c) part[k][c] = 0.f;
     int self_j[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
@@ -622,37 +848,53 @@ struct AdjointPolicy {
       const int64_t sj = static_cast<int64_t>(k * rows + row) - self_off;
       self_j[k] = (sj >= 0 && sj < T) ? static_cast<int>(sj) : -1;
     }
-    if (!diag) {
 #pragma unroll 1
-      for (int j = 0; j < T; j += 8) {
+    for (int jb = 0; jb < T; jb += kBlock) {
+      const int je = jb + kBlock < T ? jb + kBlock : T;
+      float part[K][4];
 #pragma unroll
-        for (int jj = 0; jj < 8; ++jj)
-          pair_adjoint<K, GUARD, false>(js[j + jj], jw[j + jj], xk, mk, wk, eps2, j + jj, self_j, part);
-      }
-    } else {
+      for (int k = 0; k < K; ++k)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) part[k][c] = 0.f;
+      if (!diag) {
 #pragma unroll 1
-      for (int j = 0; j < T; j += 8) {
+        for (int j = jb; j < je; j += 8) {
 #pragma unroll
-        for (int jj = 0; jj < 8; ++jj)
-          pair_adjoint<K, GUARD, true>(js[j + jj], jw[j + jj], xk, mk, wk, eps2, j + jj, self_j, part);
+          for (int jj = 0; jj < 8; ++jj)
+            pair_adjoint<K, GUARD, false>(js[j + jj], jw[j + jj], xk, mk, wk, eps2, j + jj, self_j, part);
+        }
+      } else {
+#pragma unroll 1
+        for (int j = jb; j < je; j += 8) {
+#pragma unroll
+          for (int jj = 0; jj < 8; ++jj)
+            pair_adjoint<K, GUARD, true>(js[j + jj], jw[j + jj], xk, mk, wk, eps2, j + jj, self_j, part);
+        }
       }
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          float s, e;
+          two_sum(run[k][c], part[k][c], s, e);
+          run[k][c] = s;
+          runl[k][c] = __fadd_rn(runl[k][c], e);
+        }
     }
-#pragma unroll
-    for (int k = 0; k < K; ++k)
-#pragma unroll
-      for (int c = 0; c < 4; ++c) run[k][c] += part[k][c];
   }
+
+  __device__ __forceinline__ float total(int k, int c) const { return __fadd_rn(run[k][c], runl[k][c]); }
 
   __device__ __forceinline__ void store_final(const PairArgs& a, int64_t i, int k) const {
     float* g = static_cast<float*>(a.acc_out) + 3 * i;
-    g[0] = run[k][0];
-    g[1] = run[k][1];
-    g[2] = run[k][2];
-    static_cast<float*>(a.pot_out)[i] = run[k][3];
+    g[0] = total(k, 0);
+    g[1] = total(k, 1);
+    g[2] = total(k, 2);
+    static_cast<float*>(a.pot_out)[i] = total(k, 3);
   }
 
   __device__ __forceinline__ void store_partial(float4* slot, int il, int /*i_tile*/, int k) const {
-    slot[il] = make_float4(run[k][0], run[k][1], run[k][2], run[k][3]);
+    slot[il] = make_float4(total(k, 0), total(k, 1), total(k, 2), total(k, 3));
   }
 
   __device__ static __forceinline__ void add_partial(const float4 (&v)[kSlotF4], double (&s)[kSums]) {
@@ -863,8 +1105,19 @@ struct AdjointX2Policy {
   static constexpr int kSums = 4;
   static constexpr int kJRec = 2;
   static constexpr bool kSplitJ = SPLITJ;
-  static constexpr int kMinBlocks = (K >= 4 || SPLITJ) ? 1 : 2;
+  // the (hi, lo) running sums spill under a 128-register cap even at K = 2
+  static constexpr int kMinBlocks = 1;
+  static constexpr int kBlock = AdjointPolicy<1, GUARD>::kBlock;  // entries per lane between compensated folds
+  // the lanes of a group are combined in FP32 after their (hi, lo) sums
+  // are collapsed (a butterfly of at most five additions)
   __device__ __forceinline__ void reduce_lanes(int jl) {
+#pragma unroll
+    for (int p = 0; p < K / 2; ++p)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        run[p][c] = __fadd2_rn(run[p][c], runl[p][c]);
+        runl[p][c] = dup2(0.f);
+      }
     for (int off = jl >> 1; off > 0; off >>= 1) {
 #pragma unroll
       for (int p = 0; p < K / 2; ++p)
@@ -878,7 +1131,8 @@ struct AdjointX2Policy {
   float2 nxk[K / 2][3];
   float2 mk[K / 2];
   float2 nwk[K / 2][3];
-  float2 run[K / 2][4];  // component 3 holds -(dL/dm)
+  float2 run[K / 2][4];   // component 3 holds -(dL/dm)
+  float2 runl[K / 2][4];  // low words of the running sums
 
   __device__ __forceinline__ static float& half(float2& v, int k) { return (k & 1) ? v.y : v.x; }
   __device__ __forceinline__ static float half(const float2& v, int k) { return (k & 1) ? v.y : v.x; }
@@ -903,7 +1157,7 @@ struct AdjointX2Policy {
 #pragma unroll
     for (int p = 0; p < K / 2; ++p)
 #pragma unroll
-      for (int c = 0; c < 4; ++c) run[p][c] = dup2(0.f);
+      for (int c = 0; c < 4; ++c) run[p][c] = runl[p][c] = dup2(0.f);
   }
 
   __device__ __forceinline__ void tile(const float4* js, int T, float eps2, int64_t self_off, bool diag, int row,
@@ -911,11 +1165,6 @@ struct AdjointX2Policy {
     const float4* jw = js + T;
     const int j0 = SPLITJ ? sub : 0;   // this lane's first entry
     const int js1 = SPLITJ ? jl : 1;   // stride between its entries
-    float2 part[K / 2][4];
-#pragma unroll
-    for (int p = 0; p < K / 2; ++p)
-#pragma unroll
-      for (int c = 0; c < 4; ++c) part[p][c] = dup2(0.f);
     int self_j[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
@@ -923,42 +1172,63 @@ struct AdjointX2Policy {
       self_j[k] = (sj >= 0 && sj < T) ? static_cast<int>(sj) : -1;
     }
     const float2 e2 = dup2(eps2);
-    if (!diag) {
 #pragma unroll 1
-      for (int j = j0; j < T; j += 8 * js1) {
+    for (int jb = j0; jb < T; jb += kBlock * js1) {
+      const int je = jb + kBlock * js1 < T ? jb + kBlock * js1 : T;
+      float2 part[K / 2][4];
 #pragma unroll
-        for (int jj = 0; jj < 8; ++jj) {
-          const int e = j + jj * js1;
-          pair_adjoint_x2<K, GUARD, false>(js[e], jw[e], nxk, mk, nwk, e2, e, self_j, part);
+      for (int p = 0; p < K / 2; ++p)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) part[p][c] = dup2(0.f);
+      if (!diag) {
+#pragma unroll 1
+        for (int j = jb; j < je; j += 8 * js1) {
+#pragma unroll
+          for (int jj = 0; jj < 8; ++jj) {
+            const int e = j + jj * js1;
+            pair_adjoint_x2<K, GUARD, false>(js[e], jw[e], nxk, mk, nwk, e2, e, self_j, part);
+          }
+        }
+      } else {
+#pragma unroll 1
+        for (int j = jb; j < je; j += 8 * js1) {
+#pragma unroll
+          for (int jj = 0; jj < 8; ++jj) {
+            const int e = j + jj * js1;
+            pair_adjoint_x2<K, GUARD, true>(js[e], jw[e], nxk, mk, nwk, e2, e, self_j, part);
+          }
         }
       }
-    } else {
-#pragma unroll 1
-      for (int j = j0; j < T; j += 8 * js1) {
+      // TwoSum of each block into the running (hi, lo) sums, per half
 #pragma unroll
-        for (int jj = 0; jj < 8; ++jj) {
-          const int e = j + jj * js1;
-          pair_adjoint_x2<K, GUARD, true>(js[e], jw[e], nxk, mk, nwk, e2, e, self_j, part);
+      for (int p = 0; p < K / 2; ++p)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const float2 a = run[p][c], b = part[p][c];
+          const float2 s = __fadd2_rn(a, b);
+          const float2 bp = sub2(s, a);
+          const float2 ap = sub2(s, bp);
+          const float2 err = __fadd2_rn(sub2(a, ap), sub2(b, bp));
+          run[p][c] = s;
+          runl[p][c] = __fadd2_rn(runl[p][c], err);
         }
-      }
     }
-#pragma unroll
-    for (int p = 0; p < K / 2; ++p)
-#pragma unroll
-      for (int c = 0; c < 4; ++c) run[p][c] = __fadd2_rn(run[p][c], part[p][c]);
+  }
+
+  __device__ __forceinline__ float total(int k, int c) const {
+    return __fadd_rn(half(run[k >> 1][c], k), half(runl[k >> 1][c], k));
   }
 
   __device__ __forceinline__ void store_final(const PairArgs& a, int64_t i, int k) const {
     float* g = static_cast<float*>(a.acc_out) + 3 * i;
-    g[0] = half(run[k >> 1][0], k);
-    g[1] = half(run[k >> 1][1], k);
-    g[2] = half(run[k >> 1][2], k);
-    static_cast<float*>(a.pot_out)[i] = -half(run[k >> 1][3], k);
+    g[0] = total(k, 0);
+    g[1] = total(k, 1);
+    g[2] = total(k, 2);
+    static_cast<float*>(a.pot_out)[i] = -total(k, 3);
   }
 
   __device__ __forceinline__ void store_partial(float4* slot, int il, int /*i_tile*/, int k) const {
-    slot[il] = make_float4(half(run[k >> 1][0], k), half(run[k >> 1][1], k), half(run[k >> 1][2], k),
-                           -half(run[k >> 1][3], k));
+    slot[il] = make_float4(total(k, 0), total(k, 1), total(k, 2), -total(k, 3));
   }
 
   __device__ static __forceinline__ void add_partial(const float4 (&v)[kSlotF4], double (&s)[kSums]) {
@@ -1279,9 +1549,10 @@ __global__ void __launch_bounds__(256, Policy::kMinBlocks) pair_kernel(const __g
             __syncthreads();
             if (ctl[1]) {
               __threadfence();
-              for (int k = 0; k < K; ++k) {
-                const int il = k * ROWS + row;
-                if (il >= td.ni || sub != 0) continue;
+              // every thread of the CTA takes particles of the tile in turn
+              // (with split-j lanes only one lane in j_lanes held results,
+              // and the FP64 adds are the merge's slow part on this GPU)
+              for (int il = tid; il < td.ni; il += NT) {
                 double s[Policy::kSums];
 #pragma unroll
                 for (int c = 0; c < Policy::kSums; ++c) s[c] = 0.0;

@@ -2,10 +2,20 @@
 
 The CUDA gradient is checked against the oracle's analytic FP64 gradient
 and against FP64 central finite differences of L (Richardson-extrapolated)
-on a seeded subset. Tolerance: FP32 pair arithmetic with cancellation
-between the two halves of u = m_k w_p - m_p w_k; per particle
-|g_gpu - g_ref| / |g_ref| <= 1e-4 for dL/dx and max |dm_gpu - dm_ref| /
-max |dm_ref| <= 1e-5 for dL/dm.
+on a seeded subset.
+
+Tolerances come from a floor study: the kernel's FP32 pair terms (the same
+operation sequence, MUFU inverse square root modelled as a +-2^-22.9
+relative perturbation) summed exactly in FP64 give E_max 5.7e-6 for dL/dx
+on 1024 rows of the N = 65536 workload (2.9e-6 with an exact inverse square
+root), and 1.5e-7 (of max |dL/dm|) for dL/dm. The sums cancel heavily (the
+weights are signed), so the kernel adds its terms in FP32 blocks of 64 and
+folds each block into (hi, lo) running sums by TwoSum, which keeps the
+result at that floor: measured on the GPU, at most 5.4e-6 (dL/dx) and
+3.1e-7 (dL/dm) over the configurations below. The bounds are about three
+times the floor / the largest measurement:
+  dL/dx   per particle |g_gpu - g_ref| / |g_ref|        <= 1.5e-5
+  dL/dm   max |dm_gpu - dm_ref| / max |dm_ref|          <= 1e-6
 """
 
 import numpy as np
@@ -17,8 +27,8 @@ from paper_astro_ph_0703100_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
-TOL_POS = 1e-4
-TOL_MASS = 1e-5
+TOL_POS = 1.5e-5
+TOL_MASS = 1e-6
 
 
 def gpu_adjoint(cn, p, w, eps2):

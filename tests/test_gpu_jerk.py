@@ -1,9 +1,14 @@
 """Parity of cn_force_jerk (acceleration, jerk, potential) with the FP64 oracle.
 
 Tolerances per particle (relative to the oracle's vector norm): acceleration
-and potential 1e-5 as for the plain FP32 form; jerk 1e-4, since its pair term
-w - 3 (d . w) d / s is a difference of two FP32 products whose cancellation
-amplifies the FP32 rounding (measured ~1e-6 .. 1e-5).
+and potential 1e-5 as for the plain FP32 form (measured at most 1.5e-6 and
+8.2e-7 here); jerk 2e-5. The jerk's pair term w - 3 (d . w) d / s is a
+difference of two FP32 products, and a floor study (the kernel's FP32 pair
+terms, MUFU modelled as a +-2^-22.9 perturbation, summed exactly in FP64)
+gives E_max 3.1e-6 on 512 rows of the N = 131072 workload (1.3e-6 with an
+exact inverse square root); the kernel's FP32 per-tile accumulation brings
+the GPU to at most 6.1e-6 over the configurations below. The bound is about
+three times that measurement.
 """
 
 import numpy as np
@@ -16,7 +21,7 @@ from paper_astro_ph_0703100_gb300 import synth
 pytestmark = pytest.mark.gpu
 
 TOL_ACC = 1e-5
-TOL_JERK = 1e-4
+TOL_JERK = 2e-5
 
 
 def run(cn, pi, vi, pj, vj, eps2, potential=True):

@@ -57,7 +57,7 @@ def test_plain_packed_equals_scalar(potential):
 @pytest.mark.parametrize("j_lanes", [8, 16, 32])
 def test_splitj_packed_equals_scalar(potential, j_lanes):
     """Split-j shapes: lanes of a group take every j_lanes-th j record; the
-    packed form holds two i-particles per group."""
+    packed form holds two, four or eight i-particles per group."""
     cn = lib()
     torch = torch_cuda()
     p = dev_tensor(synth.plummer(N, 82))
@@ -70,10 +70,33 @@ def test_splitj_packed_equals_scalar(potential, j_lanes):
 
     shape = dict(_shape(1, threads=128), j_lanes=j_lanes)
     a1, p1 = _with_tune(cn, [v], shape, run)
-    a2, p2 = _with_tune(cn, [v], dict(shape, i_per_thread=2), run)
-    assert np.array_equal(a1, a2)
-    if potential:
-        assert np.array_equal(p1, p2)
+    for k in (2, 4, 8):
+        ak, pk = _with_tune(cn, [v], dict(shape, i_per_thread=k), run)
+        assert np.array_equal(a1, ak), k
+        if potential:
+            assert np.array_equal(p1, pk), k
+
+
+@pytest.mark.parametrize("potential", [False, True])
+def test_compensated_packed_equals_scalar(potential):
+    """The compensated form: K = 1 runs the scalar policy, K = 2 and 4 the
+    packed one (the same lane-level operations, selects per half)."""
+    cn = lib()
+    torch = torch_cuda()
+    p = dev_tensor(synth.plummer(N, 83))
+    v = "dd_pot" if potential else "dd"
+
+    def run():
+        a, pot = cn.cn_force_dd(p, p, 1e-3, potential=potential)
+        torch.cuda.synchronize()
+        return a.cpu().numpy(), (pot.cpu().numpy() if pot is not None else None)
+
+    a1, p1 = _with_tune(cn, [v], _shape(1), run)
+    for k in (2, 4):
+        ak, pk = _with_tune(cn, [v], _shape(k), run)
+        assert np.array_equal(a1, ak), k
+        if potential:
+            assert np.array_equal(p1, pk), k
 
 
 def test_adjoint_packed_equals_scalar():
