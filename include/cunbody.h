@@ -169,14 +169,19 @@ CN_API size_t cn_workspace_bytes(int variant, int64_t n_i, int64_t n_j);
  * grows a library workspace on demand and cn_force_ws needs a buffer from
  * the caller.
  *   Arguments, results and errors as cn_force; nothing is allocated.
- *   Scratch: a fixed 32 MiB array in the library's device image (every GPU
- *   that loads the library holds it until the process exits). A problem
+ *   Scratch: a fixed 32 MiB array in the library's device image. A problem
  *   whose launch shape needs more scratch than that (see
  *   cn_workspace_bytes) is rejected with CN_ERR_WORKSPACE before anything
  *   runs.
- *   The first call on each device looks up the array's device address (a
- *   one-time set-up with that device current); make that first call before
- *   capturing any stream.
+ *   Set-up: the library's first call of any entry point on a device (this
+ *   one or another) sets that device up, which looks up the array's device
+ *   address and, under CUDA's lazy module loading, loads the library's
+ *   device code there - allocating the 32 MiB, which the GPU then holds
+ *   until the process exits. Likewise the first launch of each kernel in a
+ *   process loads that kernel's code. So make one cn_force call with the
+ *   same sizes (or set CUDA_MODULE_LOADING=EAGER) on each device before the
+ *   region where allocation is not allowed, and before capturing any
+ *   stream; after that this call allocates nothing.
  *   Every call uses the same array: calls that overlap on the GPU (other
  *   streams, other host threads) race and corrupt each other's results, so
  *   serialise them. Each call clears the part that must start at zero.
@@ -379,6 +384,26 @@ CN_API cn_status cn_force_host_f64(const double *xj, const double *mj, const dou
 CN_API cn_status cn_tune_get(int variant, int64_t n_i, int64_t n_j, cn_tune *out);
 /* Stores (tune != NULL) or clears (tune == NULL) the shape for the size class. */
 CN_API cn_status cn_tune_set(int variant, int64_t n_i, int64_t n_j, const cn_tune *tune);
+
+/*
+ * Persisted tuning table (the paper has no counterpart; tuning is this
+ * library's own state). cn_tune_save writes every entry stored for the
+ * current device (by cn_tune_set or the autotuners) to `path` as JSON:
+ *   {"format": "cunbody-tune-1", "device": "<name>", "arch": "sm_103",
+ *    "sms": <multiprocessors>, "entries": [{"variant": "f32", "n_i_class": 17,
+ *    "n_j_class": 17, "i_per_thread": 8, ...}, ...]}
+ * where a size class is ceil(log2 n). Overwrites the file; CN_ERR_INVALID_ARG
+ * if it cannot be written.
+ * cn_tune_load reads such a file and stores its entries for the current
+ * device, replacing entries of the same variant and size classes. The whole
+ * file is parsed and checked first (CN_ERR_INVALID_ARG for a missing or
+ * malformed file or an invalid entry, with nothing stored); a file written
+ * on a device with another name, arch or multiprocessor count is refused
+ * with CN_ERR_UNSUPPORTED_DEVICE. *n_loaded (if not NULL) receives the
+ * number of entries stored. Host-side only; no device work.
+ */
+CN_API cn_status cn_tune_save(const char *path);
+CN_API cn_status cn_tune_load(const char *path, int32_t *n_loaded);
 
 /*
  * Times every candidate launch shape for `variant` on these inputs (CUDA

@@ -14,6 +14,7 @@ softening length.
 from __future__ import annotations
 
 import ctypes
+import os
 
 import numpy as np
 
@@ -53,6 +54,8 @@ __all__ = [
     "cn_force_host_f64",
     "cn_tune_get",
     "cn_tune_set",
+    "cn_tune_save",
+    "cn_tune_load",
     "cn_autotune",
     "cn_autotune_batched",
     "cn_get_device_status",
@@ -548,6 +551,19 @@ def cn_tune_get(variant, n_i, n_j) -> dict:
 def cn_tune_set(variant, n_i, n_j, tune) -> None:
     ref = None if tune is None else ctypes.byref(_tune_struct(tune))
     check(load().cn_tune_set(_variant(variant), int(n_i), int(n_j), ref), "cn_tune_set")
+
+
+def cn_tune_save(path) -> None:
+    """Writes the current device's tuning entries to `path` (JSON)."""
+    check(load().cn_tune_save(os.fsencode(path)), "cn_tune_save")
+
+
+def cn_tune_load(path) -> int:
+    """Stores the entries of a tuning file written on this kind of device;
+    returns how many were stored."""
+    n = ctypes.c_int32(0)
+    check(load().cn_tune_load(os.fsencode(path), ctypes.byref(n)), "cn_tune_load")
+    return int(n.value)
 
 
 def cn_autotune(variant, pos_i, pos_mass_j, eps2, reps=3, stream=None) -> dict:

@@ -65,6 +65,8 @@ SIGNATURES = {
     "cn_force_host_f64": (c_int, [vp, vp, vp, c_f64, vp, c_int, c_int]),
     "cn_tune_get": (c_int, [c_int, c_i64, c_i64, ctypes.POINTER(cn_tune)]),
     "cn_tune_set": (c_int, [c_int, c_i64, c_i64, ctypes.POINTER(cn_tune)]),
+    "cn_tune_save": (c_int, [ctypes.c_char_p]),
+    "cn_tune_load": (c_int, [ctypes.c_char_p, ctypes.POINTER(c_i32)]),
     "cn_autotune": (c_int, [c_int, c_i64, vp, c_i64, vp, c_f32, vp, vp, c_int, vp, ctypes.POINTER(cn_tune)]),
     "cn_autotune_batched": (c_int, [c_i32, vp, vp, vp, vp, vp, c_int, vp, ctypes.POINTER(cn_tune)]),
     "cn_get_device_status": (c_int, [vp]),

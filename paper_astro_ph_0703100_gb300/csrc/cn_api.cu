@@ -5,10 +5,13 @@
 #include "cn_kernels.h"
 #include "cn_sym.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
 #include <atomic>
 #include <cfloat>
 #include <cmath>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <map>
@@ -19,6 +22,7 @@
 
 namespace cn {
 cudaError_t device_status_address(int** p);
+cudaError_t static_scratch_setup();
 cudaError_t launch_timeout_probe(int* status, uint64_t wait_ns, cudaStream_t s);
 cudaError_t run_probes(cudaStream_t s, double* out);
 size_t energy_workspace_doubles();
@@ -70,6 +74,30 @@ cn_status fail_cuda(cudaError_t e, const char* what) {
   return CN_ERR_CUDA;
 }
 
+// An NVTX range around each entry point (visible to Nsight tools; a few
+// nanoseconds when no tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
+// CN_LOG=1 (read once, at the first call) prints each launch plan to stderr.
+bool log_enabled() {
+  static const bool on = [] {
+    const char* v = std::getenv("CN_LOG");
+    return v && *v && std::strcmp(v, "0") != 0;
+  }();
+  return on;
+}
+
+const char* variant_name(int v) {
+  static const char* names[] = {"f32", "f32_pot", "dd", "dd_pot", "adjoint", "batched", "batched_pot",
+                                "jerk", "jerk_pot", "symmetric", "f32_eps_i", "f32_eps_i_pot"};
+  return (v >= 0 && v < 12) ? names[v] : "?";
+}
+
 // Host-side fault injection for tests: CN_FAULT_INJECT holds a comma list of
 // "alloc", "launch", "capture"; the matching step then fails as if the CUDA
 // call had failed. Nothing is done on the device.
@@ -97,32 +125,67 @@ struct DeviceInfo {
   bool supported = false;
 };
 
-std::mutex g_mu;  // guards the maps below
-std::map<int, DeviceInfo> g_devices;
+std::mutex g_mu;  // guards the maps below and the creation of device entries
+
+// Device entries, created once per device ordinal by the first call there
+// (under g_mu) and never freed; read without a lock afterwards.
+constexpr int kMaxDevices = 64;
+std::atomic<DeviceInfo*> g_dev_table[kMaxDevices];
+
+// Bumped whenever something a cached launch plan depends on changes: a
+// tuning entry, or the address of a library workspace. Calls compare it
+// with the generation their per-thread plan cache was filled under.
+std::atomic<uint64_t> g_plan_gen{1};
+thread_local uint64_t t_own_bumps = 0;  // generation bumps made by this thread's own workspace growth
+
+// The launch plan of this thread's last single-system call, reused while the
+// call's key and the generation match (the common loop of identical calls
+// then skips the tuning, occupancy and workspace lookups).
+struct PlanCache {
+  bool valid = false;
+  uint64_t gen = 0;
+  int dev = -1;
+  int variant = -1;
+  int64_t n_i = -1, n_j = -1;
+  bool guard = false;
+  cudaStream_t stream = nullptr;
+};
+
+DeviceInfo* device_entry(int dev) {
+  return (dev >= 0 && dev < kMaxDevices) ? g_dev_table[dev].load(std::memory_order_acquire) : nullptr;
+}
 
 cn_status current_device(int* dev_out, DeviceInfo** info) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return fail_cuda(e, "cudaGetDevice");
-  std::lock_guard<std::mutex> lock(g_mu);
-  auto it = g_devices.find(dev);
-  if (it == g_devices.end()) {
-    DeviceInfo d;
-    if ((e = cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
-        (e = cudaDeviceGetAttribute(&d.major, cudaDevAttrComputeCapabilityMajor, dev)) != cudaSuccess ||
-        (e = cudaDeviceGetAttribute(&d.minor, cudaDevAttrComputeCapabilityMinor, dev)) != cudaSuccess)
-      return fail_cuda(e, "cudaDeviceGetAttribute");
-    d.supported = (d.major == 10 && d.minor == 3);
-    if (d.supported && (e = cn::device_status_address(&d.status)) != cudaSuccess)
-      return fail_cuda(e, "cudaGetSymbolAddress(device status)");
-    it = g_devices.emplace(dev, d).first;
+  if (dev < 0 || dev >= kMaxDevices) return fail(CN_ERR_UNSUPPORTED_DEVICE, "device ordinal out of range");
+  DeviceInfo* d = device_entry(dev);
+  if (!d) {
+    std::lock_guard<std::mutex> lock(g_mu);
+    d = g_dev_table[dev].load(std::memory_order_acquire);
+    if (!d) {
+      DeviceInfo nd;
+      if ((e = cudaDeviceGetAttribute(&nd.sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
+          (e = cudaDeviceGetAttribute(&nd.major, cudaDevAttrComputeCapabilityMajor, dev)) != cudaSuccess ||
+          (e = cudaDeviceGetAttribute(&nd.minor, cudaDevAttrComputeCapabilityMinor, dev)) != cudaSuccess)
+        return fail_cuda(e, "cudaDeviceGetAttribute");
+      nd.supported = (nd.major == 10 && nd.minor == 3);
+      if (nd.supported && (e = cn::device_status_address(&nd.status)) != cudaSuccess)
+        return fail_cuda(e, "cudaGetSymbolAddress(device status)");
+      // the static scratch of cn_force_noalloc: its address, and its device
+      // module loaded, on the library's first call on this device
+      if (nd.supported && (e = cn::static_scratch_setup()) != cudaSuccess)
+        return fail_cuda(e, "cudaGetSymbolAddress(static scratch)");
+      d = new DeviceInfo(nd);
+      g_dev_table[dev].store(d, std::memory_order_release);
+    }
   }
-  if (!it->second.supported)
+  if (!d->supported)
     return fail(CN_ERR_UNSUPPORTED_DEVICE, "libcunbody is built for sm_103a (GB300); device " + std::to_string(dev) +
-                                               " is sm_" + std::to_string(it->second.major) +
-                                               std::to_string(it->second.minor));
+                                               " is sm_" + std::to_string(d->major) + std::to_string(d->minor));
   if (dev_out) *dev_out = dev;
-  *info = &it->second;
+  *info = d;
   return CN_OK;
 }
 
@@ -168,6 +231,8 @@ cn_status grow(cudaStream_t s, void** buf, size_t* bytes, size_t need, bool zero
   }
   *buf = p;
   *bytes = nb;
+  g_plan_gen.fetch_add(1, std::memory_order_acq_rel);  // cached plans held the old address
+  ++t_own_bumps;
   return CN_OK;
 }
 
@@ -206,6 +271,7 @@ void release_library_workspace(cudaStream_t s) {
   if (it->second.data) cudaFree(it->second.data);
   if (it->second.aux) cudaFree(it->second.aux);
   g_ws.erase(it);
+  g_plan_gen.fetch_add(1, std::memory_order_acq_rel);
 }
 
 cn_status library_aux(cudaStream_t s, double** out) {
@@ -326,7 +392,9 @@ cn_tune mid_f32_tune(int64_t n_i, int64_t n_j, int sms) {
   return best;
 }
 
-cn_tune default_tune(int variant, int64_t n_i, int64_t n_j) {
+// Default launch shape of a variant for these sizes on a device with `sms`
+// multiprocessors (queried, never assumed).
+cn_tune default_tune(int variant, int64_t n_i, int64_t n_j, int sms) {
   cn_tune t{};
   const int64_t n = std::max(n_i, n_j);
   const bool dd = variant == cn::kDD || variant == cn::kDDPot;
@@ -351,7 +419,39 @@ cn_tune default_tune(int variant, int64_t n_i, int64_t n_j) {
     t.stages = n_j <= t.j_tile ? 1 : 3;
     return t;
   }
-  if (f32 && n_i <= 20000) return mid_f32_tune(n_i, n_j, 152);
+  if (f32) {
+    // Mid-size systems (measured on GB300, 152 SMs, N = 5000 .. 65536,
+    // graph-replayed launches): split-j lane groups holding four or eight
+    // i-particles keep the i-tiles small enough to fill the SMs while each
+    // j record feeds several packed pair terms. Sizes are compared by the
+    // work per SM, n_eff = sqrt(n_i n_j) sqrt(152 / sms), so another SM count
+    // moves the bands. Below 6500 the schedule model of mid_f32_tune decides.
+    const double n_eff = std::sqrt(static_cast<double>(n_i) * static_cast<double>(std::max<int64_t>(n_j, 1))) *
+                         std::sqrt(152.0 / std::max(sms, 1));
+    struct Band {
+      double upto;
+      int k, threads, j_tile, j_lanes;
+    };
+    static const Band bands[] = {
+        {10000.0, 4, 256, 4096, 8},   // N = 8192: 0.553 of the FP32 bound
+        {14000.0, 8, 256, 4096, 8},   // N = 12000: 0.641
+        {20000.0, 8, 256, 2048, 16},  // N = 16384: 0.711
+        {28000.0, 8, 256, 2048, 8},   // N = 24576: 0.740
+        {40000.0, 8, 256, 1024, 8},   // N = 32768: 0.784
+    };
+    if (n_i > 4096 && n_eff <= 6500.0) return mid_f32_tune(n_i, n_j, sms);
+    if (n_i > 4096 && n_eff <= bands[4].upto) {
+      for (const Band& b : bands) {
+        if (n_eff > b.upto) continue;
+        t.i_per_thread = b.k;
+        t.threads = b.threads;
+        t.j_tile = b.j_tile;
+        t.j_lanes = b.j_lanes;
+        t.stages = n_j <= b.j_tile ? 1 : 3;
+        return t;
+      }
+    }
+  }
   if ((variant == cn::kJerk || variant == cn::kJerkPot || variant == cn::kAdjoint) && n_i <= 8192) {
     // small systems, measured at N = 1024 .. 8192 (force + jerk + potential,
     // and the adjoint, with the same optima): packed split-j, two
@@ -365,19 +465,15 @@ cn_tune default_tune(int variant, int64_t n_i, int64_t n_j) {
     t.stages = n_j <= t.j_tile ? 1 : 3;
     return t;
   }
-  if (variant == cn::kSym) return sym_default_tune(n, 152, false);
+  if (variant == cn::kSym) return sym_default_tune(n, sms, false);
   if (variant == cn::kBatched || variant == cn::kBatchedPot) {
     t.i_per_thread = 4;
     t.j_tile = 256;
   } else if (f32 && n > 4096) {
-    // packed FP32, measured at N = 16384 .. 131072: K = 2 x 128 threads with
-    // 1024-record j-tiles up to N ~ 16K, K = 4 x 256 with 512-record tiles
-    // around 32K - 64K, K = 8 x 256 with 1024-record tiles above
-    if (n < 24576) {
-      t.i_per_thread = 2;
-      t.threads = 256;
-      t.j_tile = 512;
-    } else if (n < 98304) {
+    // packed FP32, measured at N = 49152 .. 131072 (smaller systems take the
+    // bands above): K = 4 x 256 with 512-record tiles below ~96K, K = 8 x 256
+    // with 1024-record tiles above
+    if (n < 98304) {
       t.i_per_thread = 4;
       t.threads = 256;
       t.j_tile = 512;
@@ -388,9 +484,9 @@ cn_tune default_tune(int variant, int64_t n_i, int64_t n_j) {
     }
   } else if (n >= 32768) {
     // measured optima (packed forms): FP32 K = 8 x 256 threads at N = 131072,
-    // DD K = 2 x 256, adjoint (N = 65536) and force-jerk (N = 131072)
-    // K = 4 x 256 with j-tiles of 256 two-record j entries
-    t.i_per_thread = adj ? 4 : (dd ? 2 : 8);
+    // compensated K = 4 x 256, adjoint (N = 65536) and force-jerk
+    // (N = 131072) K = 4 x 256 with j-tiles of 256 two-record j entries
+    t.i_per_thread = adj ? 4 : (dd ? 4 : 8);
     t.threads = 256;
     t.j_tile = adj ? 256 : 1024;
   } else if (n >= 4096) {
@@ -417,9 +513,14 @@ cn_status check_tune(int variant, const cn_tune& t) {
     return fail(CN_ERR_INVALID_ARG, "j_lanes must be 0 or a power of two up to 32");
   if (t.j_lanes > 1) {
     const bool jerk = variant == cn::kJerk || variant == cn::kJerkPot || variant == cn::kAdjoint;
-    if (variant != cn::kF32 && variant != cn::kF32Pot && variant != cn::kF32EpsI && variant != cn::kF32EpsIPot && !jerk)
-      return fail(CN_ERR_INVALID_ARG, "j_lanes > 1 is offered for the plain FP32, force-jerk and adjoint forms");
-    if (t.i_per_thread > 2) return fail(CN_ERR_INVALID_ARG, "j_lanes > 1 needs i_per_thread = 1 or 2");
+    const bool eps_i = variant == cn::kF32EpsI || variant == cn::kF32EpsIPot;
+    const bool f32 = variant == cn::kF32 || variant == cn::kF32Pot || variant == cn::kBatched ||
+                     variant == cn::kBatchedPot;
+    if (!f32 && !eps_i && !jerk)
+      return fail(CN_ERR_INVALID_ARG, "j_lanes > 1 is offered for the FP32 (single, batched, per-i softening), "
+                                      "force-jerk and adjoint forms");
+    if (eps_i && t.i_per_thread > 2)
+      return fail(CN_ERR_INVALID_ARG, "the per-i-softening form takes j_lanes > 1 with i_per_thread = 1 or 2");
     if (jerk && t.i_per_thread != 2)
       return fail(CN_ERR_INVALID_ARG, "the force-jerk and adjoint forms take j_lanes > 1 with i_per_thread = 2");
     if (t.j_tile && t.j_tile % (8 * t.j_lanes))
@@ -439,26 +540,11 @@ bool registered_tune(int dev, int variant, int64_t n_i, int64_t n_j) {
 
 cn_status resolve_plan(int dev, int variant, int64_t n_i, int64_t n_j, bool guard, const cn_tune* explicit_tune,
                        Plan* p) {
-  cn_tune t = default_tune(variant, n_i, n_j);
-  if (variant == cn::kSym) {
-    int sms = 0;
-    {
-      std::lock_guard<std::mutex> lock(g_mu);
-      auto it = g_devices.find(dev);
-      if (it != g_devices.end()) sms = it->second.sms;
-    }
-    if (sms > 0) t = sym_default_tune(std::max(n_i, n_j), sms, false);
-  }
-  if ((variant == cn::kF32 || variant == cn::kF32Pot || variant == cn::kF32EpsI || variant == cn::kF32EpsIPot) &&
-      n_i > 4096 && n_i <= 20000) {
-    int sms = 0;
-    {
-      std::lock_guard<std::mutex> lock(g_mu);
-      auto it = g_devices.find(dev);
-      if (it != g_devices.end()) sms = it->second.sms;
-    }
-    if (sms > 0) t = mid_f32_tune(n_i, n_j, sms);
-  }
+  int sms = 0;
+  if (const DeviceInfo* d = device_entry(dev)) sms = d->sms;
+  if (sms <= 0 && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return fail(CN_ERR_CUDA, "cudaDeviceGetAttribute(multiprocessor count)");
+  cn_tune t = default_tune(variant, n_i, n_j, sms);
   cn_tune chosen{};
   bool have = false;
   if (explicit_tune) {
@@ -496,8 +582,11 @@ cn_status resolve_plan(int dev, int variant, int64_t n_i, int64_t n_j, bool guar
     p->k = 1;
   }
   if (p->j_lanes > 1) {
-    // split-j: one i-particle per lane group, or two with the packed form
-    p->k = (p->k == 2 && !guard) ? 2 : 1;
+    // split-j: K i-particles per lane group (packed for K >= 2; the guarded
+    // kernels hold one, the per-i-softening ones at most two)
+    const bool eps_i = variant == cn::kF32EpsI || variant == cn::kF32EpsIPot;
+    if (guard) p->k = 1;
+    else if (eps_i && p->k > 2) p->k = 2;
     if (p->j_tile % (8 * p->j_lanes)) return fail(CN_ERR_INVALID_ARG, "j_tile must be a multiple of 8 x j_lanes");
   }
   const size_t smem = variant == cn::kSym
@@ -525,6 +614,32 @@ struct Geometry {
 };
 
 std::map<std::tuple<int, int, bool, int, int, int, size_t>, int> g_occ;
+
+// One line per launch on stderr when CN_LOG is set: the variant, sizes,
+// launch shape, grid, units, chunks and how many i-tiles are split across
+// chunks (those take the FP64 merge). Single-system schedules only count
+// split tiles; batched plans pass n_tiles_split < 0.
+void log_plan(const char* entry, int variant, int64_t n_i, int64_t n_j, bool guard, const Plan& p, const Geometry& g,
+              int64_t njt) {
+  if (!log_enabled()) return;
+  int64_t split = -1;
+  if (njt > 0 && g.units > 0 && p.chunk_units == 0) {
+    split = 0;
+    const int64_t U = g.units, Q = g.n_chunks;
+    auto chunk_of = [&](int64_t u) { return ((u + 1) * Q - 1) / U; };
+    for (int64_t t = 0; t < g.n_tiles; ++t)
+      if (chunk_of(t * njt) != chunk_of(t * njt + njt - 1)) ++split;
+  }
+  std::fprintf(stderr,
+               "[cunbody] %s: variant %s n_i %lld n_j %lld%s | K %d threads %d j_tile %d stages %d j_lanes %d "
+               "chunk_units %lld ctas_per_sm %d | grid %d units %lld chunks %lld i_tiles %lld split_tiles %lld "
+               "smem %zu ws %zu\n",
+               entry, variant_name(variant), static_cast<long long>(n_i), static_cast<long long>(n_j),
+               guard ? " (guarded)" : "", p.k, p.threads, p.j_tile, p.stages, p.j_lanes,
+               static_cast<long long>(p.chunk_units), p.ctas_per_sm, g.grid, static_cast<long long>(g.units),
+               static_cast<long long>(g.n_chunks), static_cast<long long>(g.n_tiles), static_cast<long long>(split),
+               g.smem, g.ws_bytes);
+}
 
 cn_status occupancy(int dev, int variant, bool guard, const Plan& p, size_t smem, int* ctas) {
   const auto key = std::make_tuple(dev, variant, guard, p.j_lanes, p.k, p.threads, smem);
@@ -684,13 +799,42 @@ cn_status force_common(bool dd, int64_t n_i, const float* pos_i, int64_t n_j, co
   const bool guard = eps_i || needs_guard(eps2);
   const int variant = eps_i ? (pot ? cn::kF32EpsIPot : cn::kF32EpsI)
                             : (dd ? (pot ? cn::kDDPot : cn::kDD) : (pot ? cn::kF32Pot : cn::kF32));
+  struct Cached {
+    PlanCache key;
+    Plan p;
+    Geometry g;
+    char* ctrl = nullptr;
+    char* data = nullptr;
+  };
+  thread_local Cached t_last;
   Plan p;
-  // the per-particle kernels are guarded in every shape, so K is not restricted to 1
-  if ((st = resolve_plan(dev, variant, n_i, n_j, guard && !eps_i, nullptr, &p)) != CN_OK) return st;
   Geometry g;
-  if ((st = single_geometry(dev, *d, variant, guard, p, n_i, n_j, &g)) != CN_OK) return st;
   char *ctrl = nullptr, *data = nullptr;
-  if ((st = launch_workspace(s, g, ws, ws_bytes, lib_ws, &ctrl, &data)) != CN_OK) return st;
+  const uint64_t gen0 = g_plan_gen.load(std::memory_order_acquire);
+  const PlanCache& k = t_last.key;
+  if (lib_ws && k.valid && k.gen == gen0 && k.dev == dev && k.variant == variant && k.n_i == n_i && k.n_j == n_j &&
+      k.guard == guard && k.stream == s) {
+    p = t_last.p;
+    g = t_last.g;
+    ctrl = t_last.ctrl;
+    data = t_last.data;
+  } else {
+    const uint64_t bumps0 = t_own_bumps;
+    // the per-particle kernels are guarded in every shape, so K is not restricted to 1
+    if ((st = resolve_plan(dev, variant, n_i, n_j, guard && !eps_i, nullptr, &p)) != CN_OK) return st;
+    if ((st = single_geometry(dev, *d, variant, guard, p, n_i, n_j, &g)) != CN_OK) return st;
+    if ((st = launch_workspace(s, g, ws, ws_bytes, lib_ws, &ctrl, &data)) != CN_OK) return st;
+    // cache only a plan that nothing changed under (another thread's tuning
+    // or workspace change would show as a generation step not our own)
+    const uint64_t gen1 = g_plan_gen.load(std::memory_order_acquire);
+    if (lib_ws && gen1 == gen0 + (t_own_bumps - bumps0)) {
+      t_last.key = PlanCache{true, gen1, dev, variant, n_i, n_j, guard, s};
+      t_last.p = p;
+      t_last.g = g;
+      t_last.ctrl = ctrl;
+      t_last.data = data;
+    }
+  }
   PairArgs a = base_args(ctrl, data, g, p, d->status);
   a.pos_i = reinterpret_cast<const float4*>(pos_i);
   a.pos_j = reinterpret_cast<const float4*>(pos_mass_j);
@@ -699,6 +843,7 @@ cn_status force_common(bool dd, int64_t n_i, const float* pos_i, int64_t n_j, co
   a.n_i = n_i;
   a.n_j = n_j;
   a.eps2 = eps2;
+  log_plan(dd ? "cn_force_dd" : (eps_i ? "cn_force_eps_i" : "cn_force"), variant, n_i, n_j, guard, p, g, g.njt);
   if (inject("launch")) return fail(CN_ERR_CUDA, "kernel launch: injected launch failure");
   e = dd ? cn::launch_dd(a, p, pot, guard, g.grid, s) : cn::launch_f32(a, p, pot, guard, false, g.grid, s, eps_i);
   if (e != cudaSuccess) return fail_cuda(e, "pair kernel launch");
@@ -761,6 +906,7 @@ cn_status jerk_common(int64_t n_i, const float* pos_i, const float* vel_i, int64
   a.n_i = n_i;
   a.n_j = n_j;
   a.eps2 = eps2;
+  log_plan("cn_force_jerk", variant, n_i, n_j, guard, p, g, g.njt);
   if (inject("launch")) return fail(CN_ERR_CUDA, "kernel launch: injected launch failure");
   e = cn::launch_jerk(a, p, pot, guard, g.grid, s);
   return e == cudaSuccess ? CN_OK : fail_cuda(e, "force-jerk kernel launch");
@@ -860,6 +1006,14 @@ cn_status symmetric_common(int64_t n, const float* pos_mass, float eps2, float* 
     m.first = r0 == 0;
     m.last = r1 == T;
     const int grid = static_cast<int>(std::min<int64_t>(slots, a.units));
+    if (log_enabled())
+      std::fprintf(stderr,
+                   "[cunbody] cn_force_symmetric: n %lld%s%s | K %d threads %d sub_tile %d stages %d | tile %lld "
+                   "tiles %lld band rows %lld..%lld units %lld grid %d smem %zu slots %zu bytes\n",
+                   static_cast<long long>(n), pot ? " +pot" : "", guard ? " (guarded)" : "", guard ? 1 : p.k,
+                   p.threads, p.j_tile, p.stages, static_cast<long long>(B), static_cast<long long>(T),
+                   static_cast<long long>(r0), static_cast<long long>(r1), static_cast<long long>(a.units), grid, smem,
+                   need);
     if (inject("launch")) return fail(CN_ERR_CUDA, "kernel launch: injected launch failure");
     e = cn::launch_sym(a, m, guard ? 1 : p.k, guard, p.threads, grid, smem, s, pot);
     if (e != cudaSuccess) return fail_cuda(e, "symmetric kernel launch");
@@ -910,6 +1064,12 @@ cn_status run_batched(const cn_batch_plan* plan, const float* pos_i, const float
   a.tiles = plan->d_tiles;
   a.n_i = plan->n_total;
   a.n_j = plan->n_j_total;
+  if (log_enabled()) {
+    Geometry lg = g;
+    lg.grid = plan->grid;
+    log_plan(plan->lists ? "cn_force_lists" : "cn_force_batched", plan->pot ? cn::kBatchedPot : cn::kBatched,
+             plan->n_total, plan->n_j_total, plan->guard, plan->plan, lg, 0);
+  }
   if (inject("launch")) return fail(CN_ERR_CUDA, "kernel launch: injected launch failure");
   e = cn::launch_f32(a, plan->plan, plan->pot, plan->guard, true, plan->grid, s);
   if (e != cudaSuccess) return fail_cuda(e, "batched pair kernel launch");
@@ -944,30 +1104,41 @@ cn_status build_group_plan(const std::vector<Group>& groups, bool lists, int64_t
   cn_tune fitted{};
   if (!tune && !registered_tune(dev, variant, key_i, n_i_total)) {
     // i-tile fitted to the group sizes: every group is cut into whole i-tiles,
-    // so a tile larger than the typical group leaves lanes idle. Among
-    // K = 8, 4, 2, 1 particles per thread (128 threads) take the one with
-    // the least evaluated-but-padded work, weighted by the relative pair
-    // rate of each K (measured on the 512-cluster ensemble).
-    const int ks[4] = {8, 4, 2, 1};
-    const double rate[4] = {1.0, 0.987, 0.974, 0.85};
+    // so a tile larger than the typical group leaves lanes idle. Among the
+    // shapes below take the one with the least evaluated-but-padded work,
+    // weighted by each shape's relative pair rate (measured on GB300: the
+    // packed K = 8 kernel 1.0, its split-j forms 0.95, K = 4 0.99, K = 2 x 128
+    // 0.93, one particle per thread 0.80; the split-j forms hold small tiles
+    // with eight i-particles per lane group).
+    struct Cand {
+      int k, threads, j_lanes, j_tile;
+      double rate;
+    };
+    static const Cand cands[] = {{8, 256, 1, 512, 1.0},  {8, 256, 2, 512, 0.95}, {8, 256, 4, 512, 0.95},
+                                 {8, 256, 8, 512, 0.95}, {8, 128, 8, 512, 0.94}, {4, 128, 1, 256, 0.99},
+                                 {2, 128, 1, 256, 0.93}, {1, 128, 1, 256, 0.80}};
     double best = -1.0;
-    for (int c = 0; c < 4; ++c) {
-      const int64_t it = static_cast<int64_t>(ks[c]) * 128;
+    for (const Cand& c : cands) {
+      if (guard && (c.j_lanes > 1 || c.k > 1)) continue;  // the guarded kernels hold one particle, no split-j
+      const int64_t it = static_cast<int64_t>(c.k) * c.threads / c.j_lanes;
       double padded = 0.0;
       for (const Group& gr : groups) padded += static_cast<double>(ceil_div(gr.ni, it) * it) * static_cast<double>(gr.nj);
-      const double score = padded > 0.0 ? pairs / padded * rate[c] : rate[c];
+      const double score = padded > 0.0 ? pairs / padded * c.rate : c.rate;
       if (score > best) {
         best = score;
-        fitted = default_tune(variant, key_i, n_i_total);
-        fitted.i_per_thread = ks[c];
-        fitted.threads = 128;
+        fitted = default_tune(variant, key_i, n_i_total, d->sms);
+        fitted.i_per_thread = c.k;
+        fitted.threads = c.threads;
+        fitted.j_lanes = c.j_lanes;
+        fitted.j_tile = c.j_tile;
       }
     }
     tune = &fitted;
   }
   Plan p;
   if ((st = resolve_plan(dev, variant, key_i, n_i_total, guard, tune, &p)) != CN_OK) return st;
-  if (p.j_lanes > 1) p.j_lanes = 1;  // the batched kernels hold whole i-particles per lane
+  // split-j batched kernels exist for K = 2, 4, 8 without the s = 0 guard
+  if (p.j_lanes > 1 && (guard || p.k < 2)) p.j_lanes = 1;
   // tiles in order of decreasing work (largest first for the dynamic queue)
   std::vector<size_t> order(groups.size());
   for (size_t c = 0; c < groups.size(); ++c) order[c] = c;
@@ -1123,6 +1294,164 @@ cn_status energy_common(int64_t n, const float* pos_mass, const float* pot_f, co
   return e == cudaSuccess ? CN_OK : fail_cuda(e, "potential-energy kernel launch");
 }
 
+// ------------------------------------------------------------------ tuning file
+// A small reader for the JSON the library writes (objects, arrays, strings
+// without escapes other than \" and \\, integers, true/false/null).
+struct JsonValue {
+  enum Kind { kNull, kBool, kNumber, kString, kArray, kObject } kind = kNull;
+  double number = 0.0;
+  bool boolean = false;
+  std::string text;
+  std::vector<JsonValue> items;
+  std::vector<std::pair<std::string, JsonValue>> fields;
+  const JsonValue* get(const char* key) const {
+    for (const auto& f : fields)
+      if (f.first == key) return &f.second;
+    return nullptr;
+  }
+};
+
+struct JsonReader {
+  const std::string& src;
+  size_t pos = 0;
+  int depth = 0;
+  void skip() {
+    while (pos < src.size() && (src[pos] == ' ' || src[pos] == '\n' || src[pos] == '\r' || src[pos] == '\t')) ++pos;
+  }
+  bool literal(const char* word) {
+    const size_t n = std::strlen(word);
+    if (src.compare(pos, n, word) != 0) return false;
+    pos += n;
+    return true;
+  }
+  bool string(std::string* out) {
+    if (pos >= src.size() || src[pos] != '"') return false;
+    ++pos;
+    out->clear();
+    while (pos < src.size() && src[pos] != '"') {
+      char c = src[pos++];
+      if (c == '\\') {
+        if (pos >= src.size()) return false;
+        c = src[pos++];
+        if (c != '"' && c != '\\' && c != '/') return false;
+      }
+      out->push_back(c);
+    }
+    if (pos >= src.size()) return false;
+    ++pos;
+    return true;
+  }
+  bool value(JsonValue* v) {
+    if (++depth > 16) return false;
+    skip();
+    bool ok = false;
+    if (pos >= src.size()) {
+      ok = false;
+    } else if (src[pos] == '{') {
+      v->kind = JsonValue::kObject;
+      ++pos;
+      skip();
+      if (pos < src.size() && src[pos] == '}') {
+        ++pos;
+        ok = true;
+      } else {
+        for (;;) {
+          skip();
+          std::pair<std::string, JsonValue> f;
+          if (!string(&f.first)) break;
+          skip();
+          if (pos >= src.size() || src[pos] != ':') break;
+          ++pos;
+          if (!value(&f.second)) break;
+          v->fields.push_back(std::move(f));
+          skip();
+          if (pos < src.size() && src[pos] == ',') {
+            ++pos;
+            continue;
+          }
+          if (pos < src.size() && src[pos] == '}') {
+            ++pos;
+            ok = true;
+          }
+          break;
+        }
+      }
+    } else if (src[pos] == '[') {
+      v->kind = JsonValue::kArray;
+      ++pos;
+      skip();
+      if (pos < src.size() && src[pos] == ']') {
+        ++pos;
+        ok = true;
+      } else {
+        for (;;) {
+          JsonValue item;
+          if (!value(&item)) break;
+          v->items.push_back(std::move(item));
+          skip();
+          if (pos < src.size() && src[pos] == ',') {
+            ++pos;
+            continue;
+          }
+          if (pos < src.size() && src[pos] == ']') {
+            ++pos;
+            ok = true;
+          }
+          break;
+        }
+      }
+    } else if (src[pos] == '"') {
+      v->kind = JsonValue::kString;
+      ok = string(&v->text);
+    } else if (literal("true")) {
+      v->kind = JsonValue::kBool;
+      v->boolean = true;
+      ok = true;
+    } else if (literal("false")) {
+      v->kind = JsonValue::kBool;
+      ok = true;
+    } else if (literal("null")) {
+      ok = true;
+    } else {
+      const char* start = src.c_str() + pos;
+      char* end = nullptr;
+      v->number = std::strtod(start, &end);
+      if (end != start) {
+        v->kind = JsonValue::kNumber;
+        pos += static_cast<size_t>(end - start);
+        ok = std::isfinite(v->number);
+      }
+    }
+    --depth;
+    return ok;
+  }
+};
+
+int variant_from_name(const std::string& name) {
+  for (int v = 0; v < 12; ++v)
+    if (name == variant_name(v)) return v;
+  return -1;
+}
+
+bool json_int(const JsonValue& o, const char* key, int64_t lo, int64_t hi, int64_t* out) {
+  const JsonValue* v = o.get(key);
+  if (!v || v->kind != JsonValue::kNumber || v->number != std::floor(v->number) || v->number < static_cast<double>(lo) ||
+      v->number > static_cast<double>(hi))
+    return false;
+  *out = static_cast<int64_t>(v->number);
+  return true;
+}
+
+cn_status device_identity(int dev, std::string* name, std::string* arch, int* sms) {
+  cudaDeviceProp prop{};
+  const cudaError_t e = cudaGetDeviceProperties(&prop, dev);
+  if (e != cudaSuccess) return fail_cuda(e, "cudaGetDeviceProperties");
+  *name = prop.name;
+  *arch = "sm_" + std::to_string(prop.major) + std::to_string(prop.minor);
+  *sms = prop.multiProcessorCount;
+  return CN_OK;
+}
+
 }  // namespace
 
 namespace cn {
@@ -1140,30 +1469,35 @@ extern "C" {
 
 cn_status cn_force(int64_t n_i, const float* pos_i, int64_t n_j, const float* pos_mass_j, float eps2, float* acc_out,
                    float* pot_out, cn_stream stream) {
+  NvtxRange nvtx_range("cn_force");
   return force_common(false, n_i, pos_i, n_j, pos_mass_j, eps2, acc_out, pot_out, nullptr, 0, true,
                       reinterpret_cast<cudaStream_t>(stream));
 }
 
 cn_status cn_force_eps_i(int64_t n_i, const float* pos_eps_i, int64_t n_j, const float* pos_mass_j, float* acc_out,
                          float* pot_out, cn_stream stream) {
+  NvtxRange nvtx_range("cn_force_eps_i");
   return force_common(false, n_i, pos_eps_i, n_j, pos_mass_j, 0.f, acc_out, pot_out, nullptr, 0, true,
                       reinterpret_cast<cudaStream_t>(stream), true);
 }
 
 cn_status cn_force_ws(int64_t n_i, const float* pos_i, int64_t n_j, const float* pos_mass_j, float eps2,
                       float* acc_out, float* pot_out, void* workspace, size_t ws_bytes, cn_stream stream) {
+  NvtxRange nvtx_range("cn_force_ws");
   return force_common(false, n_i, pos_i, n_j, pos_mass_j, eps2, acc_out, pot_out, workspace, ws_bytes, false,
                       reinterpret_cast<cudaStream_t>(stream));
 }
 
 cn_status cn_force_dd(int64_t n_i, const float* pos_i, int64_t n_j, const float* pos_mass_j, float eps2,
                       double* acc_out, double* pot_out, cn_stream stream) {
+  NvtxRange nvtx_range("cn_force_dd");
   return force_common(true, n_i, pos_i, n_j, pos_mass_j, eps2, acc_out, pot_out, nullptr, 0, true,
                       reinterpret_cast<cudaStream_t>(stream));
 }
 
 cn_status cn_force_dd_ws(int64_t n_i, const float* pos_i, int64_t n_j, const float* pos_mass_j, float eps2,
                          double* acc_out, double* pot_out, void* workspace, size_t ws_bytes, cn_stream stream) {
+  NvtxRange nvtx_range("cn_force_dd_ws");
   return force_common(true, n_i, pos_i, n_j, pos_mass_j, eps2, acc_out, pot_out, workspace, ws_bytes, false,
                       reinterpret_cast<cudaStream_t>(stream));
 }
@@ -1189,6 +1523,7 @@ size_t cn_workspace_bytes(int variant, int64_t n_i, int64_t n_j) {
 
 cn_status cn_batch_plan_create(int32_t n_clusters, const int64_t* offsets_host, const float* eps2_host,
                                const cn_tune* tune, int with_potential, cn_batch_plan** plan_out) {
+  NvtxRange nvtx_range("cn_batch_plan_create");
   return build_batch_plan(n_clusters, offsets_host, eps2_host, tune, with_potential, plan_out);
 }
 
@@ -1212,6 +1547,7 @@ cn_status cn_batch_plan_info(const cn_batch_plan* plan, int64_t* n_total, double
 
 cn_status cn_force_batched(const cn_batch_plan* plan, const float* pos_mass, float* acc_out, float* pot_out,
                            void* workspace, size_t ws_bytes, cn_stream stream) {
+  NvtxRange nvtx_range("cn_force_batched");
   if (plan && plan->lists) return fail(CN_ERR_INVALID_ARG, "an interaction-list plan runs with cn_force_lists");
   return run_batched(plan, pos_mass, pos_mass, acc_out, pot_out, workspace, ws_bytes,
                      reinterpret_cast<cudaStream_t>(stream));
@@ -1220,12 +1556,14 @@ cn_status cn_force_batched(const cn_batch_plan* plan, const float* pos_mass, flo
 cn_status cn_list_plan_create(int32_t n_groups, const int64_t* i_offsets_host, const int64_t* j_begin_host,
                               const int64_t* j_count_host, const float* eps2_host, const cn_tune* tune,
                               int with_potential, cn_batch_plan** plan_out) {
+  NvtxRange nvtx_range("cn_list_plan_create");
   return build_list_plan(n_groups, i_offsets_host, j_begin_host, j_count_host, eps2_host, tune, with_potential,
                          plan_out);
 }
 
 cn_status cn_force_lists(const cn_batch_plan* plan, const float* pos_i, const float* pos_mass_j, float* acc_out,
                          float* pot_out, void* workspace, size_t ws_bytes, cn_stream stream) {
+  NvtxRange nvtx_range("cn_force_lists");
   if (plan && !plan->lists) return fail(CN_ERR_INVALID_ARG, "a cluster plan runs with cn_force_batched");
   return run_batched(plan, pos_i, pos_mass_j, acc_out, pot_out, workspace, ws_bytes,
                      reinterpret_cast<cudaStream_t>(stream));
@@ -1263,17 +1601,20 @@ cn_status capture_plan(cn_batch_plan* plan, const float* pos_i, const float* pos
 
 cn_status cn_batch_plan_capture(cn_batch_plan* plan, const float* pos_mass, float* acc_out, float* pot_out,
                                 void* workspace, size_t ws_bytes, cn_stream stream) {
+  NvtxRange nvtx_range("cn_batch_plan_capture");
   if (plan && plan->lists) return fail(CN_ERR_INVALID_ARG, "an interaction-list plan is captured with cn_list_plan_capture");
   return capture_plan(plan, pos_mass, pos_mass, acc_out, pot_out, workspace, ws_bytes, stream);
 }
 
 cn_status cn_list_plan_capture(cn_batch_plan* plan, const float* pos_i, const float* pos_mass_j, float* acc_out,
                                float* pot_out, void* workspace, size_t ws_bytes, cn_stream stream) {
+  NvtxRange nvtx_range("cn_list_plan_capture");
   if (plan && !plan->lists) return fail(CN_ERR_INVALID_ARG, "a cluster plan is captured with cn_batch_plan_capture");
   return capture_plan(plan, pos_i, pos_mass_j, acc_out, pot_out, workspace, ws_bytes, stream);
 }
 
 cn_status cn_batch_plan_launch(const cn_batch_plan* plan, cn_stream stream) {
+  NvtxRange nvtx_range("cn_batch_plan_launch");
   if (!plan || !plan->exec) return fail(CN_ERR_INVALID_ARG, "plan has no captured graph");
   if (inject("launch")) return fail(CN_ERR_CUDA, "cudaGraphLaunch: injected launch failure");
   cudaError_t e = cudaGraphLaunch(plan->exec, reinterpret_cast<cudaStream_t>(stream));
@@ -1282,6 +1623,7 @@ cn_status cn_batch_plan_launch(const cn_batch_plan* plan, cn_stream stream) {
 
 cn_status cn_force_adjoint(int64_t n, const float* pos_mass, float eps2, const float* w, float* grad_pos,
                            float* grad_mass, cn_stream stream) {
+  NvtxRange nvtx_range("cn_force_adjoint");
   auto s = reinterpret_cast<cudaStream_t>(stream);
   if (n < 0) return fail(CN_ERR_INVALID_ARG, "n must be >= 0");
   cn_status st;
@@ -1320,6 +1662,7 @@ cn_status cn_force_adjoint(int64_t n, const float* pos_mass, float eps2, const f
   a.n_i = n;
   a.n_j = n;
   a.eps2 = eps2;
+  log_plan("cn_force_adjoint", cn::kAdjoint, n, n, guard, p, g, g.njt);
   e = cn::launch_adjoint(a, p, guard, g.grid, s);
   return e == cudaSuccess ? CN_OK : fail_cuda(e, "adjoint kernel launch");
 }
@@ -1327,26 +1670,31 @@ cn_status cn_force_adjoint(int64_t n, const float* pos_mass, float eps2, const f
 cn_status cn_force_jerk(int64_t n_i, const float* pos_i, const float* vel_i, int64_t n_j, const float* pos_mass_j,
                         const float* vel_j, float eps2, float* acc_out, float* jerk_out, float* pot_out,
                         cn_stream stream) {
+  NvtxRange nvtx_range("cn_force_jerk");
   return jerk_common(n_i, pos_i, vel_i, n_j, pos_mass_j, vel_j, eps2, acc_out, jerk_out, pot_out,
                      reinterpret_cast<cudaStream_t>(stream));
 }
 
 cn_status cn_force_symmetric(int64_t n, const float* pos_mass, float eps2, float* acc_out, float* pot_out,
                              cn_stream stream) {
+  NvtxRange nvtx_range("cn_force_symmetric");
   return symmetric_common(n, pos_mass, eps2, acc_out, pot_out, reinterpret_cast<cudaStream_t>(stream));
 }
 
 cn_status cn_potential_energy(int64_t n, const float* pos_mass, const float* pot, double* w_out, cn_stream stream) {
+  NvtxRange nvtx_range("cn_potential_energy");
   return energy_common(n, pos_mass, pot, nullptr, w_out, reinterpret_cast<cudaStream_t>(stream));
 }
 
 cn_status cn_potential_energy_dd(int64_t n, const float* pos_mass, const double* pot, double* w_out,
                                  cn_stream stream) {
+  NvtxRange nvtx_range("cn_potential_energy_dd");
   return energy_common(n, pos_mass, nullptr, pot, w_out, reinterpret_cast<cudaStream_t>(stream));
 }
 
 cn_status cn_force_host(int64_t n_i, const float* pos_i_host, int64_t n_j, const float* pos_mass_j_host, float eps2,
                         float* acc_host, float* pot_host, cn_stream stream) {
+  NvtxRange nvtx_range("cn_force_host");
   auto s = reinterpret_cast<cudaStream_t>(stream);
   if (n_i < 0 || n_j < 0) return fail(CN_ERR_INVALID_ARG, "n_i and n_j must be >= 0");
   if ((n_i > 0 && (!pos_i_host || !acc_host)) || (n_j > 0 && !pos_mass_j_host))
@@ -1385,6 +1733,7 @@ cn_status cn_force_host(int64_t n_i, const float* pos_i_host, int64_t n_j, const
 
 cn_status cn_force_host_f64(const double* xj, const double* mj, const double* xi, double eps2, double* a, int ni,
                             int nj) {
+  NvtxRange nvtx_range("cn_force_host_f64");
   if (ni < 0 || nj < 0) return fail(CN_ERR_INVALID_ARG, "ni and nj must be >= 0");
   if ((ni > 0 && (!xi || !a)) || (nj > 0 && (!xj || !mj))) return fail(CN_ERR_INVALID_ARG, "NULL host array");
   if (!std::isfinite(eps2) || eps2 < 0.0) return fail(CN_ERR_INVALID_ARG, "eps2 must be finite and >= 0");
@@ -1440,11 +1789,123 @@ cn_status cn_tune_set(int variant, int64_t n_i, int64_t n_j, const cn_tune* tune
     g_tune[key] = *tune;
   else
     g_tune.erase(key);
+  g_plan_gen.fetch_add(1, std::memory_order_acq_rel);
+  return CN_OK;
+}
+
+cn_status cn_tune_save(const char* path) {
+  if (!path) return fail(CN_ERR_INVALID_ARG, "path is NULL");
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail_cuda(e, "cudaGetDevice");
+  std::string name, arch;
+  int sms = 0;
+  cn_status st = device_identity(dev, &name, &arch, &sms);
+  if (st != CN_OK) return st;
+  std::string out = "{\"format\": \"cunbody-tune-1\", \"device\": \"";
+  for (char c : name) {
+    if (c == '"' || c == '\\') out.push_back('\\');
+    out.push_back(c);
+  }
+  out += "\", \"arch\": \"" + arch + "\", \"sms\": " + std::to_string(sms) + ", \"entries\": [";
+  {
+    std::lock_guard<std::mutex> lock(g_mu);
+    bool first = true;
+    for (const auto& kv : g_tune) {
+      if (std::get<0>(kv.first) != dev) continue;
+      const cn_tune& t = kv.second;
+      char line[512];
+      std::snprintf(line, sizeof(line),
+                    "%s\n  {\"variant\": \"%s\", \"n_i_class\": %d, \"n_j_class\": %d, \"i_per_thread\": %d, "
+                    "\"threads\": %d, \"j_tile\": %d, \"stages\": %d, \"ctas_per_sm\": %d, \"chunk_units\": %d, "
+                    "\"j_lanes\": %d}",
+                    first ? "" : ",", variant_name(std::get<1>(kv.first)), std::get<2>(kv.first), std::get<3>(kv.first),
+                    t.i_per_thread, t.threads, t.j_tile, t.stages, t.ctas_per_sm, t.chunk_units, t.j_lanes);
+      out += line;
+      first = false;
+    }
+  }
+  out += "\n]}\n";
+  FILE* f = std::fopen(path, "w");
+  if (!f) return fail(CN_ERR_INVALID_ARG, std::string("cannot write ") + path);
+  const bool ok = std::fwrite(out.data(), 1, out.size(), f) == out.size();
+  if (std::fclose(f) != 0 || !ok) return fail(CN_ERR_INVALID_ARG, std::string("writing ") + path + " failed");
+  return CN_OK;
+}
+
+cn_status cn_tune_load(const char* path, int32_t* n_loaded) {
+  if (n_loaded) *n_loaded = 0;
+  if (!path) return fail(CN_ERR_INVALID_ARG, "path is NULL");
+  FILE* f = std::fopen(path, "r");
+  if (!f) return fail(CN_ERR_INVALID_ARG, std::string("cannot read ") + path);
+  std::string text;
+  char buf[4096];
+  size_t got;
+  while ((got = std::fread(buf, 1, sizeof(buf), f)) > 0 && text.size() < (static_cast<size_t>(1) << 24))
+    text.append(buf, got);
+  std::fclose(f);
+  JsonValue root;
+  JsonReader rd{text};
+  if (!rd.value(&root) || root.kind != JsonValue::kObject) return fail(CN_ERR_INVALID_ARG, "tuning file: not a JSON object");
+  rd.skip();
+  if (rd.pos != text.size()) return fail(CN_ERR_INVALID_ARG, "tuning file: trailing characters");
+  const JsonValue* fmt = root.get("format");
+  const JsonValue* dname = root.get("device");
+  const JsonValue* darch = root.get("arch");
+  const JsonValue* entries = root.get("entries");
+  int64_t file_sms = 0;
+  if (!fmt || fmt->kind != JsonValue::kString || fmt->text != "cunbody-tune-1")
+    return fail(CN_ERR_INVALID_ARG, "tuning file: unknown format");
+  if (!dname || dname->kind != JsonValue::kString || !darch || darch->kind != JsonValue::kString ||
+      !json_int(root, "sms", 1, 1 << 20, &file_sms) || !entries || entries->kind != JsonValue::kArray)
+    return fail(CN_ERR_INVALID_ARG, "tuning file: device, arch, sms or entries missing");
+  struct Entry {
+    int variant, ci, cj;
+    cn_tune t;
+  };
+  std::vector<Entry> parsed;
+  for (const JsonValue& e : entries->items) {
+    if (e.kind != JsonValue::kObject) return fail(CN_ERR_INVALID_ARG, "tuning file: an entry is not an object");
+    const JsonValue* vn = e.get("variant");
+    const int variant = (vn && vn->kind == JsonValue::kString) ? variant_from_name(vn->text) : -1;
+    int64_t ci, cj, k, th, jt, stg, cps, ch, jl;
+    if (variant < 0 || !json_int(e, "n_i_class", 0, 62, &ci) || !json_int(e, "n_j_class", 0, 62, &cj) ||
+        !json_int(e, "i_per_thread", 0, 8, &k) || !json_int(e, "threads", 0, 1024, &th) ||
+        !json_int(e, "j_tile", 0, 4096, &jt) || !json_int(e, "stages", 0, 8, &stg) ||
+        !json_int(e, "ctas_per_sm", 0, 64, &cps) || !json_int(e, "chunk_units", 0, INT32_MAX, &ch) ||
+        !json_int(e, "j_lanes", 0, 32, &jl))
+      return fail(CN_ERR_INVALID_ARG, "tuning file: an entry has a missing or out-of-range field");
+    Entry en{variant, static_cast<int>(ci), static_cast<int>(cj),
+             cn_tune{static_cast<int32_t>(k), static_cast<int32_t>(th), static_cast<int32_t>(jt),
+                     static_cast<int32_t>(stg), static_cast<int32_t>(cps), static_cast<int32_t>(ch),
+                     static_cast<int32_t>(jl)}};
+    const cn_status st = check_tune(variant, en.t);
+    if (st != CN_OK) return st;
+    parsed.push_back(en);
+  }
+  int dev = 0;
+  cudaError_t ce = cudaGetDevice(&dev);
+  if (ce != cudaSuccess) return fail_cuda(ce, "cudaGetDevice");
+  std::string name, arch;
+  int sms = 0;
+  cn_status st = device_identity(dev, &name, &arch, &sms);
+  if (st != CN_OK) return st;
+  if (name != dname->text || arch != darch->text || sms != file_sms)
+    return fail(CN_ERR_UNSUPPORTED_DEVICE, "tuning file was written on " + dname->text + " (" + darch->text + ", " +
+                                               std::to_string(file_sms) + " SMs), this device is " + name + " (" +
+                                               arch + ", " + std::to_string(sms) + " SMs)");
+  {
+    std::lock_guard<std::mutex> lock(g_mu);
+    for (const Entry& en : parsed) g_tune[std::make_tuple(dev, en.variant, en.ci, en.cj)] = en.t;
+    g_plan_gen.fetch_add(1, std::memory_order_acq_rel);
+  }
+  if (n_loaded) *n_loaded = static_cast<int32_t>(parsed.size());
   return CN_OK;
 }
 
 cn_status cn_autotune(int variant, int64_t n_i, const float* pos_i, int64_t n_j, const float* pos_mass_j, float eps2,
                       void* acc_out, void* pot_out, int reps, cn_stream stream, cn_tune* best_out) {
+  NvtxRange nvtx_range("cn_autotune");
   if (variant < cn::kF32 || variant > cn::kDDPot) return fail(CN_ERR_INVALID_ARG, "cn_autotune covers the F32 and DD variants");
   if (n_i <= 0 || n_j <= 0) return fail(CN_ERR_INVALID_ARG, "autotuning needs n_i > 0 and n_j > 0");
   const bool dd = variant == cn::kDD || variant == cn::kDDPot;
@@ -1479,8 +1940,10 @@ cn_status cn_autotune(int variant, int64_t n_i, const float* pos_i, int64_t n_j,
         for (int64_t jt : {static_cast<int64_t>(512), static_cast<int64_t>(2048), round_up(std::max<int64_t>(n_j, 1), 8 * jl),
                            static_cast<int64_t>(4096)}) {
           if (jt % (8 * jl) || jt > 4096 || jt < 8 * jl) continue;
-          for (int k : {1, 2})  // one i-particle per lane group, or two (packed)
+          for (int k : {1, 2, 4, 8}) {  // i-particles per lane group (packed for K >= 2)
+            if (static_cast<int64_t>(k) * th / jl > 4 * std::max<int64_t>(n_i, 64)) continue;
             cands.push_back(cn_tune{k, th, static_cast<int32_t>(jt), jt >= n_j ? 1 : 3, 0, 0, jl});
+          }
         }
     }
   }
@@ -1561,6 +2024,7 @@ cn_status cn_autotune(int variant, int64_t n_i, const float* pos_i, int64_t n_j,
 cn_status cn_autotune_batched(int32_t n_clusters, const int64_t* offsets_host, const float* eps2_host,
                               const float* pos_mass, float* acc_out, float* pot_out, int reps, cn_stream stream,
                               cn_tune* best_out) {
+  NvtxRange nvtx_range("cn_autotune_batched");
   if (n_clusters <= 0 || !offsets_host) return fail(CN_ERR_INVALID_ARG, "empty ensemble");
   auto s = reinterpret_cast<cudaStream_t>(stream);
   if (reps < 1) reps = 1;
@@ -1575,38 +2039,43 @@ cn_status cn_autotune_batched(int32_t n_clusters, const int64_t* offsets_host, c
   float best_ms = 1e30f;
   cn_tune best{};
   cn_status result = CN_OK;
+  std::vector<cn_tune> cands;
   for (int k : ks)
     for (int th : ths)
       for (int jt : tiles)
-        for (int ch : chunks) {
-          if (result != CN_OK) break;
-          cn_tune t{k, th, jt, 4, 0, ch};
-          cn_batch_plan* plan = nullptr;
-          cn_status st = build_batch_plan(n_clusters, offsets_host, eps2_host, &t, pot_out != nullptr, &plan);
-          if (st != CN_OK) {
-            if (st == CN_ERR_INVALID_ARG) continue;
-            result = st;
-            break;
-          }
-          st = run_batched(plan, pos_mass, pos_mass, acc_out, pot_out, nullptr, 0, s);
-          if (st == CN_OK) {
-            cudaEventRecord(e0, s);
-            for (int r = 0; r < reps; ++r) run_batched(plan, pos_mass, pos_mass, acc_out, pot_out, nullptr, 0, s);
-            cudaEventRecord(e1, s);
-            if (cudaEventSynchronize(e1) == cudaSuccess) {
-              float ms = 0.f;
-              cudaEventElapsedTime(&ms, e0, e1);
-              if (ms < best_ms) {
-                best_ms = ms;
-                best = t;
-              }
-            } else {
-              st = fail(CN_ERR_CUDA, "autotune: event synchronisation failed");
-            }
-          }
-          cn_batch_plan_destroy(plan);
-          if (st != CN_OK) result = st;
+        for (int ch : chunks) cands.push_back(cn_tune{k, th, jt, 4, 0, ch, 1});
+  // split-j shapes: eight i-particles per lane group, small i-tiles
+  for (int jl : {2, 4, 8})
+    for (int jt : {256, 512})
+      for (int ch : {0, 8}) cands.push_back(cn_tune{8, 256, jt, 4, 0, ch, jl});
+  for (const cn_tune& t : cands) {
+    if (result != CN_OK) break;
+    cn_batch_plan* plan = nullptr;
+    cn_status st = build_batch_plan(n_clusters, offsets_host, eps2_host, &t, pot_out != nullptr, &plan);
+    if (st != CN_OK) {
+      if (st == CN_ERR_INVALID_ARG) continue;
+      result = st;
+      break;
+    }
+    st = run_batched(plan, pos_mass, pos_mass, acc_out, pot_out, nullptr, 0, s);
+    if (st == CN_OK) {
+      cudaEventRecord(e0, s);
+      for (int r = 0; r < reps; ++r) run_batched(plan, pos_mass, pos_mass, acc_out, pot_out, nullptr, 0, s);
+      cudaEventRecord(e1, s);
+      if (cudaEventSynchronize(e1) == cudaSuccess) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) {
+          best_ms = ms;
+          best = t;
         }
+      } else {
+        st = fail(CN_ERR_CUDA, "autotune: event synchronisation failed");
+      }
+    }
+    cn_batch_plan_destroy(plan);
+    if (st != CN_OK) result = st;
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (result != CN_OK) return result;
@@ -1618,6 +2087,7 @@ cn_status cn_autotune_batched(int32_t n_clusters, const int64_t* offsets_host, c
 }
 
 cn_status cn_get_device_status(cn_stream stream) {
+  NvtxRange nvtx_range("cn_get_device_status");
   auto s = reinterpret_cast<cudaStream_t>(stream);
   int dev = 0;
   DeviceInfo* d = nullptr;

@@ -106,9 +106,14 @@ cudaError_t launch_energy(int64_t n, const float4* pos_mass, const float* pot_f,
 inline cudaError_t prepare_kernel(const void* fn, size_t smem) {
   static std::mutex mu;
   static std::map<std::pair<int, const void*>, size_t> raised;
+  // this thread's last (device, kernel, limit): repeated launches skip the lock
+  thread_local int last_dev = -1;
+  thread_local const void* last_fn = nullptr;
+  thread_local size_t last_smem = 0;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
+  if (dev == last_dev && fn == last_fn && smem <= last_smem) return cudaSuccess;
   std::lock_guard<std::mutex> lock(mu);
   size_t& cur = raised[{dev, fn}];
   if (smem > cur) {
@@ -116,6 +121,9 @@ inline cudaError_t prepare_kernel(const void* fn, size_t smem) {
     if (e != cudaSuccess) return e;
     cur = smem;
   }
+  last_dev = dev;
+  last_fn = fn;
+  last_smem = cur;
   return cudaSuccess;
 }
 

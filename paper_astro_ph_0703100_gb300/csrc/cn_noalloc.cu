@@ -10,6 +10,8 @@
 #include "cunbody.h"
 #include "cn_kernels.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <map>
 #include <mutex>
 #include <string>
@@ -23,45 +25,74 @@ cn_status set_error(cn_status st, const std::string& msg);
 namespace {
 
 // The scratch: 32 MiB of device memory in the library image. Every GPU on
-// which this library's device code is loaded holds it until the process
-// exits, whether or not this entry point is ever called there.
+// which the library has been used holds it until the process exits,
+// whether or not this entry point is ever called there.
 constexpr size_t kStaticScratchBytes = static_cast<size_t>(32) << 20;
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
 std::mutex g_mu;
 std::map<int, void*> g_scratch_addr;  // device ordinal -> device address of g_static_scratch
 
-// Host code cannot use g_static_scratch directly: on the host that name is
-// a stand-in, not a device address. Look the address up once per device,
-// with that device current.
+// The address recorded for the current device by the device set-up below.
 cn_status scratch_address(void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cn::set_error(CN_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
   std::lock_guard<std::mutex> lock(g_mu);
   auto it = g_scratch_addr.find(dev);
-  if (it != g_scratch_addr.end()) {
-    *out = it->second;
-    return CN_OK;
-  }
-  void* p = nullptr;
-  e = cudaGetSymbolAddress(&p, g_static_scratch);
-  if (e != cudaSuccess || p == nullptr)
-    return cn::set_error(CN_ERR_CUDA, std::string("cudaGetSymbolAddress(static scratch): ") + cudaGetErrorString(e));
-  g_scratch_addr[dev] = p;
-  *out = p;
+  if (it == g_scratch_addr.end())
+    return cn::set_error(CN_ERR_CUDA, "cn_force_noalloc: the static scratch of this device was not set up");
+  *out = it->second;
   return CN_OK;
 }
 
 }  // namespace
 
+namespace cn {
+// Device set-up, run once per device by the library's first call there
+// (any entry point), with that device current. Host code cannot use
+// g_static_scratch directly: on the host that name is a stand-in, not a
+// device address, so the address is looked up here. With CUDA's lazy
+// module loading the lookup also loads this file's device module, which
+// is when the 32 MiB array is allocated on the device - inside the
+// library's first call on that device, never inside a cn_force_noalloc
+// call made after it.
+cudaError_t static_scratch_setup() {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  void* p = nullptr;
+  e = cudaGetSymbolAddress(&p, g_static_scratch);
+  if (e != cudaSuccess) return e;
+  if (p == nullptr) return cudaErrorInvalidSymbol;
+  std::lock_guard<std::mutex> lock(g_mu);
+  g_scratch_addr[dev] = p;
+  return cudaSuccess;
+}
+}  // namespace cn
+
+namespace {
+cn_status noalloc_call(int64_t n_i, const float* pos_i, int64_t n_j, const float* pos_mass_j, float eps2,
+                       float* acc_out, float* pot_out, cn_stream stream);
+}  // namespace
+
 extern "C" cn_status cn_force_noalloc(int64_t n_i, const float* pos_i, int64_t n_j, const float* pos_mass_j,
                                       float eps2, float* acc_out, float* pot_out, cn_stream stream) {
+  nvtxRangePushA("cn_force_noalloc");
+  const cn_status st = noalloc_call(n_i, pos_i, n_j, pos_mass_j, eps2, acc_out, pot_out, stream);
+  nvtxRangePop();
+  return st;
+}
+
+namespace {
+cn_status noalloc_call(int64_t n_i, const float* pos_i, int64_t n_j, const float* pos_mass_j, float eps2,
+                       float* acc_out, float* pot_out, cn_stream stream) {
   auto s = reinterpret_cast<cudaStream_t>(stream);
   void* scratch = nullptr;
   if (n_i > 0 && n_j > 0) {
-    // Scratch this problem needs under its launch shape; 0 means the
-    // arguments or the device are invalid, which the call below reports.
+    // Scratch this problem needs under its launch shape (this also sets the
+    // device up on a first call); 0 means the arguments or the device are
+    // invalid, which the call below reports.
     const size_t need = cn_workspace_bytes(pot_out ? CN_VARIANT_F32_POT : CN_VARIANT_F32, n_i, n_j);
     if (need > kStaticScratchBytes)
       return cn::set_error(CN_ERR_WORKSPACE,
@@ -79,3 +110,4 @@ extern "C" cn_status cn_force_noalloc(int64_t n_i, const float* pos_i, int64_t n
   return cn::force_f32_on_workspace(n_i, pos_i, n_j, pos_mass_j, eps2, acc_out, pot_out, scratch,
                                     scratch ? kStaticScratchBytes : 0, s);
 }
+}  // namespace

@@ -129,8 +129,11 @@ def test_batch_plan_validation(lib):
     assert lib.cn_tune_set(0, 1024, 1024, ctypes.byref(t)) == 1
     t = cn_tune(1, 128, 256, 4, 0, 0, 3)  # j_lanes must be a power of two
     assert lib.cn_tune_set(0, 1024, 1024, ctypes.byref(t)) == 1
-    t = cn_tune(4, 128, 256, 4, 0, 0, 8)  # j_lanes > 1 needs one or two i-particles per thread
-    assert lib.cn_tune_set(0, 1024, 1024, ctypes.byref(t)) == 1
+    t = cn_tune(4, 128, 256, 4, 0, 0, 8)  # per-i softening with j_lanes > 1: one or two i-particles per thread
+    assert lib.cn_tune_set(10, 1024, 1024, ctypes.byref(t)) == 1
+    assert lib.cn_tune_set(4, 1024, 1024, ctypes.byref(t)) == 1  # the adjoint with j_lanes > 1: exactly two
+    t = cn_tune(8, 128, 256, 4, 0, 0, 8)  # the compensated form takes no j_lanes
+    assert lib.cn_tune_set(2, 1024, 1024, ctypes.byref(t)) == 1
     t = cn_tune(1, 128, 96, 4, 0, 0, 8)  # j_tile not a multiple of 8 x j_lanes
     assert lib.cn_tune_set(0, 1024, 1024, ctypes.byref(t)) == 1
 
@@ -164,3 +167,32 @@ def test_binding_has_every_entry_point_by_name():
         names = re.findall(r"CN_API\s+[\w\s\*]+?\b(cn_\w+)\s*\(", f.read())
     assert len(names) >= 30
     assert [n for n in names if not hasattr(cn, n)] == []
+
+
+def test_tuning_file_is_checked_before_any_device_work(lib, tmp_path):
+    """cn_tune_load parses and validates the whole file on the host first:
+    a missing, malformed or foreign-format file, or an entry with an invalid
+    field, is refused with CN_ERR_INVALID_ARG and nothing is stored."""
+    n = ctypes.c_int32(7)
+    assert lib.cn_tune_load(str(tmp_path / "missing.json").encode(), ctypes.byref(n)) == 1
+    assert n.value == 0
+    assert lib.cn_tune_load(None, None) == 1
+    assert lib.cn_tune_save(None) == 1
+    head = '{"format": "cunbody-tune-1", "device": "X", "arch": "sm_103", "sms": 152, "entries": ['
+    entry = ('{"variant": "f32", "n_i_class": 17, "n_j_class": 17, "i_per_thread": %d, "threads": 256, '
+             '"j_tile": 1024, "stages": 4, "ctas_per_sm": 0, "chunk_units": 0, "j_lanes": 1}')
+    bad = {
+        "not json": "{not json",
+        "trailing": head + "]} x",
+        "format": '{"format": "other", "device": "X", "arch": "sm_103", "sms": 152, "entries": []}',
+        "no entries": '{"format": "cunbody-tune-1", "device": "X", "arch": "sm_103", "sms": 152}',
+        "unknown variant": head + entry.replace('"f32"', '"nope"') % 8 + "]}",
+        "k = 3": head + entry % 3 + "]}",
+        "missing field": head + '{"variant": "f32", "n_i_class": 17}' + "]}",
+        "deep": "[" * 40 + "]" * 40,
+    }
+    for name, text in bad.items():
+        p = tmp_path / (name.replace(" ", "_") + ".json")
+        p.write_text(text)
+        assert lib.cn_tune_load(str(p).encode(), ctypes.byref(n)) == 1, name
+        assert n.value == 0, name

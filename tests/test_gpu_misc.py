@@ -179,3 +179,39 @@ def test_concurrent_host_threads_on_separate_streams():
     assert cn.cn_get_device_status() == 0
     for a, r in zip(out, ref):
         assert torch.equal(a, r)
+
+
+def test_tuning_file_save_and_load(tmp_path):
+    """cn_tune_save writes this device's entries; after they are cleared,
+    cn_tune_load restores them, and a launch uses the restored shape. A
+    file naming another device is refused."""
+    import json
+
+    cn = lib()
+    torch = torch_cuda()
+    shape = {"i_per_thread": 4, "threads": 128, "j_tile": 512, "stages": 3, "ctas_per_sm": 0, "chunk_units": 0,
+             "j_lanes": 1}
+    cn.cn_tune_set("f32", 3000, 3000, shape)
+    path = tmp_path / "tune.json"
+    try:
+        cn.cn_tune_save(str(path))
+        doc = json.loads(path.read_text())
+        assert doc["format"] == "cunbody-tune-1" and doc["arch"] == "sm_103"
+        assert any(e["variant"] == "f32" and e["i_per_thread"] == 4 and e["threads"] == 128 for e in doc["entries"])
+        cn.cn_tune_set("f32", 3000, 3000, None)
+        assert cn.cn_tune_get("f32", 3000, 3000) != shape
+        assert cn.cn_tune_load(str(path)) == len(doc["entries"])
+        assert cn.cn_tune_get("f32", 3000, 3000) == shape
+        p = dev_tensor(synth.plummer(3000, 12))
+        acc, _ = cn.cn_force(p, p, 1e-3)
+        torch.cuda.synchronize()
+        ref, _ = oracle.force(synth.plummer(3000, 12), synth.plummer(3000, 12), 1e-3, potential=False)
+        assert e_max(acc.cpu().numpy(), ref) <= 1e-5
+        doc["device"] = "some other GPU"
+        other = tmp_path / "other.json"
+        other.write_text(json.dumps(doc))
+        with pytest.raises(cn.CunbodyError) as ei:
+            cn.cn_tune_load(str(other))
+        assert ei.value.code == "CN_ERR_UNSUPPORTED_DEVICE"
+    finally:
+        cn.cn_tune_set("f32", 3000, 3000, None)
