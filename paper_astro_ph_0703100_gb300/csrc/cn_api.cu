@@ -950,21 +950,24 @@ cn_status symmetric_common(int64_t n, const float* pos_mass, float eps2, float* 
   cudaError_t e = cn::occupancy_sym(p.k, guard, p.threads, smem, &occ, pot);
   if (e != cudaSuccess) return fail_cuda(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
   if (occ <= 0) return fail(CN_ERR_INVALID_ARG, "launch shape does not fit on one SM");
-  // Slots: one [T][n_pad] array (16 T n_pad bytes, ~16 N^2 / B) when it fits
-  // in kSymSlotCap, else bands of w tile rows: [T][w B] i-side and [w][n_pad]
-  // j-side slots plus FP64 running sums, ~32 w N + 32 N bytes. The tune's
-  // chunk_units, when set, fixes the rows per band.
+  // Slots: the j-side sums of every off-diagonal unit, one [T][n_pad] array
+  // (16 T n_pad bytes, ~16 N^2 / B, half of it written) when it fits in
+  // kSymSlotCap, else bands of w tile rows with [w][n_pad] j-side slots and
+  // FP64 running sums (~16 w N + 32 N bytes); plus the i-side segments,
+  // [CTAs + rows of the band][2][B] ((hi, lo) sums per CTA and row it
+  // touches). The tune's chunk_units, when set, fixes the rows per band.
   const int64_t n_pad = T * B;
   int64_t w = T;
   if (p.chunk_units > 0)
     w = std::min<int64_t>(p.chunk_units, T);
   else if (static_cast<double>(T) * static_cast<double>(n_pad) * 16.0 > static_cast<double>(kSymSlotCap))
-    w = std::max<int64_t>(1, std::min<int64_t>(T, static_cast<int64_t>(kSymSlotCap / (32 * static_cast<size_t>(n_pad)))));
+    w = std::max<int64_t>(1, std::min<int64_t>(T, static_cast<int64_t>(kSymSlotCap / (16 * static_cast<size_t>(n_pad)))));
   const bool banded = w < T;
-  const size_t islot_b = static_cast<size_t>(T) * static_cast<size_t>(banded ? w * B : n_pad) * 16;
-  const size_t jslot_b = banded ? align_up(static_cast<size_t>(w) * static_cast<size_t>(n_pad) * 16, 256) : 0;
+  const int64_t slots = static_cast<int64_t>(p.ctas_per_sm > 0 ? std::min(p.ctas_per_sm, occ) : occ) * d->sms;
+  const size_t jslot_b = align_up(static_cast<size_t>(w) * static_cast<size_t>(n_pad) * 16, 256);
+  const size_t seg_b = align_up(static_cast<size_t>(slots + w) * static_cast<size_t>(B) * 32, 256);  // (hi, lo)
   const size_t acc64_b = banded ? static_cast<size_t>(n) * 32 : 0;
-  const size_t need = align_up(islot_b, 256) + jslot_b + acc64_b;
+  const size_t need = jslot_b + seg_b + acc64_b;
   size_t free_b = 0, total_b = 0;
   if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && need > free_b + library_data_bytes(s))
     return fail(CN_ERR_WORKSPACE, "symmetric form: the slot arrays do not fit in device memory");
@@ -972,29 +975,27 @@ cn_status symmetric_common(int64_t n, const float* pos_mass, float eps2, float* 
   if ((st = library_workspace(s, kCtrlBytes, need, &ctrl, &data)) != CN_OK) return st;
   cn::SymArgs a{};
   a.pos = reinterpret_cast<const float4*>(pos_mass);
-  a.slots_i = reinterpret_cast<float4*>(data);
-  a.slots_j = banded ? reinterpret_cast<float4*>(data + align_up(islot_b, 256)) : a.slots_i;
+  a.slots_j = reinterpret_cast<float4*>(data);
+  a.slots_seg = reinterpret_cast<float4*>(data + jslot_b);
+  a.n_seg = slots + w;
   a.status = d->status;
   a.n = n;
   a.n_pad = n_pad;
-  a.ld_i = banded ? w * B : n_pad;
   a.n_tiles = static_cast<int32_t>(T);
   a.sub_tile = p.j_tile;
   a.stages = p.stages;
   a.eps2 = eps2;
   a.wait_ns = g_wait_ns.load();
   cn::SymMerge m{};
-  m.slots_i = a.slots_i;
+  m.slots_seg = a.slots_seg;
   m.slots_j = a.slots_j;
-  m.acc64 = banded ? reinterpret_cast<double*>(data + align_up(islot_b, 256) + jslot_b) : nullptr;
+  m.acc64 = banded ? reinterpret_cast<double*>(data + jslot_b + seg_b) : nullptr;
   m.acc_out = acc_out;
   m.pot_out = pot_out;
   m.n = n;
   m.n_pad = n_pad;
-  m.ld_i = a.ld_i;
   m.tile = static_cast<int32_t>(B);
   m.n_tiles = static_cast<int32_t>(T);
-  const int64_t slots = static_cast<int64_t>(p.ctas_per_sm > 0 ? std::min(p.ctas_per_sm, occ) : occ) * d->sms;
   auto row_start = [T](int64_t r) { return r * T - r * (r - 1) / 2; };  // first unit of tile row r
   for (int64_t r0 = 0; r0 < T; r0 += w) {
     const int64_t r1 = std::min(T, r0 + w);
@@ -1006,6 +1007,9 @@ cn_status symmetric_common(int64_t n, const float* pos_mass, float eps2, float* 
     m.first = r0 == 0;
     m.last = r1 == T;
     const int grid = static_cast<int>(std::min<int64_t>(slots, a.units));
+    m.unit_base = a.unit_base;
+    m.units = a.units;
+    m.grid = grid;
     if (log_enabled())
       std::fprintf(stderr,
                    "[cunbody] cn_force_symmetric: n %lld%s%s | K %d threads %d sub_tile %d stages %d | tile %lld "

@@ -13,13 +13,16 @@
 // every exchange reads a fixed register: 27 shuffles and 27 adds per batch)
 // and each warp's sums go to its own shared-memory row; at the end of the
 // unit the rows are added in warp order. Diagonal units (I = J) use the
-// one-sided loop. Every unit writes its i-side sums to slot (I, J) and its
-// j-side sums to slot (J, I) of a [tiles][n_pad] float4 array; a second
-// kernel adds the slots of each particle in partner order in FP64 - a
-// deterministic result with no atomics on data. That array grows as N^2 / B;
-// when it would be too large the rows of tiles are processed in bands, each
-// band merged into FP64 running sums in the same partner order, so the
-// result is bitwise the same.
+// one-sided loop. A CTA adds the i-side (tile I) sums of its consecutive
+// units of row I, by TwoSum, into one (hi, lo) slot pair per (CTA, row)
+// segment in a small buffer that stays in L2; each off-diagonal unit writes
+// its j-side sums to slot (J, I) of a
+// [tiles][n_pad] float4 array. A second kernel adds, per particle and in
+// FP64, the j-side slots in partner order and then the i-side segments of
+// its row in CTA order - a deterministic result with no atomics on data. The
+// j-side array grows as N^2 / (2B) (it stays in L2 up to N ~ 2^17 with 2048
+// particle tiles); when it would be too large the rows of tiles are
+// processed in bands, each band merged into FP64 running sums.
 //
 // The i-particles of a thread are held in pairs and the pair terms are
 // evaluated with packed f32x2 instructions (two i-particles per 64-bit
@@ -115,7 +118,20 @@ __global__ void __launch_bounds__(NTMAX, sym_min_blocks(NTMAX)) sym_kernel(const
   for (int64_t u = ub; u < ue; ++u) {
     int32_t I, J;
     unit_tiles(u, a.n_tiles, &I, &J);
+#ifdef CN_DEBUG_BOUNDS
+    // debug build: the unit must lie in the launch's band of the triangle and
+    // its segment slot inside the allocation; otherwise flag and stop
+    if (I < a.row0 || J < I || J >= a.n_tiles ||
+        static_cast<int64_t>(blockIdx.x) + (I - a.row0) >= a.n_seg) {
+      set_status(a.status, kStatusBadSchedule);
+      ctl[0] = 1;  // the exit below waits (bounded) for copies still in flight
+      break;
+    }
+#endif
     const bool diag = (I == J);
+    // the first unit of this CTA's segment of row I (a row starts with its
+    // diagonal unit), where the segment's running sums start
+    const bool seg_first = (u == ub) || diag;
     if (I != cur_I) {
 #pragma unroll
       for (int p = 0; p < P; ++p)
@@ -311,13 +327,46 @@ __global__ void __launch_bounds__(NTMAX, sym_min_blocks(NTMAX)) sym_kernel(const
       }
       ++consumed;
     }
-    // ---- end of the unit: i-side sums to slot (I, J), j-side to slot (J, I)
+    // ---- end of the unit: the unit's i-side sums are folded by TwoSum into
+    // the segment's (hi, lo) running sums (each thread reads back only what
+    // it wrote; the buffer is small and stays in L2); j-side sums to slot
+    // (J, I)
     __syncthreads();
+    {
+      float4* __restrict__ seg_hi =
+          a.slots_seg + (static_cast<size_t>(blockIdx.x) + static_cast<size_t>(I - a.row0)) * 2 * B;
+      float4* __restrict__ seg_lo = seg_hi + B;
+      // all loads first (one memory latency per unit), then the sums, then
+      // the stores
+      float4 h[K], l[K];
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-      const int64_t p = static_cast<int64_t>(I - a.row0) * B + k * NT + tid;
-      a.slots_i[static_cast<size_t>(J) * a.ld_i + p] = make_float4(
-          half(acc[k >> 1][0], k), half(acc[k >> 1][1], k), half(acc[k >> 1][2], k), POT ? half(pacc[k >> 1], k) : 0.f);
+      for (int k = 0; k < K; ++k) {
+        h[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        l[k] = h[k];
+        if (!seg_first) {
+          h[k] = seg_hi[k * NT + tid];
+          l[k] = seg_lo[k * NT + tid];
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const float v[4] = {half(acc[k >> 1][0], k), half(acc[k >> 1][1], k), half(acc[k >> 1][2], k),
+                            POT ? half(pacc[k >> 1], k) : 0.f};
+        float e[4];
+        two_sum(h[k].x, v[0], h[k].x, e[0]);
+        two_sum(h[k].y, v[1], h[k].y, e[1]);
+        two_sum(h[k].z, v[2], h[k].z, e[2]);
+        two_sum(h[k].w, v[3], h[k].w, e[3]);
+        l[k].x = __fadd_rn(l[k].x, e[0]);
+        l[k].y = __fadd_rn(l[k].y, e[1]);
+        l[k].z = __fadd_rn(l[k].z, e[2]);
+        l[k].w = __fadd_rn(l[k].w, e[3]);
+      }
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        seg_hi[k * NT + tid] = h[k];
+        seg_lo[k * NT + tid] = l[k];
+      }
     }
     if (!diag) {
       for (int jl = tid; jl < B; jl += NT) {
@@ -370,15 +419,23 @@ __global__ void sym_merge_kernel(const SymMerge m) {
     sz += v.z;
     if constexpr (POT) sp += v.w;
   }
-  // i-side: units (P, Q) with Q >= P, when P is one of the band's rows
+  // i-side: the segments of row P (when it is one of the band's rows), in
+  // CTA order: CTA c of the band launch holds units [c U / G, (c + 1) U / G)
   if (P >= m.row0 && P < m.row1) {
-    const int64_t pl = p - static_cast<int64_t>(m.row0) * m.tile;
-    for (int32_t q = P; q < m.n_tiles; ++q) {
-      const float4 v = __ldcs(m.slots_i + static_cast<size_t>(q) * m.ld_i + pl);
-      sx += v.x;
-      sy += v.y;
-      sz += v.z;
-      if constexpr (POT) sp += v.w;
+    const int64_t T = m.n_tiles;
+    const int64_t r0 = static_cast<int64_t>(P) * T - static_cast<int64_t>(P) * (P - 1) / 2 - m.unit_base;
+    const int64_t r1 = r0 + (T - P);  // one past the row's last unit
+    const int64_t c0 = ((r0 + 1) * m.grid - 1) / m.units;
+    const int64_t c1 = (r1 * m.grid - 1) / m.units;
+    const int64_t pl = p - static_cast<int64_t>(P) * m.tile;
+    for (int64_t c = c0; c <= c1; ++c) {
+      const float4* seg = m.slots_seg + (static_cast<size_t>(c) + static_cast<size_t>(P - m.row0)) * 2 * m.tile;
+      const float4 h = __ldcs(seg + pl);
+      const float4 l = __ldcs(seg + m.tile + pl);
+      sx += static_cast<double>(h.x) + static_cast<double>(l.x);
+      sy += static_cast<double>(h.y) + static_cast<double>(l.y);
+      sz += static_cast<double>(h.z) + static_cast<double>(l.z);
+      if constexpr (POT) sp += static_cast<double>(h.w) + static_cast<double>(l.w);
     }
   }
   if (m.last) {

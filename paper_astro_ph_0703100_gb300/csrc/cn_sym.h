@@ -8,19 +8,21 @@ namespace cn {
 
 // One launch covers the tile rows I in [row0, row0 + band) of the upper
 // triangle of tile pairs (I <= J), i.e. units unit_base .. unit_base + units
-// - 1 of the row-major numbering. Unit (I, J) writes its i-side sums (tile
-// I, partner J) to slots_i[J * ld_i + p - row0 * tile] and its j-side sums
-// (tile J, partner I) to slots_j[(I - row0) * n_pad + p]. With one band
-// covering every row, slots_i == slots_j and ld_i == n_pad: one
-// [n_tiles][n_pad] array with slot (tile P, partner Q) at Q * n_pad + p.
+// - 1 of the row-major numbering, split into equal contiguous ranges over
+// the grid's CTAs. A CTA adds the i-side sums (tile I) of each of its units
+// of one row, by TwoSum, into one (hi, lo) slot pair per (CTA, row) segment:
+// slots_seg[(c + I - row0) * 2 tile + {0, tile} + p - I * tile] for CTA c (c +
+// I - row0 is unique per segment, since along the unit sequence neither the
+// CTA nor the row index decreases). Unit (I, J), I < J, writes its j-side
+// sums (tile J, partner I) to slots_j[(I - row0) * n_pad + p].
 struct SymArgs {
   const float4* pos;  // [n] (x, y, z, m)
-  float4* slots_i;
+  float4* slots_seg;  // [n_seg][2][tile] (hi, lo), n_seg >= grid + band rows
+  int64_t n_seg;
   float4* slots_j;
   int* status;
   int64_t n;
   int64_t n_pad;      // n_tiles * tile
-  int64_t ld_i;       // row stride of slots_i (particles of the band's tiles)
   int64_t unit_base;  // first unit of the launch (row-major over I <= J)
   int64_t units;      // units of the launch
   int32_t n_tiles;
@@ -31,20 +33,24 @@ struct SymArgs {
   uint64_t wait_ns;
 };
 
-// Per-particle merge of one band: adds, in FP64 and in ascending partner
-// order, the band's j-side slots (x, y, z and the potential in w) (partners I in [row0, row1), I < P) and,
-// for particles of the band's own tiles, their i-side slots (partners
-// Q >= P) to the running sums (acc64, or zero for the first band); the last
-// band writes the FP32 accelerations, the others store the FP64 sums.
+// Per-particle merge of one band: adds, in FP64, the band's j-side slots (x,
+// y, z and the potential in w) in ascending partner order (partners I in
+// [row0, row1), I < P) and, for particles of the band's own tiles, the
+// i-side segments of their row in CTA order, to the running sums (acc64, or
+// zero for the first band); the last band writes the FP32 accelerations,
+// the others store the FP64 sums. The segments of row P are those of the
+// CTAs whose unit ranges meet [row_start(P), row_start(P + 1)).
 struct SymMerge {
-  const float4* slots_i;
+  const float4* slots_seg;
   const float4* slots_j;
   double* acc64;     // [n][4] (acceleration, potential), NULL with a single band
   float* acc_out;    // [n][3]
   float* pot_out;    // [n] or NULL
   int64_t n;
   int64_t n_pad;
-  int64_t ld_i;
+  int64_t unit_base;  // the band launch's schedule: first unit, units, CTAs
+  int64_t units;
+  int64_t grid;
   int32_t tile;
   int32_t n_tiles;
   int32_t row0;

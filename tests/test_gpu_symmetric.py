@@ -3,8 +3,9 @@
 The symmetric form computes the same accelerations as the paper's kernel
 (Eq. 1 with the i set equal to the j set), so it is held to the same
 per-particle bound E_max <= 1e-5 as the plain FP32 form. Its partial sums
-are per (tile, partner tile) in FP32, merged in FP64 in partner order, so
-repeated calls with one launch shape are bitwise equal.
+are FP32 (the j-side per tile pair, the i-side per CTA and tile row),
+merged in FP64 in a fixed order, so repeated calls with one launch shape
+are bitwise equal.
 """
 
 import numpy as np
@@ -114,9 +115,12 @@ def test_symmetric_deterministic_and_matches_plain_form():
 
 
 @pytest.mark.parametrize("rows", [1, 2, 3])
-def test_symmetric_bands_bitwise_equal_one_band(rows):
-    """Banded evaluation (chunk_units = tile rows per band) merges partners in
-    the same order in FP64, so it reproduces the one-band result bit for bit."""
+def test_symmetric_bands_reproducible_and_close_to_one_band(rows):
+    """Banded evaluation (chunk_units = tile rows per band): each launch
+    configuration gives bit-identical results when repeated; the band
+    launches cut the tile rows into other CTA segments than the one-band
+    launch, so the two differ only by the FP32 rounding of those segment
+    sums (and both match the oracle)."""
     cn = lib()
     torch = torch_cuda()
     n = 5000
@@ -126,13 +130,19 @@ def test_symmetric_bands_bitwise_equal_one_band(rows):
     cn.cn_tune_set("symmetric", n, n, shape)
     try:
         one, pone = cn.cn_force_symmetric(d, 1e-4, potential=True)
+        one2, pone2 = cn.cn_force_symmetric(d, 1e-4, potential=True)
         cn.cn_tune_set("symmetric", n, n, dict(shape, chunk_units=rows))
         banded, pband = cn.cn_force_symmetric(d, 1e-4, potential=True)
+        banded2, pband2 = cn.cn_force_symmetric(d, 1e-4, potential=True)
         torch.cuda.synchronize()
     finally:
         cn.cn_tune_set("symmetric", n, n, None)
     assert cn.cn_get_device_status() == 0
-    assert torch.equal(one, banded) and torch.equal(pone, pband)
+    assert torch.equal(one, one2) and torch.equal(pone, pone2)
+    assert torch.equal(banded, banded2) and torch.equal(pband, pband2)
+    a1 = one.cpu().numpy().astype(np.float64)
+    assert e_max(banded.cpu().numpy(), a1) <= 1e-6
+    assert rel_pot_err(pband.cpu().numpy(), pone.cpu().numpy()) <= 1e-6
     ref, rpot = oracle.force(p, p, 1e-4)
     assert e_max(banded.cpu().numpy(), ref) <= TOL
     assert rel_pot_err(pband.cpu().numpy(), rpot) <= TOL
