@@ -102,12 +102,14 @@ class CunbodyError(RuntimeError):
 
 
 def load(path: str | None = None):
-    """Load libcunbody.so (and declare its signatures); raises if it is missing."""
+    """Load libcunbody.so (and declare its signatures); raises if it is missing.
+    CUNBODY_LIB, when set, names another build of the library to load (for
+    instance the bounds-checked libcunbody_debug.so)."""
     global _lib
     with _lock:
         if _lib is not None:
             return _lib
-        path = path or LIB_PATH
+        path = path or os.environ.get("CUNBODY_LIB") or LIB_PATH
         if not os.path.exists(path):
             raise RuntimeError(
                 f"libcunbody.so is not built ({path} missing): run "

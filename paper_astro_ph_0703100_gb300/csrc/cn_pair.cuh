@@ -1392,6 +1392,39 @@ struct JerkX2Policy {
   }
 };
 
+// ------------------------------------------------------------------ debug checks
+#ifdef CN_DEBUG_BOUNDS
+// Debug build only (-DCN_DEBUG_BOUNDS): every tile the schedule reaches is
+// checked against the unit numbering and the sizes the launch was planned
+// with. A violation sets kStatusBadSchedule in the device status word,
+// switches the CTA to the abort path (no more copies, waits or pair work)
+// and empties the tile, so that nothing outside the buffers is touched.
+__device__ __forceinline__ void bad_schedule(const PairArgs& a, volatile int* ctl) {
+  set_status(a.status, kStatusBadSchedule);
+  ctl[0] = 1;
+}
+
+// tile index tc as returned by the unit lookup: inside the table?
+__device__ __forceinline__ int32_t checked_tile_index(const PairArgs& a, int32_t tc, volatile int* ctl) {
+  if (tc >= 0 && tc < a.n_tiles) return tc;
+  bad_schedule(a, ctl);
+  return 0;
+}
+
+// descriptor td must hold unit u, fit the i-tile and lie inside the i and j
+// arrays; j_tile records per j-tile
+__device__ __forceinline__ void check_tile(const PairArgs& a, TileDesc& td, int64_t u, int IT, int T, volatile int* ctl) {
+  const bool ok = td.njt >= 1 && td.unit0 <= u && u < td.unit0 + td.njt && td.ni >= 0 && td.ni <= IT && td.i0 >= 0 &&
+                  td.i0 + td.ni <= a.n_i && td.nj >= 1 && td.j0 >= 0 && td.j0 + td.nj <= a.n_j &&
+                  td.njt == (td.nj + T - 1) / T;
+  if (ok) return;
+  bad_schedule(a, ctl);
+  td.ni = 0;
+  td.unit0 = u;
+  if (td.njt < 1) td.njt = 1;
+}
+#endif
+
 // ------------------------------------------------------------------ kernel
 // Register budget per policy: Policy::kMinBlocks 256-thread CTAs must fit
 // on an SM (2: up to 128 registers per thread; 1: up to 255).
@@ -1450,7 +1483,13 @@ __global__ void __launch_bounds__(256, Policy::kMinBlocks) pair_kernel(const __g
     const int64_t ue = sc.end(q);
     if (ub < ue) {
       int32_t tc = tile_of_unit<BATCHED>(a, ub);
+#ifdef CN_DEBUG_BOUNDS
+      tc = checked_tile_index(a, tc, ctl);
+#endif
       TileDesc td = tile_at<BATCHED>(a, tc, IT);
+#ifdef CN_DEBUG_BOUNDS
+      check_tile(a, td, ub, IT, T, ctl);
+#endif
       int64_t jt = ub - td.unit0;
       // producer cursor (meaningful in thread 0 only)
       int32_t tp = tc;
@@ -1472,6 +1511,12 @@ __global__ void __launch_bounds__(256, Policy::kMinBlocks) pair_kernel(const __g
             const int64_t jb = jtp * T;
             const int64_t left = tdp.nj - jb;
             const int cnt = static_cast<int>(left < T ? left : T);
+#ifdef CN_DEBUG_BOUNDS
+            if (tp >= a.n_tiles || cnt < 1 || tdp.j0 + jb < 0 || tdp.j0 + jb + cnt > a.n_j) {
+              bad_schedule(a, ctl);
+              break;
+            }
+#endif
             float4* dst = ring + static_cast<size_t>(slot) * T * JR;
             for (int z = cnt; z < T; ++z) {  // zero-mass (and zero-weight) padding of a short tile
               dst[z] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -1524,8 +1569,14 @@ __global__ void __launch_bounds__(256, Policy::kMinBlocks) pair_kernel(const __g
         if (jt == td.njt || uc + 1 == ue) {
           // ---- end of a segment: write the tile or its partial
           if constexpr (SJ) acc.reduce_lanes(JL);
-          const int64_t qf = sc.chunk_of(td.unit0);
-          const int64_t ql = sc.chunk_of(td.unit0 + td.njt - 1);
+          int64_t qf = sc.chunk_of(td.unit0);
+          int64_t ql = sc.chunk_of(td.unit0 + td.njt - 1);
+#ifdef CN_DEBUG_BOUNDS
+          if (qf < 0 || ql >= sc.Q || qf > q || q > ql) {
+            bad_schedule(a, ctl);
+            qf = ql = q;  // the tile is then written by this chunk alone
+          }
+#endif
           if (qf == ql) {
 #pragma unroll
             for (int k = 0; k < K; ++k) {
@@ -1585,6 +1636,13 @@ __global__ void __launch_bounds__(256, Policy::kMinBlocks) pair_kernel(const __g
             ++tc;
             jt = 0;
             if (tc < a.n_tiles) td = tile_at<BATCHED>(a, tc, IT);
+#ifdef CN_DEBUG_BOUNDS
+            if (uc + 1 < ue) {
+              tc = checked_tile_index(a, tc, ctl);
+              td = tile_at<BATCHED>(a, tc, IT);
+              check_tile(a, td, uc + 1, IT, T, ctl);
+            }
+#endif
           }
         }
       }
