@@ -40,6 +40,19 @@
  *    a CUDA graph (CN_ERR_WORKSPACE): make one call on that stream before
  *    capturing, or use the *_ws forms.
  *  - Thread safety: concurrent calls are safe on different streams.
+ *  - Kernels are launched with programmatic stream serialization
+ *    (programmatic dependent launch): a library kernel may be scheduled
+ *    while the previous kernel of the stream is still running, and it waits
+ *    for that kernel to complete before it touches global memory, so stream
+ *    order holds for the data. A kernel of the caller's that follows a
+ *    library call in the stream and is itself launched with that attribute
+ *    must wait in the same way (cudaGridDependencySynchronize) before it
+ *    reads the library's outputs.
+ *  - Environment: CN_PDL=0 launches in plain stream order and CN_LOG=1
+ *    prints each new launch plan (variant, shape, grid, split tiles) to
+ *    stderr (both read once per process); CN_FAULT_INJECT, a comma list of
+ *    alloc, launch and capture, makes those host steps fail as if the CUDA
+ *    call had failed (read at every call; for testing error paths).
  */
 #ifndef CUNBODY_H
 #define CUNBODY_H

@@ -52,7 +52,7 @@ cudaError_t launch_adjoint(const PairArgs& a, const Plan& p, bool guard, int gri
   cudaError_t e = prepare_kernel(f, smem);
   if (e != cudaSuccess) return e;
   void* args[] = {const_cast<PairArgs*>(&a)};
-  return cudaLaunchKernel(f, dim3(grid), dim3(p.threads), args, smem, s);
+  return launch_pdl(f, dim3(grid), dim3(p.threads), args, smem, s);
 }
 
 cudaError_t launch_pack_w(const float* w, float4* wrec, int64_t n, cudaStream_t s) {

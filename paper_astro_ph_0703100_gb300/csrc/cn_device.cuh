@@ -106,6 +106,17 @@ __device__ __forceinline__ void ds_accumulate(float& hi, float& lo, float x) {
   lo = __fadd_rn(lo, e);
 }
 
+// Programmatic dependent launch (PTX griddepcontrol, sm_90 and later).
+// grid_dependency_wait: returns once the grids this one depends on in its
+// stream have completed and their memory writes are visible (immediately
+// when the kernel was launched without programmatic serialization).
+// grid_launch_dependents: lets the stream's next grid, if it was launched
+// with programmatic serialization, be scheduled before this one ends.
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 __device__ __forceinline__ void set_status(int* status, int bits) {
   if (status) atomicOr(status, bits);
 }

@@ -86,7 +86,7 @@ cudaError_t launch_f32(const PairArgs& a, const Plan& p, bool pot, bool guard, b
   cudaError_t e = prepare_kernel(f, smem);
   if (e != cudaSuccess) return e;
   void* args[] = {const_cast<PairArgs*>(&a)};
-  return cudaLaunchKernel(f, dim3(grid), dim3(p.threads), args, smem, s);
+  return launch_pdl(f, dim3(grid), dim3(p.threads), args, smem, s);
 }
 
 }  // namespace cn

@@ -55,7 +55,7 @@ cudaError_t launch_jerk(const PairArgs& a, const Plan& p, bool pot, bool guard, 
   cudaError_t e = prepare_kernel(f, smem);
   if (e != cudaSuccess) return e;
   void* args[] = {const_cast<PairArgs*>(&a)};
-  return cudaLaunchKernel(f, dim3(grid), dim3(p.threads), args, smem, s);
+  return launch_pdl(f, dim3(grid), dim3(p.threads), args, smem, s);
 }
 
 }  // namespace cn

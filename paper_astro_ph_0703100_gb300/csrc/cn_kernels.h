@@ -4,6 +4,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <cstdlib>
 #include <cuda_runtime.h>
 
 #include <map>
@@ -101,6 +102,36 @@ cudaError_t launch_jerk(const PairArgs& a, const Plan& p, bool pot, bool guard, 
 cudaError_t occupancy_jerk(const Plan& p, bool pot, bool guard, size_t smem, int* ctas);
 cudaError_t launch_energy(int64_t n, const float4* pos_mass, const float* pot_f, const double* pot_d,
                           double* partials, int* counter, double* w_out, cudaStream_t s);
+
+// Launches a kernel with programmatic stream serialization allowed
+// (programmatic dependent launch): the GPU may schedule it while the
+// previous kernel of the stream is still running, which removes most of the
+// gap between back-to-back launches. Every kernel launched this way calls
+// grid_dependency_wait() before its first global memory access, so stream
+// order still holds for the data. CN_PDL=0 in the environment (read once)
+// launches in plain stream order instead.
+inline bool pdl_enabled() {
+  static const bool on = [] {
+    const char* v = std::getenv("CN_PDL");
+    return !(v && v[0] == '0');
+  }();
+  return on;
+}
+
+inline cudaError_t launch_pdl(const void* fn, dim3 grid, dim3 block, void** args, size_t smem, cudaStream_t s) {
+  if (!pdl_enabled()) return cudaLaunchKernel(fn, grid, block, args, smem, s);
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelExC(&cfg, fn, args);
+}
 
 // Raises a kernel's dynamic shared-memory limit once per (device, kernel).
 inline cudaError_t prepare_kernel(const void* fn, size_t smem) {

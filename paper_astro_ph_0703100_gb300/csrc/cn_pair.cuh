@@ -1458,6 +1458,10 @@ __global__ void __launch_bounds__(256, Policy::kMinBlocks) pair_kernel(const __g
     mbar_init_fence();
   }
   __syncthreads();
+  // Up to here only shared memory was touched; the previous kernel of the
+  // stream may still be writing global memory until the wait returns.
+  grid_dependency_wait();
+  grid_launch_dependents();
 
   const Sched sc{a.total_units, a.n_chunks, a.chunk_units};
   const bool dynamic = a.chunk_units > 0;

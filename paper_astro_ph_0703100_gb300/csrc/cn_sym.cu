@@ -97,6 +97,11 @@ __global__ void __launch_bounds__(NTMAX, sym_min_blocks(NTMAX)) sym_kernel(const
     mbar_init_fence();
   }
   __syncthreads();
+  // only shared memory so far: global memory after the previous kernel ends.
+  // No early grid_launch_dependents() here: the merge kernel's CTAs would
+  // then be placed on the SMs beside this one and wait there, which cost
+  // 1.1% at N = 131072; the implicit trigger at exit is enough.
+  grid_dependency_wait();
 
   const int64_t U = a.units;
   const int64_t G = gridDim.x;
@@ -400,6 +405,8 @@ __global__ void __launch_bounds__(NTMAX, sym_min_blocks(NTMAX)) sym_kernel(const
 // skipped, since FP64 additions are the merge's slow part on this GPU.
 template <bool POT>
 __global__ void sym_merge_kernel(const SymMerge m) {
+  grid_dependency_wait();  // the slots are complete once the symmetric kernel has ended
+  grid_launch_dependents();
   const int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (p >= m.n) return;
   double sx = 0.0, sy = 0.0, sz = 0.0, sp = 0.0;
@@ -497,15 +504,14 @@ cudaError_t launch_sym(const SymArgs& a, const SymMerge& m, int k, bool guard, i
   cudaError_t e = prepare_kernel(f, smem);
   if (e != cudaSuccess) return e;
   void* args[] = {const_cast<SymArgs*>(&a)};
-  e = cudaLaunchKernel(f, dim3(grid), dim3(threads), args, smem, s);
+  e = launch_pdl(f, dim3(grid), dim3(threads), args, smem, s);
   if (e != cudaSuccess) return e;
   const int mt = 256;
   const int64_t mb = (m.n + mt - 1) / mt;
-  if (pot)
-    sym_merge_kernel<true><<<static_cast<unsigned>(mb), mt, 0, s>>>(m);
-  else
-    sym_merge_kernel<false><<<static_cast<unsigned>(mb), mt, 0, s>>>(m);
-  return cudaGetLastError();
+  void* margs[] = {const_cast<SymMerge*>(&m)};
+  const void* mf = pot ? reinterpret_cast<const void*>(&sym_merge_kernel<true>)
+                       : reinterpret_cast<const void*>(&sym_merge_kernel<false>);
+  return launch_pdl(mf, dim3(static_cast<unsigned>(mb)), dim3(mt), margs, 0, s);
 }
 
 }  // namespace cn
