@@ -169,7 +169,7 @@ def gpu_selector(torch, device):
 # ------------------------------------------------------------------ profile evidence
 
 KERNEL_SOURCES = ("cn_pair.cuh", "cn_device.cuh", "cn_kernels.h", "cn_force_f32.cu")
-PROFILE_F32 = os.path.join(ROOT, "profiles", "pair_f32_n131072.md")
+PROFILE_F32 = os.path.join(ROOT, "profiles", "pair_f32_n131072.json")
 
 
 def kernel_source_hash() -> str:
@@ -183,20 +183,17 @@ def kernel_source_hash() -> str:
 
 
 def profiled_traffic(shape: dict):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the kernel as it is now and in this launch shape; else None."""
+    """DRAM bytes per launch from the committed ncu record of the headline
+    kernel (profiles/pair_f32_n131072.json), if it was taken on the kernel
+    sources as they are now and in this launch shape; else None."""
     try:
-        kv = {}
         with open(PROFILE_F32) as f:
-            for line in f:
-                if ":" in line and line.startswith("- `"):
-                    k, v = line[3:].split("`", 1)[0].split(":", 1)
-                    kv[k.strip()] = v.strip()
-        same_shape = kv.get("launch_shape") == "{},{},{},{}".format(
-            shape["i_per_thread"], shape["threads"], shape["j_tile"], shape["stages"])
-        if kv.get("source_sha256") == kernel_source_hash() and same_shape:
-            return float(kv["dram_bytes_per_launch"])
-    except (OSError, KeyError, ValueError):
+            rec = json.load(f)
+        same_shape = rec["launch_shape"] == [shape["i_per_thread"], shape["threads"], shape["j_tile"],
+                                             shape["stages"]]
+        if rec["source_sha256"] == kernel_source_hash() and same_shape:
+            return float(rec["dram_bytes_per_launch"])
+    except (OSError, KeyError, ValueError, TypeError):
         pass
     return None
 
@@ -376,8 +373,11 @@ def run_ours(args):
             "unit": UNIT,
             "ms_per_step": 1e3 * dd_mean_s,
             "frac_of_fp32_peak": dd_rate / peak,
+            "frac_of_own_roofline": dd_rate / (peak * FP32_LANE_OPS_PER_PAIR / DD_LANE_OPS_PER_PAIR),
+            "own_roofline_basis": f"{DD_LANE_OPS_PER_PAIR} FP32 lane operations per pair (packed f32x2 issue)",
+            "launch_shape": tuned_dd or cn.cn_tune_get("dd", n, n),
             "steps": args.dd_steps,
-            "dtype": "f32 pairs, double-single accumulation, f64 output",
+            "dtype": "f32 pair arithmetic with its roundings recovered, TwoSum (hi, lo) sums, f64 tile folds and output",
         },
         "e2e": {
             "value": aggregate_rate(pairs * e2e_steps, world, e2e_s),
@@ -397,17 +397,113 @@ def run_ours(args):
     return line
 
 
+# Back-to-back cn_force calls from C on device buffers: the host cost of a
+# call without Python (the binding adds its own on top), the wall time per
+# call of a long run of calls, and the device time per evaluation when the
+# same calls are replayed from a CUDA graph.
+C_TIMING = r"""
+#define _POSIX_C_SOURCE 200112L
+#include <stdio.h>
+#include <stdlib.h>
+#include <time.h>
+#include <cuda_runtime.h>
+#include "cunbody.h"
+static double now(void) { struct timespec t; clock_gettime(CLOCK_MONOTONIC, &t); return t.tv_sec + 1e-9 * t.tv_nsec; }
+int main(int argc, char **argv) {
+    const char *path = argv[1];
+    const int n = atoi(argv[2]), calls = atoi(argv[3]), pot = atoi(argv[4]);
+    const float eps2 = (float)atof(argv[5]);
+    float *h = malloc((size_t)n * 16);
+    FILE *f = fopen(path, "rb");
+    if (!f || fread(h, 16, (size_t)n, f) != (size_t)n) return 2;
+    fclose(f);
+    float *dp, *da, *dq;
+    if (cudaMalloc((void **)&dp, (size_t)n * 16) || cudaMalloc((void **)&da, (size_t)n * 12) ||
+        cudaMalloc((void **)&dq, (size_t)n * 4)) return 3;
+    cudaMemcpy(dp, h, (size_t)n * 16, cudaMemcpyHostToDevice);
+    cudaStream_t s;
+    cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    cn_stream cs = (cn_stream)s;
+    for (int r = 0; r < 50; ++r)
+        if (cn_force(n, dp, n, dp, eps2, da, pot ? dq : NULL, cs) != CN_OK) return 4;
+    cudaStreamSynchronize(s);
+    double t0 = now();
+    for (int r = 0; r < calls; ++r) cn_force(n, dp, n, dp, eps2, da, pot ? dq : NULL, cs);
+    double t1 = now();
+    cudaStreamSynchronize(s);
+    double t2 = now();
+    cudaGraph_t g;
+    cudaGraphExec_t ge;
+    cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    for (int r = 0; r < 100; ++r) cn_force(n, dp, n, dp, eps2, da, pot ? dq : NULL, cs);
+    cudaStreamEndCapture(s, &g);
+    cudaGraphInstantiate(&ge, g, 0);
+    cudaGraphLaunch(ge, s);
+    cudaStreamSynchronize(s);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    for (int k = 0; k < 5; ++k) {
+        float ms;
+        cudaEventRecord(e0, s);
+        cudaGraphLaunch(ge, s);
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) best = ms;
+    }
+    if (cudaGetLastError() != cudaSuccess) return 5;
+    printf("%.4f %.4f %.4f\n", 1e6 * (t1 - t0) / calls, 1e6 * (t2 - t0) / calls, 1e3 * best / 100);
+    return 0;
+}
+"""
+
+
+def c_call_timing(p, eps2, potential, calls=2000):
+    """Host and wall microseconds per cn_force call from C, and device
+    microseconds per evaluation (graph replay); None if no C toolchain."""
+    import shutil
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    cuda = os.environ.get("CUDA_HOME", "/usr/local/cuda")
+    if not cc or not os.path.exists(os.path.join(cuda, "include", "cuda_runtime.h")):
+        return None
+    lib_dir = os.path.join(ROOT, "paper_astro_ph_0703100_gb300")
+    with tempfile.TemporaryDirectory() as d:
+        src, exe, rec = os.path.join(d, "t.c"), os.path.join(d, "t"), os.path.join(d, "rec.bin")
+        with open(src, "w") as f:
+            f.write(C_TIMING)
+        np.ascontiguousarray(p, dtype=np.float32).tofile(rec)
+        lib64 = os.path.join(cuda, "lib64")
+        r = subprocess.run([cc, "-O2", "-std=c99", "-I", os.path.join(ROOT, "include"), "-I",
+                            os.path.join(cuda, "include"), src, "-L", lib_dir, "-lcunbody", f"-Wl,-rpath,{lib_dir}",
+                            "-L", lib64, "-lcudart", f"-Wl,-rpath,{lib64}", "-o", exe], capture_output=True, text=True)
+        if r.returncode != 0:
+            return None
+        try:
+            r = subprocess.run([exe, rec, str(p.shape[0]), str(calls), "1" if potential else "0", repr(eps2)],
+                               capture_output=True, text=True, timeout=120)
+        except subprocess.TimeoutExpired:
+            return None
+        if r.returncode != 0:
+            return None
+        host, wall, dev = (float(x) for x in r.stdout.split())
+    return {"us_host_per_call_c": host, "us_per_call_c": wall, "us_per_eval_device_c": dev,
+            "calls": calls, "note": "C program, back-to-back cn_force on device buffers, one stream"}
+
+
 # FP32 lane operations per pair of the packed (f32x2) adjoint and
 # force-jerk-potential kernels: the FP32 pipe is their bound, as for the
-# plain kernel. The compensated kernel issues scalar FP32 instructions only
-# (MUFU negligible), so its bound is the issue slot at 104 per pair.
+# plain kernel. The compensated kernel (packed f32x2 issue) does 82 FP32
+# lane operations per pair (plus 6 FMNMX on the ALU pipe and 1 MUFU).
 ADJOINT_LANE_OPS_PER_PAIR = 30
-DD_ISSUE_PER_PAIR = 104
+DD_LANE_OPS_PER_PAIR = 82
 JERK_POT_LANE_OPS_PER_PAIR = 29  # 27 + 1 (d^2 then + eps2) + 1 (potential sum)
 # symmetric form (packed f32x2 issue): 16 FP32 lane operations per unordered
 # pair, plus per j record and lane 3 FADD joining the two packed halves and
-# 27/8 FADD of the warp reduce-scatter, over K = 8 pairs
-SYM_LANE_OPS_PER_UNORDERED_PAIR = 16 + (3 + 27 / 8) / 8
+# 24/8 FADD of the warp reduce-scatter, over K = 8 pairs
+SYM_LANE_OPS_PER_UNORDERED_PAIR = 16 + (3 + 24 / 8) / 8
 
 
 def _events_ms(torch, fn, reps, stream):
@@ -454,6 +550,7 @@ def measure_rows(args, cn, torch, device, peak):
     dt = time.perf_counter() - t0
     rows["c1_plummer1024_acc_pot"] = {
         "pairs_per_s": 1024.0 ** 2 / (us_dev / 1e6), "us_per_eval_device": us_dev, "us_per_call_direct": 1e3 * ms,
+        "c_calls": c_call_timing(p, eps2, True),
         "emax": oracle.e_max(acc.cpu().numpy(), ref_a),
         "pot_rel_err": float(np.max(np.abs(pot.cpu().numpy() - ref_p) / np.abs(ref_p))),
         "cpu_baseline": {"value": 1024.0 ** 2 / dt, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
@@ -475,7 +572,7 @@ def measure_rows(args, cn, torch, device, peak):
         dt = time.perf_counter() - t0
         rows[f"c2_plummer{n}"] = {
             "pairs_per_s": float(n) * n / (us_dev / 1e6), "us_per_eval_device": us_dev,
-            "us_per_call_direct": 1e3 * ms,
+            "us_per_call_direct": 1e3 * ms, "c_calls": c_call_timing(p, eps2, False) if n <= 4096 else None,
             "frac": float(n) * n / (us_dev / 1e6) / peak, "launch_shape": cn.cn_tune_get("f32", n, n),
             "gflops_at_38": float(n) * n / (us_dev / 1e6) * FLOP_PER_PAIR / 1e9,
             "paper_gflops_8800gtx": paper_gflops[n],
@@ -505,7 +602,7 @@ def measure_rows(args, cn, torch, device, peak):
         "f32": {"pairs_per_s": pairs / (ms32 / 1e3), "frac": pairs / (ms32 / 1e3) / peak,
                 "emax": float(e32.max()), "p99": float(np.percentile(e32, 99)), "median": float(np.median(e32))},
         "compensated": {"pairs_per_s": pairs / (msdd / 1e3),
-                        "frac_of_own_roofline": pairs / (msdd / 1e3) / (lane_rate / DD_ISSUE_PER_PAIR),
+                        "frac_of_own_roofline": pairs / (msdd / 1e3) / (lane_rate / DD_LANE_OPS_PER_PAIR),
                         "emax": float(edd.max()), "p99": float(np.percentile(edd, 99)),
                         "median": float(np.median(edd))},
         "cpu_baseline": {"value": r.size * n / dt, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
