@@ -90,22 +90,36 @@ def _torch():
     return torch
 
 
+_current_stream = None  # () -> cudaStream_t of PyTorch's current stream on the current device
+
+
 def _stream_handle(stream):
-    torch = _torch()
-    if stream is None:
-        stream = torch.cuda.current_stream()
-    return ctypes.c_void_p(int(stream.cuda_stream))
+    """The cudaStream_t of `stream`, as an int; None means PyTorch's current
+    stream on the current device (read through torch's raw-stream query where
+    it exists: torch.cuda.current_stream() builds a Stream object, ~3 us)."""
+    global _current_stream
+    if stream is not None:
+        return int(stream.cuda_stream)
+    if _current_stream is None:
+        torch = _torch()
+        raw = getattr(torch._C, "_cuda_getCurrentRawStream", None)
+        dev = getattr(torch._C, "_cuda_getDevice", None)
+        if raw is not None and dev is not None:
+            _current_stream = lambda: raw(dev())
+        else:
+            _current_stream = lambda: int(torch.cuda.current_stream().cuda_stream)
+    return _current_stream()
 
 
 def _ptr(t):
-    return None if t is None else ctypes.c_void_p(t.data_ptr())
+    return None if t is None else t.data_ptr()
 
 
 def _records(t, name):
     torch = _torch()
-    if not isinstance(t, torch.Tensor) or t.dtype != torch.float32 or t.dim() != 2 or t.shape[1] != 4:
+    if not (isinstance(t, torch.Tensor) and t.dtype == torch.float32 and t.dim() == 2 and t.shape[1] == 4):
         raise TypeError(f"{name} must be a float32 tensor of shape (n, 4)")
-    if not t.is_cuda or not t.is_contiguous():
+    if not (t.is_cuda and t.is_contiguous()):
         raise TypeError(f"{name} must be a contiguous CUDA tensor")
     return t
 

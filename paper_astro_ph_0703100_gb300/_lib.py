@@ -106,6 +106,8 @@ def load(path: str | None = None):
     CUNBODY_LIB, when set, names another build of the library to load (for
     instance the bounds-checked libcunbody_debug.so)."""
     global _lib
+    if _lib is not None:  # loaded: no lock on the per-call path
+        return _lib
     with _lock:
         if _lib is not None:
             return _lib
