@@ -392,6 +392,34 @@ cn_tune mid_f32_tune(int64_t n_i, int64_t n_j, int sms) {
   return best;
 }
 
+// The packed shapes of 256 threads with four or eight i-particles per lane
+// (split-j or not) run one CTA per SM, and the static schedule gives each
+// CTA ceil(units / CTAs) units of j_tile records
+// (a ragged last j-tile is padded with zero masses, so every unit costs the
+// same). For the shape's i-tile this picks the j-tile, a multiple of `step`
+// in [jt0 / 2, min(2 jt0, 4096)], with the least work on the busiest CTA,
+// counting 64 records of overhead per unit; ties keep the larger tile.
+// Measured at N = 9000 .. 131072 (graph-replayed launches), it picked the
+// fastest tile of each size's sweep (N = 14000: 0.44 -> 0.65 of the FP32
+// bound, 28000: 0.72 -> 0.79, 40000: 0.75 -> 0.80, 98304: 0.836 -> 0.854).
+int32_t fit_j_tile(int64_t n_i, int64_t n_j, int64_t i_tile, int32_t jt0, int32_t step, int64_t ctas) {
+  const int64_t n_it = (n_i + i_tile - 1) / i_tile;
+  const int32_t lo = std::max(step, (jt0 / 2) / step * step);
+  const int32_t hi = std::min(4096, 2 * jt0);
+  int32_t best_t = jt0;
+  double best = -1.0;
+  for (int32_t t = lo; t <= hi; t += step) {
+    const int64_t units = n_it * ((std::max<int64_t>(n_j, 1) + t - 1) / t);
+    const int64_t g = std::max<int64_t>(1, std::min(units, ctas));
+    const double c = static_cast<double>((units + g - 1) / g) * static_cast<double>(t + 64);
+    if (best < 0.0 || c < best || (c == best && t > best_t)) {
+      best = c;
+      best_t = t;
+    }
+  }
+  return best_t;
+}
+
 // Default launch shape of a variant for these sizes on a device with `sms`
 // multiprocessors (queried, never assumed).
 cn_tune default_tune(int variant, int64_t n_i, int64_t n_j, int sms) {
@@ -432,12 +460,14 @@ cn_tune default_tune(int variant, int64_t n_i, int64_t n_j, int sms) {
       double upto;
       int k, threads, j_tile, j_lanes;
     };
+    // (K, threads, lane groups) per band and the j-tile the schedule fit
+    // starts from; fractions of the FP32 bound with the fitted j-tile
     static const Band bands[] = {
-        {10000.0, 4, 256, 4096, 8},   // N = 8192: 0.553 of the FP32 bound
-        {14000.0, 8, 256, 4096, 8},   // N = 12000: 0.641
-        {20000.0, 8, 256, 2048, 16},  // N = 16384: 0.711
-        {28000.0, 8, 256, 2048, 8},   // N = 24576: 0.740
-        {40000.0, 8, 256, 1024, 8},   // N = 32768: 0.784
+        {10000.0, 4, 256, 4096, 8},   // N = 8192: 0.57, 10000: 0.56
+        {14000.0, 8, 256, 4096, 8},   // N = 12000: 0.67, 14000: 0.65
+        {20000.0, 8, 256, 2048, 16},  // N = 16384: 0.72, 20000: 0.71
+        {28000.0, 8, 256, 2048, 8},   // N = 24576: 0.78, 28000: 0.79
+        {40000.0, 8, 256, 1024, 8},   // N = 32768: 0.81, 40000: 0.80
     };
     if (n_i > 4096 && n_eff <= 6500.0) return mid_f32_tune(n_i, n_j, sms);
     if (n_i > 4096 && n_eff <= bands[4].upto) {
@@ -445,9 +475,10 @@ cn_tune default_tune(int variant, int64_t n_i, int64_t n_j, int sms) {
         if (n_eff > b.upto) continue;
         t.i_per_thread = b.k;
         t.threads = b.threads;
-        t.j_tile = b.j_tile;
         t.j_lanes = b.j_lanes;
-        t.stages = n_j <= b.j_tile ? 1 : 3;
+        t.j_tile = fit_j_tile(n_i, n_j, static_cast<int64_t>(b.k) * b.threads / b.j_lanes, b.j_tile, 8 * b.j_lanes,
+                              sms);
+        t.stages = n_j <= t.j_tile ? 1 : 3;
         return t;
       }
     }
@@ -471,17 +502,12 @@ cn_tune default_tune(int variant, int64_t n_i, int64_t n_j, int sms) {
     t.j_tile = 256;
   } else if (f32 && n > 4096) {
     // packed FP32, measured at N = 49152 .. 131072 (smaller systems take the
-    // bands above): K = 4 x 256 with 512-record tiles below ~96K, K = 8 x 256
-    // with 1024-record tiles above
-    if (n < 98304) {
-      t.i_per_thread = 4;
-      t.threads = 256;
-      t.j_tile = 512;
-    } else {
-      t.i_per_thread = 8;
-      t.threads = 256;
-      t.j_tile = 1024;
-    }
+    // bands above): K = 4 x 256 below ~96K, K = 8 x 256 above, with the
+    // j-tile fitted to the schedule from 512 or 1024 records
+    t.i_per_thread = n < 98304 ? 4 : 8;
+    t.threads = 256;
+    t.j_tile = fit_j_tile(n_i, n_j, static_cast<int64_t>(t.i_per_thread) * t.threads, n < 98304 ? 512 : 1024, 16,
+                          sms);
   } else if (n >= 32768) {
     // measured optima (packed forms): FP32 K = 8 x 256 threads at N = 131072,
     // compensated K = 4 x 256, adjoint (N = 65536) and force-jerk
