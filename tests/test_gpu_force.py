@@ -3,8 +3,9 @@
 Tolerances (per-particle |a_gpu - a_oracle| / |a_oracle|, max over the
 checked particles, Eq. 3), as the target accuracy of each form states:
   plain FP32       <= 1e-5
-  compensated      <= 1e-7 (double-single pair arithmetic and sums: the
-                   expected error is ~1e-10, so the bound has a wide margin)
+  compensated      <= 1e-7 (the pair term in FP32 with its roundings
+                   recovered, (hi, lo) sums: measured ~1e-9, 1.6e-8 at
+                   N = 2^20, so the bound keeps a margin)
 Potentials: relative error <= 1e-5 (FP32) / 1e-7 (compensated).
 """
 
@@ -66,6 +67,35 @@ def test_c2_large_sampled_rows_autotuned(n):
     ref, _ = oracle.force(p, p, eps2, rows=rows, potential=False)
     assert e_max(acc.cpu().numpy()[rows], ref) <= TOL_F32
     cn.cn_tune_set("f32", n, n, None)
+
+
+@pytest.mark.parametrize("n_i,n_j", [(9000, 9000), (14000, 14000), (22000, 22000), (28000, 28000),
+                                     (45000, 45000), (14000, 9000), (9000, 22000)])
+def test_default_shapes_with_fitted_j_tiles(n_i, n_j):
+    """Between the measured sizes the default j-tile is fitted to the static
+    schedule, so it is often not a power of two (and the last j-tile is
+    ragged): sampled rows against the oracle in those default shapes."""
+    cn = lib()
+    torch = torch_cuda()
+    pi, pj = synth.plummer(n_i, n_i + 3), synth.plummer(n_j, n_j + 4)
+    eps2 = float(np.float32(synth.plummer_eps(max(n_i, n_j))) ** 2)
+    cn.cn_tune_set("f32", n_i, n_j, None)
+    shape = cn.cn_tune_get("f32", n_i, n_j)
+    acc, _ = cn.cn_force(dev_tensor(pi), dev_tensor(pj), eps2)
+    torch.cuda.synchronize()
+    assert cn.cn_get_device_status() == 0
+    rows = synth.sample_rows(n_i, 1024, seed=n_i + n_j)
+    ref, _ = oracle.force(pi, pj, eps2, rows=rows, potential=False)
+    assert e_max(acc.cpu().numpy()[rows], ref) <= TOL_F32, shape
+    assert shape["j_tile"] % 16 == 0
+
+
+def test_fitted_j_tiles_include_non_powers_of_two():
+    """The sizes above exercise j-tiles that are not powers of two (on a
+    152-SM GB300: 9000 -> 2304, 14000 -> 2816, 22000 -> 3200, 45000 -> 944)."""
+    cn = lib()
+    tiles = [cn.cn_tune_get("f32", n, n)["j_tile"] for n in (9000, 14000, 22000, 28000, 45000)]
+    assert any(t & (t - 1) for t in tiles), tiles
 
 
 def test_c2_131072_default_shape_sampled():
