@@ -404,9 +404,12 @@ cn_tune mid_f32_tune(int64_t n_i, int64_t n_j, int sms) {
 // bound, 28000: 0.72 -> 0.79, 40000: 0.75 -> 0.80, 98304: 0.836 -> 0.854).
 int32_t fit_j_tile(int64_t n_i, int64_t n_j, int64_t i_tile, int32_t jt0, int32_t step, int64_t ctas) {
   const int64_t n_it = (n_i + i_tile - 1) / i_tile;
-  const int32_t lo = std::max(step, (jt0 / 2) / step * step);
-  const int32_t hi = std::min(4096, 2 * jt0);
-  int32_t best_t = jt0;
+  // no tile longer than the j set (rounded up to the step): the padding of a
+  // short tile is written by one thread
+  const int64_t nj_up = (std::max<int64_t>(n_j, 1) + step - 1) / step * step;
+  const int32_t hi = static_cast<int32_t>(std::min<int64_t>(std::min(4096, 2 * jt0), nj_up));
+  const int32_t lo = std::min(hi, std::max(step, (jt0 / 2) / step * step));
+  int32_t best_t = hi;
   double best = -1.0;
   for (int32_t t = lo; t <= hi; t += step) {
     const int64_t units = n_it * ((std::max<int64_t>(n_j, 1) + t - 1) / t);

@@ -70,7 +70,8 @@ def test_c2_large_sampled_rows_autotuned(n):
 
 
 @pytest.mark.parametrize("n_i,n_j", [(9000, 9000), (14000, 14000), (22000, 22000), (28000, 28000),
-                                     (45000, 45000), (14000, 9000), (9000, 22000)])
+                                     (45000, 45000), (14000, 9000), (9000, 22000), (1000000, 50),
+                                     (200000, 2000)])
 def test_default_shapes_with_fitted_j_tiles(n_i, n_j):
     """Between the measured sizes the default j-tile is fitted to the static
     schedule, so it is often not a power of two (and the last j-tile is
