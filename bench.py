@@ -6,7 +6,8 @@ sphere of N = 131072 particles (i set = j set, eps = 4 / N^(1/3), FP32
 records) with the plain FP32 kernel: N^2 pair interactions. The headline
 value is pair interactions per second over the K timed steps (CUDA events
 on the launching stream, L2 flushed between steps by writing 256 MiB).
-Beside it the line reports the compensated (double-single) form on the
+Beside it the line reports the compensated form (FP32 pair with its
+roundings recovered, (hi, lo) sums, FP64 folds) on the
 same input, the roofline fraction of the pair kernel, the end-to-end rate
 through the host-buffer C-ABI call (copies included), and the FP64 oracle
 timed on the host cores on a bounded sample of the same workload.

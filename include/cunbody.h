@@ -149,14 +149,16 @@ CN_API cn_status cn_force_ws(int64_t n_i, const float *pos_i, int64_t n_j, const
  * Compensated ("split-precision") direct sum with FP64 outputs.
  *   acc_out : double[n_i][3]; pot_out : double[n_i] or NULL; other
  *   arguments as cn_force.
- * FP32 instructions only: every quantity of the pair term (x_j - x_i, the
- * softened squared distance, its inverse square root from the MUFU
- * estimate plus an FMA-formed residual, the cube, the mass and direction
- * products) is carried as a double-single (hi, lo) pair with each rounding
- * recovered by TwoSum or an FMA, and every term is added to a
- * double-single running sum with Knuth's TwoSum. Partial sums of split
- * i-tiles are merged in FP64 in a fixed order. Per-particle relative error
- * against an exact sum is of order 1e-10 or below (the FP32 form: ~1e-6).
+ * FP32 instructions only: the pair term is evaluated in FP32 with the
+ * roundings that matter recovered (a fast two-sum for x_j - x_i, exact
+ * squares and ordered two-sums for the softened squared distance, the MUFU
+ * inverse square root corrected to first order by an FMA-formed residual,
+ * the residuals of the mass and direction products); each term is added to
+ * a (hi, lo) FP32 running sum with Knuth's TwoSum, and the sums of every
+ * j-tile are folded into FP64. Partial sums of split i-tiles are merged in
+ * FP64 in a fixed order. Per-particle relative error against an exact sum:
+ * ~1e-9 on Plummer spheres, 1.6e-8 at worst on the N = 2^20 Hernquist
+ * workload (the FP32 form: ~1e-6).
  * The wide accumulators of the GRAPE pipelines (Section 1.6) and the
  * FORCE-LOOP error analysis (Section 2.2.2) motivate the form.
  */

@@ -194,7 +194,8 @@ def cn_force_ws(pos_i, pos_mass_j, eps2, workspace, acc_out=None, pot_out=None, 
 
 
 def cn_force_dd(pos_i, pos_mass_j, eps2, acc_out=None, pot_out=None, potential=False, stream=None):
-    """Compensated (double-single) form; FP64 outputs."""
+    """Compensated form (FP32 pair term with its roundings recovered, (hi, lo)
+    sums folded into FP64); FP64 outputs."""
     return _force("cn_force_dd", True, pos_i, pos_mass_j, eps2, acc_out, pot_out, potential, stream)
 
 
