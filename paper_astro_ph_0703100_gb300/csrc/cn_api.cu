@@ -394,28 +394,28 @@ cn_tune mid_f32_tune(int64_t n_i, int64_t n_j, int sms) {
 
 // The packed shapes of 256 threads with four or eight i-particles per lane
 // (split-j or not) run one CTA per SM, and the static schedule gives each
-// CTA ceil(units / CTAs) units of j_tile records
-// (a ragged last j-tile is padded with zero masses, so every unit costs the
-// same). For the shape's i-tile this picks the j-tile, a multiple of `step`
-// in [jt0 / 2, min(2 jt0, 4096)], with the least work on the busiest CTA,
-// counting 64 records of overhead per unit; ties keep the larger tile.
-// Measured at N = 9000 .. 131072 (graph-replayed launches), it picked the
-// fastest tile of each size's sweep (N = 14000: 0.44 -> 0.65 of the FP32
-// bound, 28000: 0.72 -> 0.79, 40000: 0.75 -> 0.80, 98304: 0.836 -> 0.854).
-int32_t fit_j_tile(int64_t n_i, int64_t n_j, int64_t i_tile, int32_t jt0, int32_t step, int64_t ctas) {
+// CTA ceil(units / CTAs) units of j_tile records (a ragged last j-tile is
+// padded with zero masses, so every unit costs the same). For the shape's
+// i-tile this picks the j-tile, a multiple of `step` in [lo, hi] and no
+// longer than the j set, with the least work on the busiest CTA, counting
+// 64 records of overhead per unit; ties take the smaller tile. Measured at
+// N = 8192 .. 131072 (graph-replayed launches), it picked the fastest or a
+// tile within 1% of it at each size of the sweeps (N = 14000: 0.44 -> 0.72
+// of the FP32 bound, 28000: 0.72 -> 0.80, 98304: 0.836 -> 0.852).
+int32_t fit_j_tile(int64_t n_i, int64_t n_j, int64_t i_tile, int32_t lo, int32_t hi, int32_t step, int64_t ctas) {
   const int64_t n_it = (n_i + i_tile - 1) / i_tile;
-  // no tile longer than the j set (rounded up to the step): the padding of a
-  // short tile is written by one thread
+  // the padding of a short tile is written by one thread
   const int64_t nj_up = (std::max<int64_t>(n_j, 1) + step - 1) / step * step;
-  const int32_t hi = static_cast<int32_t>(std::min<int64_t>(std::min(4096, 2 * jt0), nj_up));
-  const int32_t lo = std::min(hi, std::max(step, (jt0 / 2) / step * step));
+  hi = static_cast<int32_t>(std::min<int64_t>(std::min(hi, 4096), nj_up)) / step * step;
+  hi = std::max(hi, step);
+  lo = std::min(hi, std::max(step, lo / step * step));
   int32_t best_t = hi;
   double best = -1.0;
   for (int32_t t = lo; t <= hi; t += step) {
     const int64_t units = n_it * ((std::max<int64_t>(n_j, 1) + t - 1) / t);
     const int64_t g = std::max<int64_t>(1, std::min(units, ctas));
     const double c = static_cast<double>((units + g - 1) / g) * static_cast<double>(t + 64);
-    if (best < 0.0 || c < best || (c == best && t > best_t)) {
+    if (best < 0.0 || c < best) {
       best = c;
       best_t = t;
     }
@@ -452,35 +452,33 @@ cn_tune default_tune(int variant, int64_t n_i, int64_t n_j, int sms) {
   }
   if (f32) {
     // Mid-size systems (measured on GB300, 152 SMs, N = 5000 .. 65536,
-    // graph-replayed launches): split-j lane groups holding four or eight
-    // i-particles keep the i-tiles small enough to fill the SMs while each
-    // j record feeds several packed pair terms. Sizes are compared by the
+    // graph-replayed launches): split-j lane groups of 8 holding four or
+    // eight i-particles keep the i-tiles small enough to fill the SMs while
+    // each j record feeds several packed pair terms. Sizes are compared by the
     // work per SM, n_eff = sqrt(n_i n_j) sqrt(152 / sms), so another SM count
     // moves the bands. Below 6500 the schedule model of mid_f32_tune decides.
     const double n_eff = std::sqrt(static_cast<double>(n_i) * static_cast<double>(std::max<int64_t>(n_j, 1))) *
                          std::sqrt(152.0 / std::max(sms, 1));
     struct Band {
       double upto;
-      int k, threads, j_tile, j_lanes;
+      int k, threads, j_lanes, jt_lo, jt_hi;
     };
-    // (K, threads, lane groups) per band and the j-tile the schedule fit
-    // starts from; fractions of the FP32 bound with the fitted j-tile
+    // (K, threads, lane groups) per band and the window of the j-tile fit;
+    // fractions of the FP32 bound measured with the fitted j-tile
     static const Band bands[] = {
-        {10000.0, 4, 256, 4096, 8},   // N = 8192: 0.57, 10000: 0.56
-        {14000.0, 8, 256, 4096, 8},   // N = 12000: 0.67, 14000: 0.65
-        {20000.0, 8, 256, 2048, 16},  // N = 16384: 0.72, 20000: 0.71
-        {28000.0, 8, 256, 2048, 8},   // N = 24576: 0.78, 28000: 0.79
-        {40000.0, 8, 256, 1024, 8},   // N = 32768: 0.81, 40000: 0.80
+        {8600.0, 4, 256, 8, 2048, 4096},   // N = 8192: 0.563
+        {40000.0, 8, 256, 8, 512, 4096},   // 9000: 0.60, 14000: 0.72, 16384: 0.74, 20000: 0.76,
+                                           // 24576: 0.80, 32768: 0.82, 40000: 0.81
     };
     if (n_i > 4096 && n_eff <= 6500.0) return mid_f32_tune(n_i, n_j, sms);
-    if (n_i > 4096 && n_eff <= bands[4].upto) {
+    if (n_i > 4096 && n_eff <= bands[1].upto) {
       for (const Band& b : bands) {
         if (n_eff > b.upto) continue;
         t.i_per_thread = b.k;
         t.threads = b.threads;
         t.j_lanes = b.j_lanes;
-        t.j_tile = fit_j_tile(n_i, n_j, static_cast<int64_t>(b.k) * b.threads / b.j_lanes, b.j_tile, 8 * b.j_lanes,
-                              sms);
+        t.j_tile = fit_j_tile(n_i, n_j, static_cast<int64_t>(b.k) * b.threads / b.j_lanes, b.jt_lo, b.jt_hi,
+                              8 * b.j_lanes, sms);
         t.stages = n_j <= t.j_tile ? 1 : 3;
         return t;
       }
@@ -509,8 +507,8 @@ cn_tune default_tune(int variant, int64_t n_i, int64_t n_j, int sms) {
     // j-tile fitted to the schedule from 512 or 1024 records
     t.i_per_thread = n < 98304 ? 4 : 8;
     t.threads = 256;
-    t.j_tile = fit_j_tile(n_i, n_j, static_cast<int64_t>(t.i_per_thread) * t.threads, n < 98304 ? 512 : 1024, 16,
-                          sms);
+    const int32_t jt0 = n < 98304 ? 512 : 1024;
+    t.j_tile = fit_j_tile(n_i, n_j, static_cast<int64_t>(t.i_per_thread) * t.threads, jt0 / 2, 2 * jt0, 16, sms);
   } else if (n >= 32768) {
     // measured optima (packed forms): FP32 K = 8 x 256 threads at N = 131072,
     // compensated K = 4 x 256, adjoint (N = 65536) and force-jerk

@@ -93,7 +93,7 @@ def test_default_shapes_with_fitted_j_tiles(n_i, n_j):
 
 def test_fitted_j_tiles_include_non_powers_of_two():
     """The sizes above exercise j-tiles that are not powers of two (on a
-    152-SM GB300: 9000 -> 2304, 14000 -> 2816, 22000 -> 3200, 45000 -> 944)."""
+    152-SM GB300: 9000 -> 2304, 14000 -> 1280, 22000 -> 3200, 45000 -> 944)."""
     cn = lib()
     tiles = [cn.cn_tune_get("f32", n, n)["j_tile"] for n in (9000, 14000, 22000, 28000, 45000)]
     assert any(t & (t - 1) for t in tiles), tiles
