@@ -111,9 +111,10 @@ typedef struct cn_tune {
                              band (0 = one band while its slots fit in 2 GiB, else bands)       */
     int32_t j_lanes;      /* single-system FP32, per-i-softening, force-jerk and adjoint forms:
                              lanes sharing the thread's i-particles (1, 2, 4, ..., 32; needs
-                             i_per_thread = 1 or 2 - exactly 2 for the force-jerk and adjoint
-                             forms - and j_tile a multiple of 8 x j_lanes); their partial sums
-                             are combined by warp shuffles. Ignored (1) for calls with eps2 = 0
+                             j_tile a multiple of 8 x j_lanes; i_per_thread up to 8 for the
+                             plain FP32 forms, 1 or 2 for per-i softening, exactly 2 for the
+                             force-jerk and adjoint forms); their partial sums are combined
+                             by warp shuffles. Ignored (1) for calls with eps2 = 0
                              of the force-jerk and adjoint forms                                */
 } cn_tune;
 
@@ -228,9 +229,12 @@ CN_API cn_status cn_force_eps_i(int64_t n_i, const float *pos_eps_i, int64_t n_j
  * from the other). Not in the paper, whose kernel evaluates every ordered
  * pair: 16 FP32 lane operations and one MUFU per unordered pair plus a warp
  * reduce-scatter of the j-side sums, against 2 x 12 for the two ordered
- * pairs. Results are accumulated per (tile, partner tile) and merged in
- * FP64 in a fixed order (bitwise reproducible for a given launch shape);
- * accuracy as cn_force.
+ * pairs. The j-side sums of each tile pair and the i-side sums of each
+ * (CTA, tile row) segment are merged per particle in FP64 in a fixed order
+ * (bitwise reproducible for a given launch shape); accuracy as cn_force.
+ * It pays off from about N = 24576 on a GB300 (1.15x cn_force at 24576,
+ * 1.29x at 131072); at N = 16384 the two take the same time and below it
+ * cn_force is faster (about 1.9x at 8192).
  *   pos_mass : float[n][4] device records (x, y, z, m), 16-byte aligned
  *   eps2     : softening squared, finite and >= 0 (0: coincident pairs
  *              contribute nothing)
@@ -240,13 +244,15 @@ CN_API cn_status cn_force_eps_i(int64_t n_i, const float *pos_eps_i, int64_t n_j
  * Asynchronous on `stream`; n == 0 is a no-op. Errors: CN_ERR_INVALID_ARG
  * (n < 0, bad eps2, NULL or overlapping buffers, a tune with j_lanes),
  * CN_ERR_MISALIGNED, CN_ERR_CUDA (launch), CN_ERR_WORKSPACE (below).
- * Uses a library workspace of per-(tile, partner) slots: 16 N^2 / B bytes
- * for tiles of B particles (134 MB at N = 131072 with the default
- * 2048-particle tiles) while that fits in 2 GiB; above, the tile rows are
- * processed in bands of w rows (about 32 w N + 32 N bytes, w chosen to fit
- * 2 GiB, or set by the tune's chunk_units), one kernel and one merge per
- * band, with bitwise the same result. CN_ERR_WORKSPACE when even one band
- * cannot be held.
+ * Uses a library workspace of j-side slots, 16 N^2 / B bytes for tiles of
+ * B particles (134 MB at N = 131072 with the default 2048-particle tiles,
+ * half of it written), plus the i-side segments (32 B per particle of a
+ * tile per CTA and row), while the slots fit in 2 GiB; above, the tile rows
+ * are processed in bands of w rows (about 16 w N + 32 N bytes, w chosen to
+ * fit 2 GiB, or set by the tune's chunk_units), one kernel and one merge
+ * per band. A banded launch cuts the rows into other segments than a
+ * one-band launch, so the two agree to FP32 rounding of the segment sums,
+ * not bitwise. CN_ERR_WORKSPACE when even one band cannot be held.
  */
 CN_API cn_status cn_force_symmetric(int64_t n, const float *pos_mass, float eps2, float *acc_out, float *pot_out,
                                     cn_stream stream);
