@@ -4,9 +4,10 @@ j arrays, each bulk copy's range, the chunk range of split tiles) and the
 symmetric kernel's unit and segment indices are checked on the device; a
 violation would set the device status bit kStatusBadSchedule and stop the
 CTA's work. Here the batched, interaction-list, dynamic-queue and split-j
-paths (and the compensated, adjoint, force-jerk and banded symmetric forms)
-run under that build, in a separate process: no check fires, and the
-results still match the FP64 oracle.
+paths, default shapes with j-tiles fitted to the schedule (and the
+compensated, adjoint, force-jerk and banded symmetric forms) run under that
+build, in a separate process: no check fires, and the results still match
+the FP64 oracle.
 """
 
 import json
@@ -84,6 +85,15 @@ SCRIPT = textwrap.dedent(r"""
         cn.cn_tune_set("f32", 5000, 3001, None)
         status("force " + name)
         out["errors"]["force " + name] = oracle.e_max(acc.cpu().numpy(), ref)
+    # default shapes with j-tiles fitted to the schedule (ragged last j-tile,
+    # lane groups of 8 with the constant-stride loop), and a tiny j set
+    for n_i, n_j in ((14000, 14000), (9000, 22000), (1000000, 50)):
+        pi, pj = synth.plummer(n_i, n_i + 1), synth.plummer(n_j, n_j + 2)
+        acc, _ = cn.cn_force(d(pi), d(pj), 1e-3)
+        status("default %dx%d" % (n_i, n_j))
+        rows = synth.sample_rows(n_i, 256, seed=n_i)
+        ref_r, _ = oracle.force(pi, pj, 1e-3, rows=rows, potential=False)
+        out["errors"]["default %dx%d" % (n_i, n_j)] = oracle.e_max(acc.cpu().numpy()[rows], ref_r)
     acc, _ = cn.cn_force_dd(d(p), d(q), 1e-3)
     status("compensated")
     out["errors"]["compensated"] = oracle.e_max(acc.cpu().numpy(), ref)
