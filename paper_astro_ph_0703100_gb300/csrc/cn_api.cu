@@ -1141,19 +1141,26 @@ cn_status build_group_plan(const std::vector<Group>& groups, bool lists, int64_t
     // i-tile fitted to the group sizes: every group is cut into whole i-tiles,
     // so a tile larger than the typical group leaves lanes idle. Among the
     // shapes below take the one with the least evaluated-but-padded work,
-    // weighted by each shape's relative pair rate (measured on GB300: the
-    // packed K = 8 kernel 1.0, its split-j forms 0.95, K = 4 0.99, K = 2 x 128
-    // 0.93, one particle per thread 0.80; the split-j forms hold small tiles
-    // with eight i-particles per lane group).
+    // weighted by each shape's relative pair rate, measured on GB300: the
+    // packed K = 8 kernel 1.0, its split-j forms 0.95, K = 4 0.99, K = 2 x
+    // 128 0.93, one particle per thread 0.80. Ensembles (eight of them, 64 ..
+    // 65536 particles per cluster) add K = 4 x 64 at 0.99, ahead of 4 x 128
+    // (the same rate with half the i-tile), and rate the 128-thread split-j
+    // form 0.75 (0.29 against 0.67 of the FP32 bound for 4096 clusters of
+    // 256); interaction lists keep their measured set (groups of 256 against
+    // 4096-record lists: the 256-thread split-j form 0.72, 4 x 64 below 0.70).
     struct Cand {
       int k, threads, j_lanes, j_tile;
       double rate;
+      int use;  // 1: ensembles, 2: lists, 3: both
     };
-    static const Cand cands[] = {{8, 256, 1, 512, 1.0},  {8, 256, 2, 512, 0.95}, {8, 256, 4, 512, 0.95},
-                                 {8, 256, 8, 512, 0.95}, {8, 128, 8, 512, 0.94}, {4, 128, 1, 256, 0.99},
-                                 {2, 128, 1, 256, 0.93}, {1, 128, 1, 256, 0.80}};
+    static const Cand cands[] = {{8, 256, 1, 512, 1.0, 3},   {8, 256, 2, 512, 0.95, 3}, {8, 256, 4, 512, 0.95, 3},
+                                 {8, 256, 8, 512, 0.95, 3},  {8, 128, 8, 512, 0.94, 2}, {8, 128, 8, 512, 0.75, 1},
+                                 {4, 64, 1, 256, 0.99, 1},   {4, 128, 1, 256, 0.99, 3}, {2, 128, 1, 256, 0.93, 3},
+                                 {1, 128, 1, 256, 0.80, 3}};
     double best = -1.0;
     for (const Cand& c : cands) {
+      if (!(c.use & (lists ? 2 : 1))) continue;
       if (guard && (c.j_lanes > 1 || c.k > 1)) continue;  // the guarded kernels hold one particle, no split-j
       const int64_t it = static_cast<int64_t>(c.k) * c.threads / c.j_lanes;
       double padded = 0.0;
@@ -1205,6 +1212,25 @@ cn_status build_group_plan(const std::vector<Group>& groups, bool lists, int64_t
   if (!tiles.empty() && (st = layout(dev, *d, variant, guard, p, static_cast<int64_t>(tiles.size()), units, 0, &g)) !=
                             CN_OK)
     return st;
+  // Ragged ensembles (cluster sizes spanning 4x or more) with the fitted
+  // shape and many units per resident CTA take the dynamic queue in chunks
+  // of 32 units (measured: 0.74 -> 0.78 of the FP32 bound on 512 clusters
+  // of 256 .. 16384, 0.60 -> 0.63 on 2048 of 256 .. 2048, 0.77 -> 0.81 on
+  // 256 of 128 .. 65536). Equal clusters keep the static schedule (1000 of
+  // 1024: 0.73 static, 0.62 dynamic; 64 of 16384: 0.83 static, 0.72
+  // dynamic), and so do launches with few units per slot, where the chunks
+  // leave CTAs idle.
+  int64_t ni_min = INT64_MAX, ni_max = 0;
+  for (const Group& gr : groups)
+    if (gr.ni > 0 && gr.nj > 0) {
+      ni_min = std::min(ni_min, gr.ni);
+      ni_max = std::max(ni_max, gr.ni);
+    }
+  if (!lists && tune == &fitted && !tiles.empty() && p.chunk_units == 0 && ni_max >= 4 * ni_min &&
+      units >= 20 * static_cast<int64_t>(g.grid)) {
+    p.chunk_units = 32;
+    if ((st = layout(dev, *d, variant, guard, p, static_cast<int64_t>(tiles.size()), units, 0, &g)) != CN_OK) return st;
+  }
   auto* plan = new cn_batch_plan();
   plan->dev = dev;
   plan->lists = lists;
