@@ -1139,13 +1139,15 @@ cn_status build_group_plan(const std::vector<Group>& groups, bool lists, int64_t
   cn_tune fitted{};
   if (!tune && !registered_tune(dev, variant, key_i, n_i_total)) {
     // i-tile fitted to the group sizes: every group is cut into whole i-tiles,
-    // so a tile larger than the typical group leaves lanes idle. Among the
+    // so a tile larger than the typical group leaves lanes idle, and every
+    // j range into whole j-tiles (padded with zero masses). Among the
     // shapes below take the one with the least evaluated-but-padded work,
     // weighted by each shape's relative pair rate, measured on GB300: the
     // packed K = 8 kernel 1.0, its split-j forms 0.95, K = 4 0.99, K = 2 x
     // 128 0.93, one particle per thread 0.80. Ensembles (eight of them, 64 ..
     // 65536 particles per cluster) add K = 4 x 64 at 0.99, ahead of 4 x 128
-    // (the same rate with half the i-tile), and rate the 128-thread split-j
+    // (the same rate with half the i-tile), K = 2 x 64 with 128-record
+    // j-tiles at 0.93 (clusters of a few hundred), and rate the 128-thread split-j
     // form 0.75 (0.29 against 0.67 of the FP32 bound for 4096 clusters of
     // 256); interaction lists keep their measured set (groups of 256 against
     // 4096-record lists: the 256-thread split-j form 0.72, 4 x 64 below 0.70).
@@ -1157,14 +1159,15 @@ cn_status build_group_plan(const std::vector<Group>& groups, bool lists, int64_t
     static const Cand cands[] = {{8, 256, 1, 512, 1.0, 3},   {8, 256, 2, 512, 0.95, 3}, {8, 256, 4, 512, 0.95, 3},
                                  {8, 256, 8, 512, 0.95, 3},  {8, 128, 8, 512, 0.94, 2}, {8, 128, 8, 512, 0.75, 1},
                                  {4, 64, 1, 256, 0.99, 1},   {4, 128, 1, 256, 0.99, 3}, {2, 128, 1, 256, 0.93, 3},
-                                 {1, 128, 1, 256, 0.80, 3}};
+                                 {2, 64, 1, 128, 0.93, 1},   {1, 128, 1, 256, 0.80, 3}};
     double best = -1.0;
     for (const Cand& c : cands) {
       if (!(c.use & (lists ? 2 : 1))) continue;
       if (guard && (c.j_lanes > 1 || c.k > 1)) continue;  // the guarded kernels hold one particle, no split-j
       const int64_t it = static_cast<int64_t>(c.k) * c.threads / c.j_lanes;
       double padded = 0.0;
-      for (const Group& gr : groups) padded += static_cast<double>(ceil_div(gr.ni, it) * it) * static_cast<double>(gr.nj);
+      for (const Group& gr : groups)
+        padded += static_cast<double>(ceil_div(gr.ni, it) * it) * static_cast<double>(ceil_div(gr.nj, c.j_tile) * c.j_tile);
       const double score = padded > 0.0 ? pairs / padded * c.rate : c.rate;
       if (score > best) {
         best = score;
