@@ -402,11 +402,14 @@ cn_tune mid_f32_tune(int64_t n_i, int64_t n_j, int sms) {
 // padded with zero masses, so every unit costs the same). For the shape's
 // i-tile this picks the j-tile, a multiple of `step` in [lo, hi] and no
 // longer than the j set, with the least work on the busiest CTA, counting
-// 64 records of overhead per unit; ties take the smaller tile. Measured at
-// N = 8192 .. 131072 (graph-replayed launches), it picked the fastest or a
-// tile within 1% of it at each size of the sweeps (N = 14000: 0.44 -> 0.72
-// of the FP32 bound, 28000: 0.72 -> 0.80, 98304: 0.836 -> 0.852).
-int32_t fit_j_tile(int64_t n_i, int64_t n_j, int64_t i_tile, int32_t lo, int32_t hi, int32_t step, int64_t ctas) {
+// `unit_cost` records of overhead per unit (64 for the 12-operation FP32
+// pair, proportionally fewer for costlier pairs); ties take the smaller
+// tile. Measured at N = 8192 .. 131072 (graph-replayed launches), it picked
+// the fastest or a tile within 1% of it at each size of the sweeps
+// (N = 14000: 0.44 -> 0.72 of the FP32 bound, 28000: 0.72 -> 0.80,
+// 98304: 0.836 -> 0.852).
+int32_t fit_j_tile(int64_t n_i, int64_t n_j, int64_t i_tile, int32_t lo, int32_t hi, int32_t step, int64_t ctas,
+                   int32_t unit_cost = 64) {
   const int64_t n_it = (n_i + i_tile - 1) / i_tile;
   // the padding of a short tile is written by one thread
   const int64_t nj_up = (std::max<int64_t>(n_j, 1) + step - 1) / step * step;
@@ -418,7 +421,7 @@ int32_t fit_j_tile(int64_t n_i, int64_t n_j, int64_t i_tile, int32_t lo, int32_t
   for (int32_t t = lo; t <= hi; t += step) {
     const int64_t units = n_it * ((std::max<int64_t>(n_j, 1) + t - 1) / t);
     const int64_t g = std::max<int64_t>(1, std::min(units, ctas));
-    const double c = static_cast<double>((units + g - 1) / g) * static_cast<double>(t + 64);
+    const double c = static_cast<double>((units + g - 1) / g) * static_cast<double>(t + unit_cost);
     if (best < 0.0 || c < best) {
       best = c;
       best_t = t;
@@ -526,11 +529,26 @@ cn_tune default_tune(int variant, int64_t n_i, int64_t n_j, int sms) {
     t.threads = 256;
     const int32_t jt0 = n < 98304 ? 512 : 1024;
     t.j_tile = fit_j_tile(n_i, n_j, static_cast<int64_t>(t.i_per_thread) * t.threads, jt0 / 2, 2 * jt0, 16, sms);
+  } else if (dd && n >= 20000) {
+    // compensated form, K = 4 x 256 (measured at N = 24576 .. 131072), the
+    // j-tile fitted to the schedule within 256 .. 1024 records; its pair
+    // costs 82 FP32 lane operations, so a unit's overhead is about 9
+    // records (N = 32768: 256-record tiles, 0.801 of its bound against
+    // 0.782 with 1024; 24576: 1024, 0.758)
+    t.i_per_thread = 4;
+    t.threads = 256;
+    t.j_tile = fit_j_tile(n_i, n_j, 1024, 256, 1024, 16, sms, 9);
+  } else if (dd && n >= 4096 && n < 12000) {
+    // compensated form, small systems: one i-particle per thread keeps the
+    // i-tiles small enough to fill the SMs (N = 8192: 0.595 of its bound
+    // against 0.548 for K = 2 x 128; 4096: 0.418 against 0.397)
+    t.i_per_thread = 1;
+    t.j_tile = 256;
   } else if (n >= 32768) {
     // measured optima (packed forms): FP32 K = 8 x 256 threads at N = 131072,
-    // compensated K = 4 x 256, adjoint (N = 65536) and force-jerk
-    // (N = 131072) K = 4 x 256 with j-tiles of 256 two-record j entries
-    t.i_per_thread = adj ? 4 : (dd ? 4 : 8);
+    // adjoint (N = 65536) and force-jerk (N = 131072) K = 4 x 256 with
+    // j-tiles of 256 two-record j entries
+    t.i_per_thread = adj ? 4 : 8;
     t.threads = 256;
     t.j_tile = adj ? 256 : 1024;
   } else if (n >= 4096) {
