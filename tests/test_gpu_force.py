@@ -91,6 +91,25 @@ def test_default_shapes_with_fitted_j_tiles(n_i, n_j):
     assert shape["j_tile"] % 16 == 0
 
 
+@pytest.mark.parametrize("n_i,n_j", [(24576, 24576), (20000, 13000), (8192, 8192)])
+def test_dd_default_shapes_by_size(n_i, n_j):
+    """The compensated form's default shapes: one i-particle per thread below
+    N = 12000, K = 4 x 256 with a j-tile fitted to the schedule above 20000
+    (432 records at 24576, 528 at 20000 on a 152-SM GB300)."""
+    cn = lib()
+    torch = torch_cuda()
+    pi, pj = synth.plummer(n_i, n_i + 5), synth.plummer(n_j, n_j + 6)
+    eps2 = float(np.float32(synth.plummer_eps(max(n_i, n_j))) ** 2)
+    cn.cn_tune_set("dd", n_i, n_j, None)
+    shape = cn.cn_tune_get("dd", n_i, n_j)
+    acc, _ = cn.cn_force_dd(dev_tensor(pi), dev_tensor(pj), eps2)
+    torch.cuda.synchronize()
+    assert cn.cn_get_device_status() == 0
+    rows = synth.sample_rows(n_i, 512, seed=n_i + 7)
+    ref, _ = oracle.force(pi, pj, eps2, rows=rows, potential=False)
+    assert e_max(acc.cpu().numpy()[rows], ref) <= TOL_DD, shape
+
+
 def test_fitted_j_tiles_include_non_powers_of_two():
     """The sizes above exercise j-tiles that are not powers of two (on a
     152-SM GB300: 9000 -> 2304, 14000 -> 1280, 22000 -> 3200, 45000 -> 944)."""
