@@ -473,7 +473,7 @@ cn_tune default_tune(int variant, int64_t n_i, int64_t n_j, int sms) {
     // (K, threads, lane groups) per band and the window of the j-tile fit;
     // fractions of the FP32 bound measured with the fitted j-tile
     static const Band bands[] = {
-        {8600.0, 4, 256, 8, 2048, 4096},   // N = 8192: 0.563
+        {8600.0, 4, 256, 8, 512, 4096},    // N = 7000: 0.516, 8000: 0.562, 8192: 0.557
         {40000.0, 8, 256, 8, 512, 4096},   // 9000: 0.60, 14000: 0.72, 16384: 0.74, 20000: 0.76,
                                            // 24576: 0.80, 32768: 0.82, 40000: 0.81
     };
