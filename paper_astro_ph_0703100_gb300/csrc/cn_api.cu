@@ -359,43 +359,6 @@ cn_tune sym_default_tune(int64_t n, int sms, bool pot) {
   return best;
 }
 
-// Launch shape of the plain FP32 form for mid-size systems (4096 < n_i <=
-// 20000; measured best shapes there are split-j with lane groups of 4 and
-// two i-particles per group). Few units per resident slot make the static
-// schedule quantise (n_i = 6000 in 564 units over 456 slots takes two
-// rounds), so the j-tile and block size come from the same schedule model
-// as the symmetric form: the busiest SM's CTAs x units per CTA x unit work,
-// at a rate that saturates with about six warps per SM. Resident CTAs per
-// SM follow from 158 registers per thread and the ring's shared memory.
-cn_tune mid_f32_tune(int64_t n_i, int64_t n_j, int sms) {
-  struct Shape {
-    int threads, j_tile, slots_per_sm;
-  };
-  static const Shape shapes[] = {{128, 1024, 3}, {128, 2048, 2}, {128, 4096, 1},
-                                 {256, 1024, 1}, {256, 2048, 1}, {256, 4096, 1}};
-  cn_tune best{};
-  double best_t = 0.0;
-  for (const Shape& sh : shapes) {
-    const int64_t it = sh.threads / 2;  // two i-particles per group of four lanes
-    const int64_t units = ((n_i + it - 1) / it) * ((std::max<int64_t>(n_j, 1) + sh.j_tile - 1) / sh.j_tile);
-    const int64_t g = std::min<int64_t>(static_cast<int64_t>(sh.slots_per_sm) * sms, units);
-    const int64_t per_sm = (g + sms - 1) / sms;
-    const int64_t per_cta = (units + g - 1) / g;
-    const double warps = static_cast<double>(per_sm) * sh.threads / 32.0;
-    const double t = static_cast<double>(per_sm * per_cta) * static_cast<double>(it * sh.j_tile) /
-                     std::min(1.0, warps / 6.0);
-    if (best_t == 0.0 || t < best_t) {
-      best_t = t;
-      best.i_per_thread = 2;
-      best.threads = sh.threads;
-      best.j_tile = sh.j_tile;
-      best.j_lanes = 4;
-      best.stages = n_j <= sh.j_tile ? 1 : 3;
-    }
-  }
-  return best;
-}
-
 // The packed shapes of 256 threads with four or eight i-particles per lane
 // (split-j or not) run one CTA per SM, and the static schedule gives each
 // CTA ceil(units / CTAs) units of j_tile records (a ragged last j-tile is
@@ -463,7 +426,7 @@ cn_tune default_tune(int variant, int64_t n_i, int64_t n_j, int sms) {
     // eight i-particles keep the i-tiles small enough to fill the SMs while
     // each j record feeds several packed pair terms. Sizes are compared by the
     // work per SM, n_eff = sqrt(n_i n_j) sqrt(152 / sms), so another SM count
-    // moves the bands. Below 6500 the schedule model of mid_f32_tune decides.
+    // moves the bands.
     const double n_eff = std::sqrt(static_cast<double>(n_i) * static_cast<double>(std::max<int64_t>(n_j, 1))) *
                          std::sqrt(152.0 / std::max(sms, 1));
     struct Band {
@@ -473,12 +436,12 @@ cn_tune default_tune(int variant, int64_t n_i, int64_t n_j, int sms) {
     // (K, threads, lane groups) per band and the window of the j-tile fit;
     // fractions of the FP32 bound measured with the fitted j-tile
     static const Band bands[] = {
+        {6500.0, 2, 256, 4, 512, 4096},    // N = 4500: 0.397, 6000: 0.503, 6400: 0.552
         {8600.0, 4, 256, 8, 512, 4096},    // N = 7000: 0.516, 8000: 0.562, 8192: 0.557
         {40000.0, 8, 256, 8, 512, 4096},   // 9000: 0.60, 14000: 0.72, 16384: 0.74, 20000: 0.76,
                                            // 24576: 0.80, 32768: 0.82, 40000: 0.81
     };
-    if (n_i > 4096 && n_eff <= 6500.0) return mid_f32_tune(n_i, n_j, sms);
-    if (n_i > 4096 && n_eff <= bands[1].upto) {
+    if (n_i > 4096 && n_eff <= bands[2].upto) {
       for (const Band& b : bands) {
         if (n_eff > b.upto) continue;
         t.i_per_thread = b.k;
