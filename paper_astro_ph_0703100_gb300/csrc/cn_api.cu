@@ -1981,6 +1981,16 @@ cn_status cn_autotune(int variant, int64_t n_i, const float* pos_i, int64_t n_j,
   cn_tune best{};
   cn_status result = CN_OK;
   std::vector<cn_tune> cands;
+  {
+    // the default shape of these sizes first (its j-tile fitted to the
+    // schedule, which the grid below does not contain), so that the result
+    // is never slower than the default by more than the timing noise
+    int dev = 0;
+    DeviceInfo* d = nullptr;
+    cn_status st = current_device(&dev, &d);
+    if (st != CN_OK) return st;
+    cands.push_back(default_tune(variant, n_i, n_j, d->sms));
+  }
   for (int k : ks) {
     if (!valid_k(variant, k)) continue;
     for (int th : ths) {
