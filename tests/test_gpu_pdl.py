@@ -16,6 +16,7 @@ import subprocess
 import sys
 import textwrap
 
+import numpy as np
 import pytest
 
 from conftest import ROOT
@@ -60,6 +61,45 @@ def test_chained_calls_match_synchronised_calls():
         assert cn.cn_get_device_status() == 0
         assert torch.equal(out2, ref2), it
         assert torch.equal(sym, refs), it
+
+
+def test_chained_adjoint_compensated_and_batched_calls():
+    """The adjoint takes as its weights the accelerations a cn_force call
+    has just written (its weight-packing kernel and its pair kernel both
+    follow that call), the compensated form and a batch plan read records
+    that call wrote; no host synchronisation in between, compared bit for
+    bit with the same calls synchronised one by one."""
+    cn = lib()
+    torch = torch_cuda()
+    n = 2000
+    p = dev_tensor(synth.plummer(n, 41))
+    offs = np.array([0, 700, 1200, n * 3 // 4], dtype=np.int64)
+    eps2s = np.array([1e-2, 2e-2, 5e-3], dtype=np.float32)
+    plan = cn.BatchPlan(offs, eps2s)
+
+    def run(sync):
+        w = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+        cn.cn_force(p, p, 1e-3, acc_out=w)
+        if sync:
+            torch.cuda.synchronize()
+        gp, gm = cn.cn_force_adjoint(p, 1e-3, w)
+        if sync:
+            torch.cuda.synchronize()
+        recs = w.view(-1, 4)  # n * 3 floats as (n * 3 / 4) records
+        dd, _ = cn.cn_force_dd(recs, recs, 1e-2)
+        if sync:
+            torch.cuda.synchronize()
+        ens, _ = plan.run(recs)
+        torch.cuda.synchronize()
+        return [x.clone() for x in (w, gp, gm, dd, ens)]
+
+    ref = run(True)
+    for _ in range(5):
+        got = run(False)
+        assert cn.cn_get_device_status() == 0
+        for a, b in zip(got, ref):
+            assert torch.equal(a, b)
+    plan.close()
 
 
 def test_chained_calls_in_a_captured_graph():
