@@ -320,6 +320,19 @@ int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 // reductions per pair), while small systems need small tiles to fill the
 // SMs.
 cn_tune sym_default_tune(int64_t n, int sms, bool pot) {
+  if (pot && n >= 28000) {
+    // with the potential, measured from N = 32768 to 131072: K = 8 x 128 runs
+    // 2-2.7% ahead of 4 x 256 (131072: 6.41 against 6.54 ms), which the
+    // schedule model below does not see (it charges multi-CTA shapes for
+    // their busiest CTA); at 24576 and below 4 x 256 stays ahead
+    cn_tune t{};
+    t.i_per_thread = 8;
+    t.threads = 128;
+    t.j_tile = 256;
+    t.stages = 4;
+    t.j_lanes = 1;
+    return t;
+  }
   struct Shape {
     int k, threads, j_tile, stages, slots_per_sm;
     double rate, rate_pot;  // saturated effective pairs/s without and with the potential
