@@ -500,10 +500,13 @@ cn_tune default_tune(int variant, int64_t n_i, int64_t n_j, int sms) {
   } else if (f32 && n > 4096) {
     // packed FP32, measured at N = 49152 .. 131072 (smaller systems take the
     // bands above): K = 4 x 256 below ~96K, K = 8 x 256 above, with the
-    // j-tile fitted to the schedule from 512 or 1024 records
-    t.i_per_thread = n < 98304 ? 4 : 8;
+    // j-tile fitted to the schedule from 512 or 1024 records. With the
+    // potential K = 4 stays ahead at large N too (131072: 0.793 of its
+    // 14-operation bound against 0.778 for K = 8)
+    const bool k4 = n < 98304 || variant == cn::kF32Pot;
+    t.i_per_thread = k4 ? 4 : 8;
     t.threads = 256;
-    const int32_t jt0 = n < 98304 ? 512 : 1024;
+    const int32_t jt0 = k4 ? 512 : 1024;
     t.j_tile = fit_j_tile(n_i, n_j, static_cast<int64_t>(t.i_per_thread) * t.threads, jt0 / 2, 2 * jt0, 16, sms);
   } else if (dd && n >= 20000) {
     // compensated form, K = 4 x 256 (measured at N = 24576 .. 131072), the
