@@ -17,7 +17,8 @@
  *
  * Conventions shared by every entry point:
  *  - Array arguments are DEVICE pointers owned by the caller unless the
- *    name says "host". Particle arrays are float[n][4] records
+ *    name says "host", in memory of the current device (kernels launch on
+ *    the current device; the library does not check where a pointer lives). Particle arrays are float[n][4] records
  *    (x, y, z, m), 16-byte aligned (else CN_ERR_MISALIGNED); the 4th
  *    component of an i-record is ignored. The i and j arrays may be the
  *    same buffer. Outputs must not overlap inputs.

@@ -91,6 +91,7 @@ def _torch():
 
 
 _current_stream = None  # () -> cudaStream_t of PyTorch's current stream on the current device
+_current_device = None  # () -> index of the current CUDA device
 
 
 def _stream_handle(stream):
@@ -115,12 +116,37 @@ def _ptr(t):
     return None if t is None else t.data_ptr()
 
 
+def _device_index():
+    """Index of the current CUDA device (the library launches there)."""
+    global _current_device
+    if _current_device is None:
+        torch = _torch()
+        dev = getattr(torch._C, "_cuda_getDevice", None)
+        _current_device = dev if dev is not None else torch.cuda.current_device
+    return _current_device()
+
+
+def _on_current_device(t, name):
+    if t.get_device() != _device_index():
+        raise TypeError(f"{name} is on cuda:{t.get_device()}, but the current device is cuda:{_device_index()} "
+                        "(the library launches on the current device; use torch.cuda.device(...))")
+
+
+def _like(t, ref, name):
+    """A further CUDA tensor of a call: contiguous and on the device of `ref`."""
+    torch = _torch()
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous() and t.device == ref.device):
+        raise TypeError(f"{name} must be a contiguous CUDA tensor on {ref.device}")
+    return t
+
+
 def _records(t, name):
     torch = _torch()
     if not (isinstance(t, torch.Tensor) and t.dtype == torch.float32 and t.dim() == 2 and t.shape[1] == 4):
         raise TypeError(f"{name} must be a float32 tensor of shape (n, 4)")
     if not (t.is_cuda and t.is_contiguous()):
         raise TypeError(f"{name} must be a contiguous CUDA tensor")
+    _on_current_device(t, name)
     return t
 
 
@@ -154,6 +180,7 @@ def _force(fn, double, pos_i, pos_mass_j, eps2, acc_out, pot_out, potential, str
         st = getattr(lib, fn)(n_i, _ptr(pos_i), n_j, _ptr(pos_mass_j), float(eps2), _ptr(acc), _ptr(pot),
                               _stream_handle(stream))
     else:
+        _like(ws, pos_i, "workspace")
         st = getattr(lib, fn)(n_i, _ptr(pos_i), n_j, _ptr(pos_mass_j), float(eps2), _ptr(acc), _ptr(pot),
                               _ptr(ws), ws.numel() * ws.element_size(), _stream_handle(stream))
     check(st, fn)
@@ -276,9 +303,11 @@ class BatchPlan:
         acc, pot = self._args(pos_mass, acc_out, pot_out)
         if workspace is None:
             workspace = self.new_workspace(pos_mass.device)
+        _like(workspace, pos_mass, "workspace")
         self._keep = (pos_mass, acc, pot, workspace)
         check(load().cn_batch_plan_capture(self._h, _ptr(pos_mass), _ptr(acc), _ptr(pot), _ptr(workspace),
-                                           workspace.numel(), _stream_handle(stream)), "cn_batch_plan_capture")
+                                           workspace.numel() * workspace.element_size(), _stream_handle(stream)),
+              "cn_batch_plan_capture")
         return acc, pot
 
     def launch(self, stream=None):
@@ -298,7 +327,7 @@ class BatchPlan:
 
 def cn_force_batched(plan: BatchPlan, pos_mass, acc_out=None, pot_out=None, workspace=None, stream=None):
     acc, pot = plan._args(pos_mass, acc_out, pot_out)
-    nbytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
+    nbytes = 0 if workspace is None else _like(workspace, pos_mass, "workspace").numel() * workspace.element_size()
     check(load().cn_force_batched(plan._h, _ptr(pos_mass), _ptr(acc), _ptr(pot), _ptr(workspace), nbytes,
                                   _stream_handle(stream)), "cn_force_batched")
     return acc, pot
@@ -367,9 +396,11 @@ class ListPlan:
         acc, pot = self._args(pos_i, pos_mass_j, acc_out, pot_out)
         if workspace is None:
             workspace = self.new_workspace(pos_i.device)
+        _like(workspace, pos_i, "workspace")
         self._keep = (pos_i, pos_mass_j, acc, pot, workspace)
         check(load().cn_list_plan_capture(self._h, _ptr(pos_i), _ptr(pos_mass_j), _ptr(acc), _ptr(pot),
-                                          _ptr(workspace), workspace.numel(), _stream_handle(stream)),
+                                          _ptr(workspace), workspace.numel() * workspace.element_size(),
+                                          _stream_handle(stream)),
               "cn_list_plan_capture")
         return acc, pot
 
@@ -390,7 +421,7 @@ class ListPlan:
 
 def cn_force_lists(plan: ListPlan, pos_i, pos_mass_j, acc_out=None, pot_out=None, workspace=None, stream=None):
     acc, pot = plan._args(pos_i, pos_mass_j, acc_out, pot_out)
-    nbytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
+    nbytes = 0 if workspace is None else _like(workspace, pos_i, "workspace").numel() * workspace.element_size()
     check(load().cn_force_lists(plan._h, _ptr(pos_i), _ptr(pos_mass_j), _ptr(acc), _ptr(pot), _ptr(workspace),
                                 nbytes, _stream_handle(stream)), "cn_force_lists")
     return acc, pot
@@ -446,8 +477,9 @@ def cn_force_adjoint(pos_mass, eps2, w, grad_pos=None, grad_mass=None, stream=No
     torch = _torch()
     _records(pos_mass, "pos_mass")
     n = pos_mass.shape[0]
-    if w.dtype != torch.float32 or tuple(w.shape) != (n, 3) or not w.is_contiguous() or not w.is_cuda:
-        raise TypeError("w must be a contiguous float32 CUDA tensor of shape (n, 3)")
+    if w.dtype != torch.float32 or tuple(w.shape) != (n, 3):
+        raise TypeError("w must be a float32 tensor of shape (n, 3)")
+    _like(w, pos_mass, "w")
     gp = _out(grad_pos, (n, 3), torch.float32, pos_mass.device, "grad_pos")
     gm = _out(grad_mass, (n,), torch.float32, pos_mass.device, "grad_mass")
     check(load().cn_force_adjoint(n, _ptr(pos_mass), float(eps2), _ptr(w), _ptr(gp), _ptr(gm),
@@ -478,6 +510,7 @@ def cn_force_jerk(pos_i, vel_i, pos_mass_j, vel_j, eps2, acc_out=None, jerk_out=
 def _energy(fn, pos_mass, pot, w_out, stream):
     torch = _torch()
     _records(pos_mass, "pos_mass")
+    _like(pot, pos_mass, "pot")
     w = _out(w_out, (1,), torch.float64, pos_mass.device, "w_out")
     check(getattr(load(), fn)(pos_mass.shape[0], _ptr(pos_mass), _ptr(pot), _ptr(w), _stream_handle(stream)), fn)
     return w
@@ -486,14 +519,14 @@ def _energy(fn, pos_mass, pot, w_out, stream):
 def cn_potential_energy(pos_mass, pot, w_out=None, stream=None):
     """W = 1/2 sum m_i phi_i (FP64, one-element CUDA tensor) from FP32 potentials."""
     torch = _torch()
-    if pot.dtype != torch.float32 or pot.shape[0] != pos_mass.shape[0]:
+    if pot.dtype != torch.float32 or tuple(pot.shape) != (pos_mass.shape[0],):
         raise TypeError("pot must be float32 of length n")
     return _energy("cn_potential_energy", pos_mass, pot, w_out, stream)
 
 
 def cn_potential_energy_dd(pos_mass, pot, w_out=None, stream=None):
     torch = _torch()
-    if pot.dtype != torch.float64 or pot.shape[0] != pos_mass.shape[0]:
+    if pot.dtype != torch.float64 or tuple(pot.shape) != (pos_mass.shape[0],):
         raise TypeError("pot must be float64 of length n")
     return _energy("cn_potential_energy_dd", pos_mass, pot, w_out, stream)
 

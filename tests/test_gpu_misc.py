@@ -215,3 +215,28 @@ def test_tuning_file_save_and_load(tmp_path):
         assert ei.value.code == "CN_ERR_UNSUPPORTED_DEVICE"
     finally:
         cn.cn_tune_set("f32", 3000, 3000, None)
+
+
+def test_binding_rejects_tensors_the_kernels_cannot_read():
+    """Tensors that are not contiguous CUDA memory of the records' device are
+    refused by the binding before anything reaches the library: host
+    potentials for the energy, host or strided workspaces and weights."""
+    cn = lib()
+    torch = torch_cuda()
+    p = dev_tensor(synth.plummer(300, 71))
+    acc, pot = cn.cn_force(p, p, 1e-3, potential=True)
+    with pytest.raises(TypeError):
+        cn.cn_potential_energy(p, pot.cpu())
+    with pytest.raises(TypeError):
+        cn.cn_force_ws(p, p, 1e-3, torch.zeros(1 << 16, dtype=torch.uint8))
+    with pytest.raises(TypeError):
+        cn.cn_force_adjoint(p, 1e-3, torch.zeros((300, 3), dtype=torch.float32))
+    with pytest.raises(TypeError):
+        cn.cn_force_adjoint(p, 1e-3, torch.zeros((3, 300), dtype=torch.float32, device="cuda").t())
+    plan = cn.BatchPlan(np.array([0, 100, 300], dtype=np.int64), np.array([1e-3, 1e-3], dtype=np.float32))
+    with pytest.raises(TypeError):
+        plan.run(p, workspace=torch.zeros(plan.workspace_bytes + 256, dtype=torch.uint8))
+    plan.close()
+    w = cn.cn_potential_energy(p, pot)  # the valid call still works
+    torch.cuda.synchronize()
+    assert np.isfinite(float(w.item()))
