@@ -102,3 +102,26 @@ def test_batched_deterministic_and_autotune():
     torch.cuda.synchronize()
     assert torch.equal(a1, a2)
     plan.close()
+
+
+@pytest.mark.parametrize("kind", ["small_ragged", "equal"])
+def test_default_plan_shapes_small_and_equal_clusters(kind):
+    """The plan's default shape for clusters of a few hundred particles (128-
+    record j-tiles, i and j padding counted) and for equal clusters (static
+    schedule): every cluster against the oracle."""
+    cn = lib()
+    torch = torch_cuda()
+    if kind == "small_ragged":
+        rec, offs, eps2 = synth.ensemble(600, 77, n_lo=64, n_hi=512)
+    else:
+        rec, offs, eps2 = synth.ensemble(200, 78, n_lo=1024, n_hi=1024)
+    plan = cn.BatchPlan(offs, eps2)
+    acc, _ = plan.run(dev_tensor(rec))
+    torch.cuda.synchronize()
+    assert cn.cn_get_device_status() == 0
+    acc = acc.cpu().numpy()
+    for c in range(0, len(offs) - 1, 7):
+        lo, hi = offs[c], offs[c + 1]
+        ref, _ = oracle.force(rec[lo:hi], rec[lo:hi], eps2[c], potential=False)
+        assert e_max(acc[lo:hi], ref) <= TOL_F32, c
+    plan.close()
