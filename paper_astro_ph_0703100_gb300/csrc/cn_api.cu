@@ -434,10 +434,10 @@ cn_tune default_tune(int variant, int64_t n_i, int64_t n_j, int sms) {
     return t;
   }
   if (f32) {
-    // Mid-size systems (measured on GB300, 152 SMs, N = 5000 .. 65536,
-    // graph-replayed launches): split-j lane groups of 8 holding four or
-    // eight i-particles keep the i-tiles small enough to fill the SMs while
-    // each j record feeds several packed pair terms. Sizes are compared by the
+    // Mid-size systems (measured on GB300, 152 SMs, N = 4200 .. 40000,
+    // graph-replayed launches): split-j lane groups of 4 or 8 holding two,
+    // four or eight i-particles keep the i-tiles small enough to fill the
+    // SMs while each j record feeds several packed pair terms. Sizes are compared by the
     // work per SM, n_eff = sqrt(n_i n_j) sqrt(152 / sms), so another SM count
     // moves the bands.
     const double n_eff = std::sqrt(static_cast<double>(n_i) * static_cast<double>(std::max<int64_t>(n_j, 1))) *
@@ -524,14 +524,15 @@ cn_tune default_tune(int variant, int64_t n_i, int64_t n_j, int sms) {
     t.i_per_thread = 1;
     t.j_tile = 256;
   } else if (n >= 32768) {
-    // measured optima (packed forms): FP32 K = 8 x 256 threads at N = 131072,
-    // adjoint (N = 65536) and force-jerk (N = 131072) K = 4 x 256 with
-    // j-tiles of 256 two-record j entries
+    // measured optima of the adjoint (N = 65536) and the force-jerk form
+    // (N = 131072): K = 4 x 256 with j-tiles of 256 two-record j entries
     t.i_per_thread = adj ? 4 : 8;
     t.threads = 256;
     t.j_tile = adj ? 256 : 1024;
   } else if (n >= 4096) {
-    t.i_per_thread = 2;  // measured at N = 16384: K = 2 x 128 threads x 256 records
+    // the compensated form between N = 12000 and 20000 (measured at 16384:
+    // K = 2 x 128 threads x 256 records, 0.755 of its bound)
+    t.i_per_thread = 2;
     t.j_tile = 256;
   } else {
     t.i_per_thread = adj ? 1 : 2;
