@@ -108,3 +108,21 @@ def test_eps_i_plummer_131072_sampled():
     rows = synth.sample_rows(n, 1024, 67)
     ra, _ = oracle.force_eps_i(pi, p, rows=rows, potential=False)
     assert e_max(a.cpu().numpy()[rows], ra) <= TOL
+
+
+@pytest.mark.parametrize("n_i,n_j", [(16384, 16384), (20000, 9000)])
+def test_eps_i_mid_size_default_shape_sampled(n_i, n_j):
+    """Mid sizes, where the plain form's default uses lane groups of 8 with
+    eight i-particles; the per-i-softening kernels hold at most two per lane
+    group, so the plan takes two (with and without the potential)."""
+    cn = lib()
+    torch = torch_cuda()
+    p = synth.plummer(n_j, n_j + 68)
+    pi = _with_eps(synth.plummer(n_i, n_i + 69), 70)
+    a, pot = cn.cn_force_eps_i(dev_tensor(pi), dev_tensor(p), potential=True)
+    torch.cuda.synchronize()
+    assert cn.cn_get_device_status() == 0
+    rows = synth.sample_rows(n_i, 512, 71)
+    ra, rp = oracle.force_eps_i(pi, p, rows=rows)
+    assert e_max(a.cpu().numpy()[rows], ra) <= TOL
+    assert rel_pot_err(pot.cpu().numpy()[rows], rp) <= TOL
