@@ -457,11 +457,16 @@ cn_tune default_tune(int variant, int64_t n_i, int64_t n_j, int sms) {
     if (n_i > 4096 && n_eff <= bands[2].upto) {
       for (const Band& b : bands) {
         if (n_eff > b.upto) continue;
-        t.i_per_thread = b.k;
+        // with the potential the K = 8 split-j kernel runs short of registers
+        // (N = 16384: 0.561 of its 14-operation bound); K = 4 with lane groups
+        // of 4 keeps the 256-particle i-tile (0.689; 24576: 0.731, 32768: 0.744)
+        const bool pot_k8 = variant == cn::kF32Pot && b.k == 8;
+        const int k = pot_k8 ? 4 : b.k;
+        const int jl = pot_k8 ? 4 : b.j_lanes;
+        t.i_per_thread = k;
         t.threads = b.threads;
-        t.j_lanes = b.j_lanes;
-        t.j_tile = fit_j_tile(n_i, n_j, static_cast<int64_t>(b.k) * b.threads / b.j_lanes, b.jt_lo, b.jt_hi,
-                              8 * b.j_lanes, sms);
+        t.j_lanes = jl;
+        t.j_tile = fit_j_tile(n_i, n_j, static_cast<int64_t>(k) * b.threads / jl, b.jt_lo, b.jt_hi, 8 * jl, sms);
         t.stages = n_j <= t.j_tile ? 1 : 3;
         return t;
       }

@@ -110,6 +110,25 @@ def test_dd_default_shapes_by_size(n_i, n_j):
     assert e_max(acc.cpu().numpy()[rows], ref) <= TOL_DD, shape
 
 
+@pytest.mark.parametrize("n_i,n_j", [(16384, 16384), (24576, 13000)])
+def test_potential_default_shapes_mid_size(n_i, n_j):
+    """With the potential the mid-size default takes K = 4 with lane groups
+    of 4 (the K = 8 split-j kernel runs short of registers there)."""
+    cn = lib()
+    torch = torch_cuda()
+    pi, pj = synth.plummer(n_i, n_i + 11), synth.plummer(n_j, n_j + 12)
+    eps2 = float(np.float32(synth.plummer_eps(max(n_i, n_j))) ** 2)
+    cn.cn_tune_set("f32_pot", n_i, n_j, None)
+    shape = cn.cn_tune_get("f32_pot", n_i, n_j)
+    acc, pot = cn.cn_force(dev_tensor(pi), dev_tensor(pj), eps2, potential=True)
+    torch.cuda.synchronize()
+    assert cn.cn_get_device_status() == 0
+    rows = synth.sample_rows(n_i, 512, seed=n_i + 13)
+    ref_a, ref_p = oracle.force(pi, pj, eps2, rows=rows)
+    assert e_max(acc.cpu().numpy()[rows], ref_a) <= TOL_F32, shape
+    assert rel_pot_err(pot.cpu().numpy()[rows], ref_p) <= TOL_F32, shape
+
+
 def test_fitted_j_tiles_include_non_powers_of_two():
     """The sizes above exercise j-tiles that are not powers of two (on a
     152-SM GB300: 9000 -> 2304, 14000 -> 1280, 22000 -> 3200, 45000 -> 944)."""
