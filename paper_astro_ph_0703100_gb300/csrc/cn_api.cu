@@ -1194,6 +1194,14 @@ cn_status build_group_plan(const std::vector<Group>& groups, bool lists, int64_t
         fitted.j_tile = c.j_tile;
       }
     }
+    // with the potential the K = 8 split-j kernel runs short of registers:
+    // K = 4 with half the lane groups keeps the i-tile (lists of 4096 records
+    // for groups of 256: 0.525 -> 0.712 of the 14-operation bound)
+    if (with_pot && fitted.i_per_thread == 8 && fitted.j_lanes > 1) {
+      fitted.i_per_thread = 4;
+      fitted.j_lanes /= 2;
+      if (fitted.j_lanes < 2) fitted.j_lanes = 0;
+    }
     tune = &fitted;
   }
   Plan p;
