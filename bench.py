@@ -742,6 +742,48 @@ def measure_rows(args, cn, torch, device, peak):
     lp.close()
     del ti, tj, acc_l, ws_l
 
+    # The same structure with the lists as index arrays into one source array
+    # (the particles followed by 32768 tree-node records), gathered by the
+    # kernel; beside it the contiguous plan (its own default shape) on the
+    # same records laid out in list order, which shows what the gather costs
+    pos_i, i_off, src, jidx, jb, jc = synth.interaction_lists_indexed(131072, 256, 4096, seed=131072)
+    lx = cn.ListPlan(i_off, jb, jc, eps2, j_index=jidx)
+    lc = cn.ListPlan(i_off, jb, jc, eps2)
+    ti, ts = torch.from_numpy(pos_i).to(device), torch.from_numpy(src).to(device)
+    tl = torch.from_numpy(src[jidx]).to(device)
+    acc_x = torch.empty((pos_i.shape[0], 3), dtype=torch.float32, device=device)
+    acc_c = torch.empty_like(acc_x)
+    with torch.cuda.stream(side):
+        ws_x, ws_c = lx.new_workspace(device), lc.new_workspace(device)
+        lx.capture(ti, ts, acc_x, workspace=ws_x, stream=side)
+        lc.capture(ti, tl, acc_c, workspace=ws_c, stream=side)
+        for _ in range(3):
+            lx.launch(side)
+            lc.launch(side)
+        ms_x = _events_ms(torch, lambda: lx.launch(side), 20, side)
+        ms_c = _events_ms(torch, lambda: lc.launch(side), 20, side)
+    torch.cuda.synchronize()
+    a_host = acc_x.cpu().numpy()
+    errs, t_or, n_or = [], 0.0, 0
+    for g in range(0, len(jc), 64):
+        lo, hi = int(i_off[g]), int(i_off[g + 1])
+        recs = src[jidx[jb[g]:jb[g] + jc[g]]]
+        t0 = time.perf_counter()
+        ref, _ = oracle.force(pos_i[lo:hi], recs, eps2, potential=False)
+        t_or += time.perf_counter() - t0
+        n_or += (hi - lo) * int(jc[g])
+        errs.append(oracle.e_max(a_host[lo:hi], ref))
+    rows["tree_lists_indexed131072"] = {
+        "pairs": lx.pairs, "pairs_per_s": lx.pairs / (ms_x / 1e3), "ms": ms_x,
+        "frac": lx.pairs / (ms_x / 1e3) / peak, "emax": max(errs),
+        "contiguous_same_records": {"pairs_per_s": lc.pairs / (ms_c / 1e3), "ms": ms_c,
+                                    "frac": lc.pairs / (ms_c / 1e3) / peak},
+        "cpu_baseline": {"value": n_or / t_or, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+                         "sample": "every 64th group against its gathered list"}}
+    lx.close()
+    lc.close()
+    del ti, ts, tl, acc_x, acc_c, ws_x, ws_c
+
     # C5: adjoint at N = 65536, eps = 0.01
     n = 65536
     p = synth.plummer(n, 65536)
@@ -798,6 +840,15 @@ def run_only(args):
         eps2 = float(np.float32(0.01) ** 2)
         lp = cn.ListPlan(i_off, jb, jc, eps2, tune=dict(tune) if tune else None)
         ti, tj = torch.from_numpy(pos_i).to(device), torch.from_numpy(lists).to(device)
+        out = torch.empty((pos_i.shape[0], 3), dtype=torch.float32, device=device)
+        ws_l = lp.new_workspace(device)
+        step = lambda: lp.run(ti, tj, acc_out=out, workspace=ws_l)
+        pairs = lp.pairs
+    elif args.only == "lists_indexed":
+        pos_i, i_off, src, jidx, jb, jc = synth.interaction_lists_indexed(n, 256, 4096, seed=n)
+        eps2 = float(np.float32(0.01) ** 2)
+        lp = cn.ListPlan(i_off, jb, jc, eps2, tune=dict(tune) if tune else None, j_index=jidx)
+        ti, tj = torch.from_numpy(pos_i).to(device), torch.from_numpy(src).to(device)
         out = torch.empty((pos_i.shape[0], 3), dtype=torch.float32, device=device)
         ws_l = lp.new_workspace(device)
         step = lambda: lp.run(ti, tj, acc_out=out, workspace=ws_l)
@@ -905,7 +956,7 @@ def main(argv=None):
                     help="target seconds of oracle work for cpu_baseline (sized from a short probe that runs slower "
                          "than the sample: about 10 s are spent)")
     ap.add_argument("--ref-rows", type=int, default=256, help="oracle rows per step of --impl reference")
-    ap.add_argument("--only", choices=("f32", "dd", "adjoint", "batched", "jerk", "sym", "lists"),
+    ap.add_argument("--only", choices=("f32", "dd", "adjoint", "batched", "jerk", "sym", "lists", "lists_indexed"),
                     help="time one kernel family alone (profiling mode; prints its own JSON)")
     ap.add_argument("--tune", help="pinned launch shape for --only: i_per_thread,threads,j_tile,stages")
     ap.add_argument("--chunk", type=int, default=0, help="dynamic chunk size for --only batched")

@@ -320,9 +320,40 @@ CN_API cn_status cn_list_plan_create(int32_t n_groups, const int64_t *i_offsets_
                                      const int64_t *j_count_host, const float *eps2_host, const cn_tune *tune,
                                      int with_potential, cn_batch_plan **plan_out);
 
+/* Interaction lists as index arrays: the form a tree code's walk produces
+ * (Section 4.4), where a list names particles and tree nodes of one source
+ * array instead of holding copies of their records. Group g evaluates its
+ * i-particles against the records pos_mass_j[j_index[e]] for the entries
+ * e = j_begin[g] .. j_begin[g] + j_count[g] - 1 of j_index, in that order;
+ * entries may repeat and lists may share or overlap entries. The kernel
+ * gathers each j-tile's records into shared memory itself (no copy of the
+ * lists is written to device memory).
+ *   i_offsets_host, j_begin_host, j_count_host, eps2_host : as for
+ *                    cn_list_plan_create, with j ranges counting entries
+ *   j_index_host   : int32[n_index] (NULL only when n_index == 0), copied
+ *                    into the plan; the host array is not kept
+ *   n_src          : number of records of the source array that
+ *                    cn_force_lists will read (at most INT32_MAX)
+ * Every entry a group with i-particles reaches must lie in 0 .. n_src - 1,
+ * and every list inside 0 .. n_index - 1: checked here, on the host;
+ * CN_ERR_INVALID_ARG otherwise. The plan runs with cn_force_lists (and
+ * cn_list_plan_capture), pos_mass_j then being the n_src source records. A
+ * plan made by cn_list_plan_create with the same arguments and the same
+ * launch shape (tune), run on the records pos_mass_j[j_index[e]] laid out
+ * in entry order, gives the same bits (the same records in the same order).
+ * Without a tune the two may differ in shape: where the fit lands on K = 8
+ * with lane groups, a gathering plan takes K = 4 with half of them (its
+ * threads also stage the records). */
+CN_API cn_status cn_list_plan_create_indexed(int32_t n_groups, const int64_t *i_offsets_host,
+                                             const int64_t *j_begin_host, const int64_t *j_count_host,
+                                             const float *eps2_host, const int32_t *j_index_host, int64_t n_index,
+                                             int64_t n_src, const cn_tune *tune, int with_potential,
+                                             cn_batch_plan **plan_out);
+
 /* One persistent launch over all groups of a list plan.
  *   pos_i      : float[n_i][4] (n_i = i_offsets[n_groups]; 4th component ignored)
  *   pos_mass_j : float[*][4] lists, long enough for every group's range
+ *                (gathering plans: the n_src source records)
  *   acc_out    : float[n_i][3]; pot_out : float[n_i] or NULL (groups with an
  *                empty list get zeros)
  *   workspace  : as for cn_force_batched. */

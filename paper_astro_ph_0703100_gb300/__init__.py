@@ -40,6 +40,7 @@ __all__ = [
     "cn_batch_plan_capture",
     "cn_batch_plan_launch",
     "cn_list_plan_create",
+    "cn_list_plan_create_indexed",
     "cn_list_plan_capture",
     "cn_status_string",
     "cn_last_error_message",
@@ -339,9 +340,16 @@ class ListPlan:
     Group g: i-particles ``i_offsets[g]:i_offsets[g+1]`` of ``pos_i`` against
     records ``j_begin[g]:j_begin[g]+j_count[g]`` of ``pos_mass_j``, softening
     ``eps2[g]`` (a scalar applies to every group).
+
+    With ``j_index`` (int32 list entries, each the index of a source record)
+    the lists are index arrays: group g's records are
+    ``pos_mass_j[j_index[e]]`` for the entries
+    ``e = j_begin[g] .. j_begin[g]+j_count[g]-1``, gathered by the kernel;
+    ``pos_mass_j`` is then the source array of ``n_src`` records (by default
+    one past the largest index).
     """
 
-    def __init__(self, i_offsets, j_begin, j_count, eps2, tune=None, potential=False):
+    def __init__(self, i_offsets, j_begin, j_count, eps2, tune=None, potential=False, j_index=None, n_src=None):
         self.i_offsets = np.ascontiguousarray(np.asarray(i_offsets, dtype=np.int64))
         n_groups = self.i_offsets.shape[0] - 1
         self.j_begin = np.ascontiguousarray(np.asarray(j_begin, dtype=np.int64))
@@ -355,9 +363,26 @@ class ListPlan:
         t = ctypes.byref(_tune_struct(tune)) if tune is not None else None
         lib = load()
         vpd = lambda a: a.ctypes.data_as(ctypes.c_void_p)
-        check(lib.cn_list_plan_create(n_groups, vpd(self.i_offsets), vpd(self.j_begin), vpd(self.j_count),
-                                      vpd(self.eps2), t, int(bool(potential)), ctypes.byref(handle)),
-              "cn_list_plan_create")
+        self.j_index = None
+        if j_index is None:
+            check(lib.cn_list_plan_create(n_groups, vpd(self.i_offsets), vpd(self.j_begin), vpd(self.j_count),
+                                          vpd(self.eps2), t, int(bool(potential)), ctypes.byref(handle)),
+                  "cn_list_plan_create")
+        else:
+            idx = np.asarray(j_index)
+            if idx.ndim != 1 or not np.issubdtype(idx.dtype, np.integer):
+                raise ValueError("j_index must be a 1-d integer array")
+            if idx.size and (idx.min() < np.iinfo(np.int32).min or idx.max() > np.iinfo(np.int32).max):
+                raise ValueError("j_index entries must fit in 32 bits")
+            self.j_index = np.ascontiguousarray(idx, dtype=np.int32)
+            if n_src is None:
+                n_src = int(self.j_index.max()) + 1 if self.j_index.size else 0
+            check(lib.cn_list_plan_create_indexed(n_groups, vpd(self.i_offsets), vpd(self.j_begin),
+                                                  vpd(self.j_count), vpd(self.eps2),
+                                                  vpd(self.j_index) if self.j_index.size else None,
+                                                  self.j_index.size, int(n_src), t, int(bool(potential)),
+                                                  ctypes.byref(handle)),
+                  "cn_list_plan_create_indexed")
         self._h = handle
         self.potential = bool(potential)
         self.n_groups = n_groups
@@ -365,7 +390,10 @@ class ListPlan:
         pairs = ctypes.c_double()
         check(lib.cn_batch_plan_info(self._h, ctypes.byref(n_total), ctypes.byref(pairs)), "cn_batch_plan_info")
         self.n_i = int(n_total.value)
-        self.n_j = int(max((self.j_begin + self.j_count)[self.j_count > 0].max(initial=0), 0)) if n_groups else 0
+        if self.j_index is not None:
+            self.n_j = int(n_src)
+        else:
+            self.n_j = int(max((self.j_begin + self.j_count)[self.j_count > 0].max(initial=0), 0)) if n_groups else 0
         self.pairs = float(pairs.value)
         self._keep = None
 
@@ -437,6 +465,11 @@ def cn_batch_plan_create(offsets, eps2, tune=None, potential=False) -> BatchPlan
 
 def cn_list_plan_create(i_offsets, j_begin, j_count, eps2, tune=None, potential=False) -> ListPlan:
     return ListPlan(i_offsets, j_begin, j_count, eps2, tune=tune, potential=potential)
+
+
+def cn_list_plan_create_indexed(i_offsets, j_begin, j_count, eps2, j_index, n_src=None, tune=None,
+                                potential=False) -> ListPlan:
+    return ListPlan(i_offsets, j_begin, j_count, eps2, tune=tune, potential=potential, j_index=j_index, n_src=n_src)
 
 
 def cn_batch_plan_destroy(plan) -> None:

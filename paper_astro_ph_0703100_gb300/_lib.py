@@ -55,6 +55,7 @@ SIGNATURES = {
     "cn_batch_plan_capture": (c_int, [vp, vp, vp, vp, vp, c_size, vp]),
     "cn_batch_plan_launch": (c_int, [vp, vp]),
     "cn_list_plan_create": (c_int, [c_i32, vp, vp, vp, vp, vp, c_int, ctypes.POINTER(vp)]),
+    "cn_list_plan_create_indexed": (c_int, [c_i32, vp, vp, vp, vp, vp, c_i64, c_i64, vp, c_int, ctypes.POINTER(vp)]),
     "cn_force_lists": (c_int, [vp, vp, vp, vp, vp, vp, c_size, vp]),
     "cn_list_plan_capture": (c_int, [vp, vp, vp, vp, vp, vp, c_size, vp]),
     "cn_force_adjoint": (c_int, [c_i64, vp, c_f32, vp, vp, vp, vp]),

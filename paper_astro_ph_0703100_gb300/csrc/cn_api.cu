@@ -43,6 +43,8 @@ struct cn_batch_plan {
   bool guard = false;
   bool pot = false;
   cn::TileDesc* d_tiles = nullptr;
+  int32_t* d_index = nullptr;  // gathering list plans: the list entries (indices into the source records)
+  int64_t n_index = 0;
   int32_t n_tiles = 0;
   int64_t units = 0;
   int64_t n_chunks = 0;
@@ -59,6 +61,7 @@ namespace {
 constexpr size_t kCtrlBytes = 4096;  // queue words and spare control space at the head of a workspace
 constexpr uint64_t kDefaultWaitNs = 2000000000ull;
 constexpr size_t kMaxSmem = 227 * 1024;
+constexpr int32_t kNoIndex = 0;  // stands for the index array of a gathering plan whose lists are all empty
 constexpr size_t kSymSlotCap = static_cast<size_t>(2) << 30;  // symmetric-form slot memory before banding
 
 thread_local std::string g_last_error;
@@ -688,8 +691,8 @@ void log_plan(const char* entry, int variant, int64_t n_i, int64_t n_j, bool gua
                g.smem, g.ws_bytes);
 }
 
-cn_status occupancy(int dev, int variant, bool guard, const Plan& p, size_t smem, int* ctas) {
-  const auto key = std::make_tuple(dev, variant, guard, p.j_lanes, p.k, p.threads, smem);
+cn_status occupancy(int dev, int variant, bool guard, const Plan& p, size_t smem, int* ctas, bool gather = false) {
+  const auto key = std::make_tuple(dev, variant + (gather ? 100 : 0), guard, p.j_lanes, p.k, p.threads, smem);
   {
     std::lock_guard<std::mutex> lock(g_mu);
     auto it = g_occ.find(key);
@@ -706,8 +709,12 @@ cn_status occupancy(int dev, int variant, bool guard, const Plan& p, size_t smem
     case cn::kDD: e = cn::occupancy_dd(p, false, guard, smem, &c); break;
     case cn::kDDPot: e = cn::occupancy_dd(p, true, guard, smem, &c); break;
     case cn::kAdjoint: e = cn::occupancy_adjoint(p, guard, smem, &c); break;
-    case cn::kBatched: e = cn::occupancy_f32(p, false, guard, true, smem, &c); break;
-    case cn::kBatchedPot: e = cn::occupancy_f32(p, true, guard, true, smem, &c); break;
+    case cn::kBatched:
+      e = gather ? cn::occupancy_f32_gather(p, false, guard, smem, &c) : cn::occupancy_f32(p, false, guard, true, smem, &c);
+      break;
+    case cn::kBatchedPot:
+      e = gather ? cn::occupancy_f32_gather(p, true, guard, smem, &c) : cn::occupancy_f32(p, true, guard, true, smem, &c);
+      break;
     case cn::kJerk: e = cn::occupancy_jerk(p, false, guard, smem, &c); break;
     case cn::kJerkPot: e = cn::occupancy_jerk(p, true, guard, smem, &c); break;
     case cn::kF32EpsI: e = cn::occupancy_f32(p, false, true, false, smem, &c, true); break;
@@ -726,14 +733,16 @@ int slot_f4(int variant) {
   return (variant == cn::kDD || variant == cn::kDDPot || variant == cn::kJerk || variant == cn::kJerkPot) ? 2 : 1;
 }
 
-// Grid and workspace layout for `units` units over `n_tiles` i-tiles.
+// Grid and workspace layout for `units` units over `n_tiles` i-tiles
+// (gather: the gathering list kernel).
 cn_status layout(int dev, const DeviceInfo& d, int variant, bool guard, const Plan& p, int64_t n_tiles,
-                 int64_t units, int64_t n_wrec, Geometry* g) {
+                 int64_t units, int64_t n_wrec, Geometry* g, bool gather = false) {
   g->n_tiles = n_tiles;
   g->units = units;
-  g->smem = two_records(variant) ? cn::adjoint_smem_bytes(p) : cn::ring_smem_bytes(p);
+  g->smem = gather ? cn::gather_smem_bytes(p) : two_records(variant) ? cn::adjoint_smem_bytes(p) : cn::ring_smem_bytes(p);
+  if (g->smem > kMaxSmem) return fail(CN_ERR_INVALID_ARG, "the launch shape exceeds the shared memory of one CTA");
   int occ = 0;
-  cn_status st = occupancy(dev, variant, guard, p, g->smem, &occ);
+  cn_status st = occupancy(dev, variant, guard, p, g->smem, &occ, gather);
   if (st != CN_OK) return st;
   const int ctas = p.ctas_per_sm > 0 ? std::min(p.ctas_per_sm, occ) : occ;
   const int64_t slots = static_cast<int64_t>(ctas) * d.sms;
@@ -1115,6 +1124,8 @@ cn_status run_batched(const cn_batch_plan* plan, const float* pos_i, const float
   a.tiles = plan->d_tiles;
   a.n_i = plan->n_total;
   a.n_j = plan->n_j_total;
+  a.j_index = plan->d_index;
+  a.n_index = plan->n_index;
   if (log_enabled()) {
     Geometry lg = g;
     lg.grid = plan->grid;
@@ -1122,7 +1133,8 @@ cn_status run_batched(const cn_batch_plan* plan, const float* pos_i, const float
              plan->n_total, plan->n_j_total, plan->guard, plan->plan, lg, 0);
   }
   if (inject("launch")) return fail(CN_ERR_CUDA, "kernel launch: injected launch failure");
-  e = cn::launch_f32(a, plan->plan, plan->pot, plan->guard, true, plan->grid, s);
+  e = plan->d_index ? cn::launch_f32_gather(a, plan->plan, plan->pot, plan->guard, plan->grid, s)
+                    : cn::launch_f32(a, plan->plan, plan->pot, plan->guard, true, plan->grid, s);
   if (e != cudaSuccess) return fail_cuda(e, "batched pair kernel launch");
   return CN_OK;
 }
@@ -1135,8 +1147,12 @@ struct Group {
 };
 
 // Builds the (group, i-tile, j-tile) unit table of a plan and uploads it.
+// index_host (gathering list plans): n_index list entries, each the index of
+// a j record; the groups' j ranges then count entries of this array.
 cn_status build_group_plan(const std::vector<Group>& groups, bool lists, int64_t n_i_total, int64_t n_j_total,
-                           const cn_tune* tune, int with_pot, cn_batch_plan** out) {
+                           const cn_tune* tune, int with_pot, cn_batch_plan** out, const int32_t* index_host = nullptr,
+                           int64_t n_index = 0) {
+  const bool gather = index_host != nullptr;
   bool guard = false, zero_first = false;
   double pairs = 0.0;
   for (const Group& gr : groups) {
@@ -1196,8 +1212,10 @@ cn_status build_group_plan(const std::vector<Group>& groups, bool lists, int64_t
     }
     // with the potential the K = 8 split-j kernel runs short of registers:
     // K = 4 with half the lane groups keeps the i-tile (lists of 4096 records
-    // for groups of 256: 0.525 -> 0.712 of the 14-operation bound)
-    if (with_pot && fitted.i_per_thread == 8 && fitted.j_lanes > 1) {
+    // for groups of 256: 0.525 -> 0.712 of the 14-operation bound); the
+    // gathering kernel, whose threads also stage records, does the same
+    // (0.651 -> 0.673 of the FP32 bound on those lists as index arrays)
+    if ((with_pot || gather) && fitted.i_per_thread == 8 && fitted.j_lanes > 1) {
       fitted.i_per_thread = 4;
       fitted.j_lanes /= 2;
       if (fitted.j_lanes < 2) fitted.j_lanes = 0;
@@ -1236,8 +1254,8 @@ cn_status build_group_plan(const std::vector<Group>& groups, bool lists, int64_t
     }
   }
   Geometry g;
-  if (!tiles.empty() && (st = layout(dev, *d, variant, guard, p, static_cast<int64_t>(tiles.size()), units, 0, &g)) !=
-                            CN_OK)
+  if (!tiles.empty() &&
+      (st = layout(dev, *d, variant, guard, p, static_cast<int64_t>(tiles.size()), units, 0, &g, gather)) != CN_OK)
     return st;
   // Ragged ensembles (cluster sizes spanning 4x or more) with the fitted
   // shape and many units per resident CTA take the dynamic queue in chunks
@@ -1256,7 +1274,8 @@ cn_status build_group_plan(const std::vector<Group>& groups, bool lists, int64_t
   if (!lists && tune == &fitted && !tiles.empty() && p.chunk_units == 0 && ni_max >= 4 * ni_min &&
       units >= 20 * static_cast<int64_t>(g.grid)) {
     p.chunk_units = 32;
-    if ((st = layout(dev, *d, variant, guard, p, static_cast<int64_t>(tiles.size()), units, 0, &g)) != CN_OK) return st;
+    if ((st = layout(dev, *d, variant, guard, p, static_cast<int64_t>(tiles.size()), units, 0, &g, gather)) != CN_OK)
+      return st;
   }
   auto* plan = new cn_batch_plan();
   plan->dev = dev;
@@ -1284,8 +1303,16 @@ cn_status build_group_plan(const std::vector<Group>& groups, bool lists, int64_t
     cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&plan->d_tiles), tiles.size() * sizeof(cn::TileDesc));
     if (e == cudaSuccess)
       e = cudaMemcpy(plan->d_tiles, tiles.data(), tiles.size() * sizeof(cn::TileDesc), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && gather) {
+      plan->n_index = n_index;
+      e = cudaMalloc(reinterpret_cast<void**>(&plan->d_index), static_cast<size_t>(n_index) * sizeof(int32_t));
+      if (e == cudaSuccess)
+        e = cudaMemcpy(plan->d_index, index_host, static_cast<size_t>(n_index) * sizeof(int32_t),
+                       cudaMemcpyHostToDevice);
+    }
     if (e != cudaSuccess) {
       cudaFree(plan->d_tiles);
+      cudaFree(plan->d_index);
       delete plan;
       return fail_cuda(e, "uploading the batched unit table");
     }
@@ -1328,6 +1355,39 @@ cn_status build_list_plan(int32_t n_groups, const int64_t* i_offsets, const int6
   }
   const int64_t n_i_total = n_groups > 0 ? i_offsets[n_groups] : 0;
   return build_group_plan(groups, true, n_i_total, n_j_total, tune, with_pot, out);
+}
+
+// Gathering list plan: group g's list is the entries j_begin[g] ..
+// j_begin[g] + j_count[g] - 1 of j_index, each the index of one of n_src
+// records. Every entry a list reaches is checked here, on the host.
+cn_status build_list_plan_indexed(int32_t n_groups, const int64_t* i_offsets, const int64_t* j_begin,
+                                  const int64_t* j_count, const float* eps2, const int32_t* j_index, int64_t n_index,
+                                  int64_t n_src, const cn_tune* tune, int with_pot, cn_batch_plan** out) {
+  if (!out) return fail(CN_ERR_INVALID_ARG, "plan_out is NULL");
+  *out = nullptr;
+  if (n_groups < 0 || (n_groups > 0 && (!i_offsets || !j_begin || !j_count || !eps2)))
+    return fail(CN_ERR_INVALID_ARG, "n_groups < 0 or a NULL array");
+  if (n_index < 0 || n_src < 0 || (n_index > 0 && !j_index))
+    return fail(CN_ERR_INVALID_ARG, "n_index < 0, n_src < 0 or a NULL j_index");
+  if (n_src > INT32_MAX) return fail(CN_ERR_INVALID_ARG, "n_src exceeds the 32-bit index range");
+  if (n_groups > 0 && i_offsets[0] != 0) return fail(CN_ERR_INVALID_ARG, "i_offsets[0] must be 0");
+  std::vector<Group> groups(static_cast<size_t>(n_groups));
+  std::vector<char> reached(static_cast<size_t>(n_index), 0);
+  for (int32_t c = 0; c < n_groups; ++c) {
+    if (i_offsets[c + 1] < i_offsets[c]) return fail(CN_ERR_INVALID_ARG, "i_offsets must be non-decreasing");
+    if (j_begin[c] < 0 || j_count[c] < 0) return fail(CN_ERR_INVALID_ARG, "negative list begin or count");
+    if (j_count[c] > 0 && j_begin[c] + j_count[c] > n_index)
+      return fail(CN_ERR_INVALID_ARG, "a list runs past the end of j_index");
+    groups[c] = Group{i_offsets[c], i_offsets[c + 1] - i_offsets[c], j_begin[c], j_count[c], eps2[c]};
+    if (groups[c].ni > 0)
+      for (int64_t e = j_begin[c]; e < j_begin[c] + j_count[c]; ++e) reached[static_cast<size_t>(e)] = 1;
+  }
+  for (int64_t e = 0; e < n_index; ++e)
+    if (reached[static_cast<size_t>(e)] && (j_index[e] < 0 || j_index[e] >= n_src))
+      return fail(CN_ERR_INVALID_ARG, "a j_index entry lies outside 0 .. n_src - 1");
+  const int64_t n_i_total = n_groups > 0 ? i_offsets[n_groups] : 0;
+  return build_group_plan(groups, true, n_i_total, n_src, tune, with_pot, out, j_index != nullptr ? j_index : &kNoIndex,
+                          n_index);
 }
 
 // Host staging buffers of cn_force_host, per (device, stream).
@@ -1620,6 +1680,7 @@ cn_status cn_batch_plan_destroy(cn_batch_plan* plan) {
   if (plan->exec) cudaGraphExecDestroy(plan->exec);
   if (plan->graph) cudaGraphDestroy(plan->graph);
   if (plan->d_tiles) cudaFree(plan->d_tiles);
+  if (plan->d_index) cudaFree(plan->d_index);
   delete plan;
   return CN_OK;
 }
@@ -1647,6 +1708,15 @@ cn_status cn_list_plan_create(int32_t n_groups, const int64_t* i_offsets_host, c
   NvtxRange nvtx_range("cn_list_plan_create");
   return build_list_plan(n_groups, i_offsets_host, j_begin_host, j_count_host, eps2_host, tune, with_potential,
                          plan_out);
+}
+
+cn_status cn_list_plan_create_indexed(int32_t n_groups, const int64_t* i_offsets_host, const int64_t* j_begin_host,
+                                      const int64_t* j_count_host, const float* eps2_host,
+                                      const int32_t* j_index_host, int64_t n_index, int64_t n_src,
+                                      const cn_tune* tune, int with_potential, cn_batch_plan** plan_out) {
+  NvtxRange nvtx_range("cn_list_plan_create_indexed");
+  return build_list_plan_indexed(n_groups, i_offsets_host, j_begin_host, j_count_host, eps2_host, j_index_host,
+                                 n_index, n_src, tune, with_potential, plan_out);
 }
 
 cn_status cn_force_lists(const cn_batch_plan* plan, const float* pos_i, const float* pos_mass_j, float* acc_out,

@@ -2,7 +2,8 @@
 //
 // Inline PTX only for what the CUDA C++ front end does not expose directly:
 // mbarrier phase tracking, the non-multicast bulk copy global -> shared
-// (the j-tile staging step, the J-PACKING of Section 2.2), the MUFU inverse
+// (the j-tile staging step, the J-PACKING of Section 2.2), the
+// asynchronous copies of the list gather, the MUFU inverse
 // square root and the global nanosecond timer used to bound every wait.
 #pragma once
 
@@ -115,6 +116,28 @@ __device__ __forceinline__ void ds_accumulate(float& hi, float& lo, float x) {
 __device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void grid_launch_dependents() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Asynchronous copies global -> shared of the gathering list kernel, issued
+// without waiting: 4 bytes (a list index), 16 bytes (a record) or 16 zero
+// bytes (src-size 0: nothing is read). cp_async_wait_all waits for every
+// committed group of this thread, cp_async_wait_prior for all but the
+// latest; cp_async_arrive_noinc makes the mbarrier count one arrival of
+// this thread once all its earlier copies have landed.
+__device__ __forceinline__ void cp_async_4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_zero_16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, 0;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prior() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_arrive_noinc(uint64_t* bar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
 __device__ __forceinline__ void set_status(int* status, int bits) {

@@ -18,7 +18,7 @@ namespace cn {
 // tile index.
 struct TileDesc {
   int64_t i0;     // first i index of the tile (into pos_i and the outputs)
-  int64_t j0;     // first j index of the tile's system (into pos_j)
+  int64_t j0;     // first j index of the tile's system (into pos_j; gathering plans: into j_index)
   int64_t nj;     // number of j-particles of the system
   int64_t unit0;  // first unit of the tile in the global unit sequence
   int32_t ni;     // valid i-particles in the tile (<= i_tile)
@@ -46,6 +46,8 @@ struct PairArgs {
   int* queue;             // [0] next chunk, [1] finished CTAs (dynamic schedule; zero between launches)
   int* status;            // device status word
   const TileDesc* tiles;  // batched schedule only
+  const int32_t* j_index;  // gathering list plans: list entries, each the index of a pos_j record
+  int64_t n_index;         // gathering list plans: entries in j_index
   int64_t n_i;            // single system: i count
   int64_t n_j;            // single system: j count
   int64_t total_units;
@@ -93,6 +95,9 @@ cudaError_t launch_f32(const PairArgs& a, const Plan& p, bool pot, bool guard, b
                        cudaStream_t s, bool eps_i = false);
 cudaError_t occupancy_f32(const Plan& p, bool pot, bool guard, bool batched, size_t smem, int* ctas,
                           bool eps_i = false);
+// list plans whose j records are gathered through an index array
+cudaError_t launch_f32_gather(const PairArgs& a, const Plan& p, bool pot, bool guard, int grid, cudaStream_t s);
+cudaError_t occupancy_f32_gather(const Plan& p, bool pot, bool guard, size_t smem, int* ctas);
 cudaError_t launch_dd(const PairArgs& a, const Plan& p, bool pot, bool guard, int grid, cudaStream_t s);
 cudaError_t occupancy_dd(const Plan& p, bool pot, bool guard, size_t smem, int* ctas);
 cudaError_t launch_adjoint(const PairArgs& a, const Plan& p, bool guard, int grid, cudaStream_t s);
@@ -161,6 +166,8 @@ inline cudaError_t prepare_kernel(const void* fn, size_t smem) {
 inline size_t ring_smem_bytes(const Plan& p) {
   return 256 + static_cast<size_t>(p.stages) * p.j_tile * 16;
 }
+// the gathering list kernel adds two buffers of j_tile list indices
+inline size_t gather_smem_bytes(const Plan& p) { return ring_smem_bytes(p) + static_cast<size_t>(p.j_tile) * 8; }
 inline size_t adjoint_smem_bytes(const Plan& p) {
   return 256 + static_cast<size_t>(p.stages) * p.j_tile * 32;
 }

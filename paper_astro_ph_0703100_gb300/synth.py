@@ -195,3 +195,37 @@ def interaction_lists(n_particles: int, group_size: int, list_size: int, seed: i
     j_begin = np.arange(n_groups, dtype=np.int64) * list_size
     j_count = np.full(n_groups, list_size, dtype=np.int64)
     return pos_i, i_offsets, lists, j_begin, j_count
+
+
+def interaction_lists_indexed(n_particles: int, group_size: int, list_size: int, seed: int,
+                              n_nodes: int | None = None, n_pseudo_frac: float = 0.5):
+    """The same group / list structure with the lists as index arrays, as a
+    tree walk produces them: one source array holds the particles (ordered
+    by x, as the i-set) followed by ``n_nodes`` pseudo-particle records
+    (random positions, 1-64x the particle mass; default ``n_particles //
+    4``), and each group's list is ``list_size`` int32 indices into it: a
+    seeded subset of the particles without repeats plus a seeded subset of
+    the nodes without repeats. Returns ``(pos_i, i_offsets, src, j_index,
+    j_begin, j_count)``; ``src[j_index]`` is the list records laid out in
+    entry order. No force arithmetic happens here.
+    """
+    p = plummer(n_particles, seed)
+    pos_i = p[np.argsort(p[:, 0], kind="stable")]
+    n_nodes = n_particles // 4 if n_nodes is None else n_nodes
+    rng = _rng(seed + 2)
+    nodes = np.empty((n_nodes, 4), dtype=np.float32)
+    nodes[:, :3] = (4.0 * rng.standard_normal((n_nodes, 3))).astype(np.float32)
+    nodes[:, 3] = (rng.uniform(1.0, 64.0, n_nodes) / n_particles).astype(np.float32)
+    src = np.concatenate([pos_i, nodes])
+    n_groups = -(-n_particles // group_size)
+    i_offsets = np.minimum(np.arange(n_groups + 1, dtype=np.int64) * group_size, n_particles)
+    n_pseudo = min(int(list_size * n_pseudo_frac), n_nodes)
+    n_real = list_size - n_pseudo
+    j_index = np.empty(n_groups * list_size, dtype=np.int32)
+    for g in range(n_groups):
+        blk = j_index[g * list_size:(g + 1) * list_size]
+        blk[:n_real] = rng.choice(n_particles, size=n_real, replace=False)
+        blk[n_real:] = n_particles + rng.choice(n_nodes, size=n_pseudo, replace=False)
+    j_begin = np.arange(n_groups, dtype=np.int64) * list_size
+    j_count = np.full(n_groups, list_size, dtype=np.int64)
+    return pos_i, i_offsets, src, j_index, j_begin, j_count

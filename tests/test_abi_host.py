@@ -138,6 +138,35 @@ def test_batch_plan_validation(lib):
     assert lib.cn_tune_set(0, 1024, 1024, ctypes.byref(t)) == 1
 
 
+def test_indexed_list_plan_validation(lib):
+    """The gathering list plan checks its index array on the host, before any
+    device work: an entry outside 0 .. n_src - 1 that a group with
+    i-particles reaches, a list running past the end of j_index, a NULL
+    j_index with entries, or n_src beyond 32 bits is CN_ERR_INVALID_ARG."""
+    h = ctypes.c_void_p()
+    i_off = (ctypes.c_int64 * 3)(0, 4, 8)
+    eps = (ctypes.c_float * 2)(0.01, 0.01)
+    create = lambda jb, jc, idx, n_index, n_src, i=i_off: lib.cn_list_plan_create_indexed(
+        2, i, (ctypes.c_int64 * 2)(*jb), (ctypes.c_int64 * 2)(*jc), eps, idx, n_index, n_src, None, 0,
+        ctypes.byref(h))
+    idx = (ctypes.c_int32 * 6)(0, 1, 2, 7, 3, 9)
+    assert create((0, 3), (3, 3), idx, 6, 9) == 1      # entry 9 outside 0 .. 8
+    assert create((0, 3), (3, 3), idx, 6, 5) == 1      # entries 7 and 9 outside 0 .. 4
+    neg = (ctypes.c_int32 * 6)(0, 1, -2, 3, 3, 3)
+    assert create((0, 3), (3, 3), neg, 6, 10) == 1     # negative entry
+    assert create((0, 4), (3, 3), idx, 6, 10) == 1     # the second list runs past the end
+    assert create((0, 3), (3, 3), None, 6, 10) == 1    # NULL index array with entries
+    assert create((0, 3), (3, 3), idx, -1, 10) == 1    # negative counts
+    assert create((0, 3), (3, 3), idx, 6, 1 << 31) == 1  # n_src beyond the 32-bit index range
+    assert create((-1, 3), (3, 3), idx, 6, 10) == 1    # negative list begin
+    assert lib.cn_list_plan_create_indexed(2, (ctypes.c_int64 * 3)(0, 4, 2), (ctypes.c_int64 * 2)(0, 3),
+                                           (ctypes.c_int64 * 2)(3, 3), eps, idx, 6, 10, None, 0,
+                                           ctypes.byref(h)) == 1  # decreasing i_offsets
+    assert lib.cn_list_plan_create_indexed(2, i_off, (ctypes.c_int64 * 2)(0, 3), (ctypes.c_int64 * 2)(3, 3), eps,
+                                           idx, 6, 10, None, 0, None) == 1  # NULL plan_out
+    assert h.value is None
+
+
 def test_host_f64_form_validation(lib):
     assert lib.cn_force_host_f64(None, None, None, 0.01, None, -1, 0) == 1
     assert lib.cn_force_host_f64(None, None, V(FAKE), 0.01, V(FAKE), 0, 0) == 0

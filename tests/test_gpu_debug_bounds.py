@@ -3,11 +3,12 @@ kernel reaches (the unit-to-tile lookup, tile descriptors against the i and
 j arrays, each bulk copy's range, the chunk range of split tiles) and the
 symmetric kernel's unit and segment indices are checked on the device; a
 violation would set the device status bit kStatusBadSchedule and stop the
-CTA's work. Here the batched, interaction-list, dynamic-queue and split-j
-paths, default shapes with j-tiles fitted to the schedule (and the
-compensated, adjoint, force-jerk and banded symmetric forms) run under that
-build, in a separate process: no check fires, and the results still match
-the FP64 oracle.
+CTA's work (the gathering list kernel also checks every list entry it
+copies against the source array). Here the batched, interaction-list,
+gathering-list, dynamic-queue and split-j paths, default shapes with
+j-tiles fitted to the schedule (and the compensated, adjoint, force-jerk
+and banded symmetric forms) run under that build, in a separate process: no
+check fires, and the results still match the FP64 oracle.
 """
 
 import json
@@ -70,6 +71,25 @@ SCRIPT = textwrap.dedent(r"""
             lo, hi = i_off[g], i_off[g + 1]
             if hi == lo or jc[g] == 0: continue
             ref, _ = oracle.force(pos_i[lo:hi], pool[jb[g]:jb[g] + jc[g]], eps2[g], potential=False)
+            e = max(e, oracle.e_max(a[lo:hi], ref))
+        out["errors"][name] = e
+        lp.close()
+
+    # gathering lists: index arrays into particles and tree nodes (ragged
+    # last j-tiles), default, dynamic and split-j shapes
+    pg, ig, sg, xg, bg, cg = synth.interaction_lists_indexed(3000, 256, 700, seed=4)
+    for name, tune in [("indexed", None),
+                       ("indexed dynamic", {"i_per_thread": 2, "threads": 64, "j_tile": 128, "stages": 3,
+                                            "chunk_units": 5}),
+                       ("indexed splitj", {"i_per_thread": 8, "threads": 256, "j_tile": 256, "stages": 4,
+                                           "j_lanes": 8})]:
+        lp = cn.ListPlan(ig, bg, cg, 1e-3, tune=tune, j_index=xg)
+        acc, _ = lp.run(d(pg), d(sg))
+        status(name)
+        a = acc.cpu().numpy(); e = 0.0
+        for g in range(0, len(cg), 3):
+            lo, hi = ig[g], ig[g + 1]
+            ref, _ = oracle.force(pg[lo:hi], sg[xg[bg[g]:bg[g] + cg[g]]], 1e-3, potential=False)
             e = max(e, oracle.e_max(a[lo:hi], ref))
         out["errors"][name] = e
         lp.close()
