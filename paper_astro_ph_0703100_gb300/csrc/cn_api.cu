@@ -1129,8 +1129,10 @@ cn_status run_batched(const cn_batch_plan* plan, const float* pos_i, const float
   if (log_enabled()) {
     Geometry lg = g;
     lg.grid = plan->grid;
-    log_plan(plan->lists ? "cn_force_lists" : "cn_force_batched", plan->pot ? cn::kBatchedPot : cn::kBatched,
-             plan->n_total, plan->n_j_total, plan->guard, plan->plan, lg, 0);
+    lg.smem = plan->d_index ? cn::gather_smem_bytes(plan->plan) : cn::ring_smem_bytes(plan->plan);
+    log_plan(plan->lists ? (plan->d_index ? "cn_force_lists (index lists)" : "cn_force_lists") : "cn_force_batched",
+             plan->pot ? cn::kBatchedPot : cn::kBatched, plan->n_total, plan->n_j_total, plan->guard, plan->plan, lg,
+             0);
   }
   if (inject("launch")) return fail(CN_ERR_CUDA, "kernel launch: injected launch failure");
   e = plan->d_index ? cn::launch_f32_gather(a, plan->plan, plan->pot, plan->guard, plan->grid, s)

@@ -240,3 +240,52 @@ def test_binding_rejects_tensors_the_kernels_cannot_read():
     w = cn.cn_potential_energy(p, pot)  # the valid call still works
     torch.cuda.synchronize()
     assert np.isfinite(float(w.item()))
+
+
+LOG_SCRIPT = r"""
+import sys
+sys.path.insert(0, sys.argv[1])
+import numpy as np, torch
+import paper_astro_ph_0703100_gb300 as cn
+from paper_astro_ph_0703100_gb300 import synth
+d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+p = d(synth.plummer(5000, 1))
+cn.cn_force(p, p, 1e-3)
+cn.cn_force_symmetric(p, 1e-3)
+pos_i, i_off, src, jidx, jb, jc = synth.interaction_lists_indexed(3000, 256, 700, seed=2)
+lx = cn.ListPlan(i_off, jb, jc, 1e-3, j_index=jidx, n_src=src.shape[0])
+lx.run(d(pos_i), d(src))
+lc = cn.ListPlan(i_off, jb, jc, 1e-3)
+lc.run(d(pos_i), d(src[jidx]))
+torch.cuda.synchronize()
+print("status", cn.cn_get_device_status())
+"""
+
+
+def test_plan_logging_names_each_launch():
+    """CN_LOG=1 prints one line per launch on stderr with the entry point,
+    variant, sizes, launch shape, grid and units (the index-list form marked
+    as such); without it the library prints nothing."""
+    import subprocess
+    import sys
+
+    from conftest import ROOT
+
+    torch_cuda()
+    runs = {}
+    for flag in ("1", "0"):
+        env = dict(os.environ, CN_LOG=flag)
+        res = subprocess.run([sys.executable, "-c", LOG_SCRIPT, ROOT], env=env, capture_output=True, text=True,
+                             timeout=300)
+        assert res.returncode == 0, res.stderr[-2000:]
+        assert res.stdout.split()[-1] == "0"
+        runs[flag] = [line for line in res.stderr.splitlines() if line.startswith("[cunbody]")]
+    assert runs["0"] == []
+    lines = runs["1"]
+    force = [x for x in lines if x.startswith("[cunbody] cn_force: variant f32 n_i 5000 n_j 5000")]
+    assert len(force) == 1 and "grid " in force[0] and "units " in force[0] and "K " in force[0]
+    assert sum(x.startswith("[cunbody] cn_force_symmetric: n 5000") for x in lines) >= 1
+    indexed = [x for x in lines if x.startswith("[cunbody] cn_force_lists (index lists): variant batched")]
+    plain = [x for x in lines if x.startswith("[cunbody] cn_force_lists: variant batched")]
+    assert len(indexed) == 1 and len(plain) == 1
+    assert "n_i 3000 n_j 3750" in indexed[0] and "n_i 3000 n_j" in plain[0]
