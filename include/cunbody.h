@@ -50,10 +50,12 @@
  *    must wait in the same way (cudaGridDependencySynchronize) before it
  *    reads the library's outputs.
  *  - Environment: CN_PDL=0 launches in plain stream order and CN_LOG=1
- *    prints each new launch plan (variant, shape, grid, split tiles) to
+ *    prints one line per launch (variant, shape, grid, split tiles) to
  *    stderr (both read once per process); CN_FAULT_INJECT, a comma list of
  *    alloc, launch and capture, makes those host steps fail as if the CUDA
- *    call had failed (read at every call; for testing error paths).
+ *    call had failed, and hostmem makes the host-side building of a batch or
+ *    list plan fail as if host memory were exhausted (CN_ERR_HOST) (read at
+ *    every call; for testing error paths).
  */
 #ifndef CUNBODY_H
 #define CUNBODY_H
@@ -81,7 +83,9 @@ typedef enum cn_status {
     CN_ERR_CUDA = 3,               /* a CUDA runtime call failed (see cn_last_error_message)  */
     CN_ERR_TIMEOUT = 4,            /* a kernel gave up waiting (reported by cn_get_device_status) */
     CN_ERR_UNSUPPORTED_DEVICE = 5, /* the current device is not sm_103 (GB300)               */
-    CN_ERR_WORKSPACE = 6           /* workspace too small, or allocation needed during capture */
+    CN_ERR_WORKSPACE = 6,          /* workspace too small, or allocation needed during capture */
+    CN_ERR_HOST = 7                /* host-side failure inside the library: host memory exhausted
+                                      or another C++ runtime error (no exception leaves the library) */
 } cn_status;
 
 /* Kernel variants, used by the workspace, tuning and autotuning calls. */

@@ -87,6 +87,7 @@ STATUS = {
     4: "CN_ERR_TIMEOUT",
     5: "CN_ERR_UNSUPPORTED_DEVICE",
     6: "CN_ERR_WORKSPACE",
+    7: "CN_ERR_HOST",
 }
 
 _lock = threading.Lock()

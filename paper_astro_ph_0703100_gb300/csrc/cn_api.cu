@@ -2,6 +2,7 @@
 // launch-shape selection, workspaces, dispatch to the kernels, batched
 // plans, host-memory forms, tuning and status.
 #include "cunbody.h"
+#include "cn_guard.h"
 #include "cn_kernels.h"
 #include "cn_sym.h"
 
@@ -1337,6 +1338,7 @@ cn_status build_batch_plan(int32_t n_clusters, const int64_t* offsets, const flo
     groups[c] = Group{offsets[c], nc, offsets[c], nc, eps2[c]};
   }
   const int64_t n_total = n_clusters > 0 ? offsets[n_clusters] : 0;
+  if (inject("hostmem")) throw std::bad_alloc();
   return build_group_plan(groups, false, n_total, n_total, tune, with_pot, out);
 }
 
@@ -1356,6 +1358,7 @@ cn_status build_list_plan(int32_t n_groups, const int64_t* i_offsets, const int6
     if (j_count[c] > 0) n_j_total = std::max(n_j_total, j_begin[c] + j_count[c]);
   }
   const int64_t n_i_total = n_groups > 0 ? i_offsets[n_groups] : 0;
+  if (inject("hostmem")) throw std::bad_alloc();
   return build_group_plan(groups, true, n_i_total, n_j_total, tune, with_pot, out);
 }
 
@@ -1388,6 +1391,7 @@ cn_status build_list_plan_indexed(int32_t n_groups, const int64_t* i_offsets, co
     if (reached[static_cast<size_t>(e)] && (j_index[e] < 0 || j_index[e] >= n_src))
       return fail(CN_ERR_INVALID_ARG, "a j_index entry lies outside 0 .. n_src - 1");
   const int64_t n_i_total = n_groups > 0 ? i_offsets[n_groups] : 0;
+  if (inject("hostmem")) throw std::bad_alloc();
   return build_group_plan(groups, true, n_i_total, n_src, tune, with_pot, out, j_index != nullptr ? j_index : &kNoIndex,
                           n_index);
 }
@@ -1612,6 +1616,15 @@ cn_status force_f32_on_workspace(int64_t n_i, const float* pos_i, int64_t n_j, c
   return force_common(false, n_i, pos_i, n_j, pos_mass_j, eps2, acc_out, pot_out, ws, ws_bytes, false, s);
 }
 cn_status set_error(cn_status st, const std::string& msg) { return fail(st, msg); }
+
+cn_status fail_nothrow(cn_status st, const char* msg) noexcept {
+  try {
+    g_last_error = msg;
+  } catch (...) {
+    g_last_error.clear();  // no room even for the message
+  }
+  return st;
+}
 }  // namespace cn
 
 // ====================================================================== C ABI
@@ -1620,96 +1633,118 @@ extern "C" {
 cn_status cn_force(int64_t n_i, const float* pos_i, int64_t n_j, const float* pos_mass_j, float eps2, float* acc_out,
                    float* pot_out, cn_stream stream) {
   NvtxRange nvtx_range("cn_force");
-  return force_common(false, n_i, pos_i, n_j, pos_mass_j, eps2, acc_out, pot_out, nullptr, 0, true,
-                      reinterpret_cast<cudaStream_t>(stream));
+  return cn::guard([&]() -> cn_status {
+    return force_common(false, n_i, pos_i, n_j, pos_mass_j, eps2, acc_out, pot_out, nullptr, 0, true,
+                        reinterpret_cast<cudaStream_t>(stream));
+  });
 }
 
 cn_status cn_force_eps_i(int64_t n_i, const float* pos_eps_i, int64_t n_j, const float* pos_mass_j, float* acc_out,
                          float* pot_out, cn_stream stream) {
   NvtxRange nvtx_range("cn_force_eps_i");
-  return force_common(false, n_i, pos_eps_i, n_j, pos_mass_j, 0.f, acc_out, pot_out, nullptr, 0, true,
-                      reinterpret_cast<cudaStream_t>(stream), true);
+  return cn::guard([&]() -> cn_status {
+    return force_common(false, n_i, pos_eps_i, n_j, pos_mass_j, 0.f, acc_out, pot_out, nullptr, 0, true,
+                        reinterpret_cast<cudaStream_t>(stream), true);
+  });
 }
 
 cn_status cn_force_ws(int64_t n_i, const float* pos_i, int64_t n_j, const float* pos_mass_j, float eps2,
                       float* acc_out, float* pot_out, void* workspace, size_t ws_bytes, cn_stream stream) {
   NvtxRange nvtx_range("cn_force_ws");
-  return force_common(false, n_i, pos_i, n_j, pos_mass_j, eps2, acc_out, pot_out, workspace, ws_bytes, false,
-                      reinterpret_cast<cudaStream_t>(stream));
+  return cn::guard([&]() -> cn_status {
+    return force_common(false, n_i, pos_i, n_j, pos_mass_j, eps2, acc_out, pot_out, workspace, ws_bytes, false,
+                        reinterpret_cast<cudaStream_t>(stream));
+  });
 }
 
 cn_status cn_force_dd(int64_t n_i, const float* pos_i, int64_t n_j, const float* pos_mass_j, float eps2,
                       double* acc_out, double* pot_out, cn_stream stream) {
   NvtxRange nvtx_range("cn_force_dd");
-  return force_common(true, n_i, pos_i, n_j, pos_mass_j, eps2, acc_out, pot_out, nullptr, 0, true,
-                      reinterpret_cast<cudaStream_t>(stream));
+  return cn::guard([&]() -> cn_status {
+    return force_common(true, n_i, pos_i, n_j, pos_mass_j, eps2, acc_out, pot_out, nullptr, 0, true,
+                        reinterpret_cast<cudaStream_t>(stream));
+  });
 }
 
 cn_status cn_force_dd_ws(int64_t n_i, const float* pos_i, int64_t n_j, const float* pos_mass_j, float eps2,
                          double* acc_out, double* pot_out, void* workspace, size_t ws_bytes, cn_stream stream) {
   NvtxRange nvtx_range("cn_force_dd_ws");
-  return force_common(true, n_i, pos_i, n_j, pos_mass_j, eps2, acc_out, pot_out, workspace, ws_bytes, false,
-                      reinterpret_cast<cudaStream_t>(stream));
+  return cn::guard([&]() -> cn_status {
+    return force_common(true, n_i, pos_i, n_j, pos_mass_j, eps2, acc_out, pot_out, workspace, ws_bytes, false,
+                        reinterpret_cast<cudaStream_t>(stream));
+  });
 }
 
 size_t cn_workspace_bytes(int variant, int64_t n_i, int64_t n_j) {
-  if (n_i <= 0 || n_j <= 0 || variant < cn::kF32 || variant > cn::kF32EpsIPot || variant == cn::kBatched ||
-      variant == cn::kBatchedPot || variant == cn::kSym)
-    return 0;
-  int dev = 0;
-  DeviceInfo* d = nullptr;
-  if (current_device(&dev, &d) != CN_OK) return 0;
-  Plan p;
-  if (resolve_plan(dev, variant, n_i, n_j, false, nullptr, &p) != CN_OK) return 0;
-  Geometry g;
-  if (single_geometry(dev, *d, variant, false, p, n_i, n_j, &g) != CN_OK) return 0;
-  // the guarded (eps2 = 0) shape uses one i-particle per thread: size for the larger of the two
-  Plan pg = p;
-  pg.k = 1;
-  Geometry gg;
-  if (single_geometry(dev, *d, variant, true, pg, n_i, n_j, &gg) != CN_OK) return g.ws_bytes;
-  return std::max(g.ws_bytes, gg.ws_bytes);
+  return cn::guard_value<size_t>(0, [&]() -> size_t {
+    if (n_i <= 0 || n_j <= 0 || variant < cn::kF32 || variant > cn::kF32EpsIPot || variant == cn::kBatched ||
+        variant == cn::kBatchedPot || variant == cn::kSym)
+      return 0;
+    int dev = 0;
+    DeviceInfo* d = nullptr;
+    if (current_device(&dev, &d) != CN_OK) return 0;
+    Plan p;
+    if (resolve_plan(dev, variant, n_i, n_j, false, nullptr, &p) != CN_OK) return 0;
+    Geometry g;
+    if (single_geometry(dev, *d, variant, false, p, n_i, n_j, &g) != CN_OK) return 0;
+    // the guarded (eps2 = 0) shape uses one i-particle per thread: size for the larger of the two
+    Plan pg = p;
+    pg.k = 1;
+    Geometry gg;
+    if (single_geometry(dev, *d, variant, true, pg, n_i, n_j, &gg) != CN_OK) return g.ws_bytes;
+    return std::max(g.ws_bytes, gg.ws_bytes);
+  });
 }
 
 cn_status cn_batch_plan_create(int32_t n_clusters, const int64_t* offsets_host, const float* eps2_host,
                                const cn_tune* tune, int with_potential, cn_batch_plan** plan_out) {
   NvtxRange nvtx_range("cn_batch_plan_create");
-  return build_batch_plan(n_clusters, offsets_host, eps2_host, tune, with_potential, plan_out);
+  return cn::guard([&]() -> cn_status {
+    return build_batch_plan(n_clusters, offsets_host, eps2_host, tune, with_potential, plan_out);
+  });
 }
 
 cn_status cn_batch_plan_destroy(cn_batch_plan* plan) {
-  if (!plan) return CN_OK;
-  if (plan->exec) cudaGraphExecDestroy(plan->exec);
-  if (plan->graph) cudaGraphDestroy(plan->graph);
-  if (plan->d_tiles) cudaFree(plan->d_tiles);
-  if (plan->d_index) cudaFree(plan->d_index);
-  delete plan;
-  return CN_OK;
+  return cn::guard([&]() -> cn_status {
+    if (!plan) return CN_OK;
+    if (plan->exec) cudaGraphExecDestroy(plan->exec);
+    if (plan->graph) cudaGraphDestroy(plan->graph);
+    if (plan->d_tiles) cudaFree(plan->d_tiles);
+    if (plan->d_index) cudaFree(plan->d_index);
+    delete plan;
+    return CN_OK;
+  });
 }
 
 size_t cn_batch_plan_workspace_bytes(const cn_batch_plan* plan) { return plan ? plan->ws_bytes : 0; }
 
 cn_status cn_batch_plan_info(const cn_batch_plan* plan, int64_t* n_total, double* pairs) {
-  if (!plan) return fail(CN_ERR_INVALID_ARG, "plan is NULL");
-  if (n_total) *n_total = plan->n_total;
-  if (pairs) *pairs = plan->pairs;
-  return CN_OK;
+  return cn::guard([&]() -> cn_status {
+    if (!plan) return fail(CN_ERR_INVALID_ARG, "plan is NULL");
+    if (n_total) *n_total = plan->n_total;
+    if (pairs) *pairs = plan->pairs;
+    return CN_OK;
+  });
 }
 
 cn_status cn_force_batched(const cn_batch_plan* plan, const float* pos_mass, float* acc_out, float* pot_out,
                            void* workspace, size_t ws_bytes, cn_stream stream) {
   NvtxRange nvtx_range("cn_force_batched");
-  if (plan && plan->lists) return fail(CN_ERR_INVALID_ARG, "an interaction-list plan runs with cn_force_lists");
-  return run_batched(plan, pos_mass, pos_mass, acc_out, pot_out, workspace, ws_bytes,
-                     reinterpret_cast<cudaStream_t>(stream));
+  return cn::guard([&]() -> cn_status {
+    if (plan && plan->lists) return fail(CN_ERR_INVALID_ARG, "an interaction-list plan runs with cn_force_lists");
+    return run_batched(plan, pos_mass, pos_mass, acc_out, pot_out, workspace, ws_bytes,
+                       reinterpret_cast<cudaStream_t>(stream));
+  });
 }
 
 cn_status cn_list_plan_create(int32_t n_groups, const int64_t* i_offsets_host, const int64_t* j_begin_host,
                               const int64_t* j_count_host, const float* eps2_host, const cn_tune* tune,
                               int with_potential, cn_batch_plan** plan_out) {
   NvtxRange nvtx_range("cn_list_plan_create");
-  return build_list_plan(n_groups, i_offsets_host, j_begin_host, j_count_host, eps2_host, tune, with_potential,
-                         plan_out);
+  return cn::guard([&]() -> cn_status {
+    return build_list_plan(n_groups, i_offsets_host, j_begin_host, j_count_host, eps2_host, tune, with_potential,
+                           plan_out);
+  });
 }
 
 cn_status cn_list_plan_create_indexed(int32_t n_groups, const int64_t* i_offsets_host, const int64_t* j_begin_host,
@@ -1717,16 +1752,20 @@ cn_status cn_list_plan_create_indexed(int32_t n_groups, const int64_t* i_offsets
                                       const int32_t* j_index_host, int64_t n_index, int64_t n_src,
                                       const cn_tune* tune, int with_potential, cn_batch_plan** plan_out) {
   NvtxRange nvtx_range("cn_list_plan_create_indexed");
-  return build_list_plan_indexed(n_groups, i_offsets_host, j_begin_host, j_count_host, eps2_host, j_index_host,
-                                 n_index, n_src, tune, with_potential, plan_out);
+  return cn::guard([&]() -> cn_status {
+    return build_list_plan_indexed(n_groups, i_offsets_host, j_begin_host, j_count_host, eps2_host, j_index_host,
+                                   n_index, n_src, tune, with_potential, plan_out);
+  });
 }
 
 cn_status cn_force_lists(const cn_batch_plan* plan, const float* pos_i, const float* pos_mass_j, float* acc_out,
                          float* pot_out, void* workspace, size_t ws_bytes, cn_stream stream) {
   NvtxRange nvtx_range("cn_force_lists");
-  if (plan && !plan->lists) return fail(CN_ERR_INVALID_ARG, "a cluster plan runs with cn_force_batched");
-  return run_batched(plan, pos_i, pos_mass_j, acc_out, pot_out, workspace, ws_bytes,
-                     reinterpret_cast<cudaStream_t>(stream));
+  return cn::guard([&]() -> cn_status {
+    if (plan && !plan->lists) return fail(CN_ERR_INVALID_ARG, "a cluster plan runs with cn_force_batched");
+    return run_batched(plan, pos_i, pos_mass_j, acc_out, pot_out, workspace, ws_bytes,
+                       reinterpret_cast<cudaStream_t>(stream));
+  });
 }
 
 cn_status capture_plan(cn_batch_plan* plan, const float* pos_i, const float* pos_j, float* acc_out, float* pot_out,
@@ -1762,550 +1801,590 @@ cn_status capture_plan(cn_batch_plan* plan, const float* pos_i, const float* pos
 cn_status cn_batch_plan_capture(cn_batch_plan* plan, const float* pos_mass, float* acc_out, float* pot_out,
                                 void* workspace, size_t ws_bytes, cn_stream stream) {
   NvtxRange nvtx_range("cn_batch_plan_capture");
-  if (plan && plan->lists) return fail(CN_ERR_INVALID_ARG, "an interaction-list plan is captured with cn_list_plan_capture");
-  return capture_plan(plan, pos_mass, pos_mass, acc_out, pot_out, workspace, ws_bytes, stream);
+  return cn::guard([&]() -> cn_status {
+    if (plan && plan->lists) return fail(CN_ERR_INVALID_ARG, "an interaction-list plan is captured with cn_list_plan_capture");
+    return capture_plan(plan, pos_mass, pos_mass, acc_out, pot_out, workspace, ws_bytes, stream);
+  });
 }
 
 cn_status cn_list_plan_capture(cn_batch_plan* plan, const float* pos_i, const float* pos_mass_j, float* acc_out,
                                float* pot_out, void* workspace, size_t ws_bytes, cn_stream stream) {
   NvtxRange nvtx_range("cn_list_plan_capture");
-  if (plan && !plan->lists) return fail(CN_ERR_INVALID_ARG, "a cluster plan is captured with cn_batch_plan_capture");
-  return capture_plan(plan, pos_i, pos_mass_j, acc_out, pot_out, workspace, ws_bytes, stream);
+  return cn::guard([&]() -> cn_status {
+    if (plan && !plan->lists) return fail(CN_ERR_INVALID_ARG, "a cluster plan is captured with cn_batch_plan_capture");
+    return capture_plan(plan, pos_i, pos_mass_j, acc_out, pot_out, workspace, ws_bytes, stream);
+  });
 }
 
 cn_status cn_batch_plan_launch(const cn_batch_plan* plan, cn_stream stream) {
   NvtxRange nvtx_range("cn_batch_plan_launch");
-  if (!plan || !plan->exec) return fail(CN_ERR_INVALID_ARG, "plan has no captured graph");
-  if (inject("launch")) return fail(CN_ERR_CUDA, "cudaGraphLaunch: injected launch failure");
-  cudaError_t e = cudaGraphLaunch(plan->exec, reinterpret_cast<cudaStream_t>(stream));
-  return e == cudaSuccess ? CN_OK : fail_cuda(e, "cudaGraphLaunch");
+  return cn::guard([&]() -> cn_status {
+    if (!plan || !plan->exec) return fail(CN_ERR_INVALID_ARG, "plan has no captured graph");
+    if (inject("launch")) return fail(CN_ERR_CUDA, "cudaGraphLaunch: injected launch failure");
+    cudaError_t e = cudaGraphLaunch(plan->exec, reinterpret_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? CN_OK : fail_cuda(e, "cudaGraphLaunch");
+  });
 }
 
 cn_status cn_force_adjoint(int64_t n, const float* pos_mass, float eps2, const float* w, float* grad_pos,
                            float* grad_mass, cn_stream stream) {
   NvtxRange nvtx_range("cn_force_adjoint");
-  auto s = reinterpret_cast<cudaStream_t>(stream);
-  if (n < 0) return fail(CN_ERR_INVALID_ARG, "n must be >= 0");
-  cn_status st;
-  if ((st = check_eps2(eps2)) != CN_OK) return st;
-  if ((st = check_records(pos_mass, n, "pos_mass")) != CN_OK) return st;
-  if (n > 0 && (!w || !grad_pos || !grad_mass)) return fail(CN_ERR_INVALID_ARG, "w, grad_pos and grad_mass are required");
-  if ((w && !aligned(w, 4)) || (grad_pos && !aligned(grad_pos, 4)) || (grad_mass && !aligned(grad_mass, 4)))
-    return fail(CN_ERR_MISALIGNED, "w and the gradients must be 4-byte aligned");
-  const size_t un = static_cast<size_t>(n);
-  if (overlaps(grad_pos, un * 12, pos_mass, un * 16) || overlaps(grad_pos, un * 12, w, un * 12) ||
-      overlaps(grad_mass, un * 4, pos_mass, un * 16) || overlaps(grad_mass, un * 4, w, un * 12) ||
-      overlaps(grad_pos, un * 12, grad_mass, un * 4))
-    return fail(CN_ERR_INVALID_ARG, "outputs overlap inputs or each other");
-  if (n == 0) return CN_OK;
-  int dev = 0;
-  DeviceInfo* d = nullptr;
-  if ((st = current_device(&dev, &d)) != CN_OK) return st;
-  const bool guard = needs_guard(eps2);
-  Plan p;
-  if ((st = resolve_plan(dev, cn::kAdjoint, n, n, guard, nullptr, &p)) != CN_OK) return st;
-  Geometry g;
-  if ((st = single_geometry(dev, *d, cn::kAdjoint, guard, p, n, n, &g)) != CN_OK) return st;
-  char *ctrl = nullptr, *data = nullptr;
-  if ((st = library_workspace(s, g.ctrl_bytes, g.data_bytes, &ctrl, &data)) != CN_OK) return st;
-  float4* wrec = reinterpret_cast<float4*>(data + g.off_wrec);
-  if (inject("launch")) return fail(CN_ERR_CUDA, "kernel launch: injected launch failure");
-  cudaError_t e = cn::launch_pack_w(w, wrec, n, s);
-  if (e != cudaSuccess) return fail_cuda(e, "weight packing launch");
-  PairArgs a = base_args(ctrl, data, g, p, d->status);
-  a.pos_i = reinterpret_cast<const float4*>(pos_mass);
-  a.pos_j = reinterpret_cast<const float4*>(pos_mass);
-  a.pos_i2 = wrec;
-  a.pos_j2 = wrec;
-  a.acc_out = grad_pos;
-  a.pot_out = grad_mass;
-  a.n_i = n;
-  a.n_j = n;
-  a.eps2 = eps2;
-  log_plan("cn_force_adjoint", cn::kAdjoint, n, n, guard, p, g, g.njt);
-  e = cn::launch_adjoint(a, p, guard, g.grid, s);
-  return e == cudaSuccess ? CN_OK : fail_cuda(e, "adjoint kernel launch");
+  return cn::guard([&]() -> cn_status {
+    auto s = reinterpret_cast<cudaStream_t>(stream);
+    if (n < 0) return fail(CN_ERR_INVALID_ARG, "n must be >= 0");
+    cn_status st;
+    if ((st = check_eps2(eps2)) != CN_OK) return st;
+    if ((st = check_records(pos_mass, n, "pos_mass")) != CN_OK) return st;
+    if (n > 0 && (!w || !grad_pos || !grad_mass)) return fail(CN_ERR_INVALID_ARG, "w, grad_pos and grad_mass are required");
+    if ((w && !aligned(w, 4)) || (grad_pos && !aligned(grad_pos, 4)) || (grad_mass && !aligned(grad_mass, 4)))
+      return fail(CN_ERR_MISALIGNED, "w and the gradients must be 4-byte aligned");
+    const size_t un = static_cast<size_t>(n);
+    if (overlaps(grad_pos, un * 12, pos_mass, un * 16) || overlaps(grad_pos, un * 12, w, un * 12) ||
+        overlaps(grad_mass, un * 4, pos_mass, un * 16) || overlaps(grad_mass, un * 4, w, un * 12) ||
+        overlaps(grad_pos, un * 12, grad_mass, un * 4))
+      return fail(CN_ERR_INVALID_ARG, "outputs overlap inputs or each other");
+    if (n == 0) return CN_OK;
+    int dev = 0;
+    DeviceInfo* d = nullptr;
+    if ((st = current_device(&dev, &d)) != CN_OK) return st;
+    const bool guard = needs_guard(eps2);
+    Plan p;
+    if ((st = resolve_plan(dev, cn::kAdjoint, n, n, guard, nullptr, &p)) != CN_OK) return st;
+    Geometry g;
+    if ((st = single_geometry(dev, *d, cn::kAdjoint, guard, p, n, n, &g)) != CN_OK) return st;
+    char *ctrl = nullptr, *data = nullptr;
+    if ((st = library_workspace(s, g.ctrl_bytes, g.data_bytes, &ctrl, &data)) != CN_OK) return st;
+    float4* wrec = reinterpret_cast<float4*>(data + g.off_wrec);
+    if (inject("launch")) return fail(CN_ERR_CUDA, "kernel launch: injected launch failure");
+    cudaError_t e = cn::launch_pack_w(w, wrec, n, s);
+    if (e != cudaSuccess) return fail_cuda(e, "weight packing launch");
+    PairArgs a = base_args(ctrl, data, g, p, d->status);
+    a.pos_i = reinterpret_cast<const float4*>(pos_mass);
+    a.pos_j = reinterpret_cast<const float4*>(pos_mass);
+    a.pos_i2 = wrec;
+    a.pos_j2 = wrec;
+    a.acc_out = grad_pos;
+    a.pot_out = grad_mass;
+    a.n_i = n;
+    a.n_j = n;
+    a.eps2 = eps2;
+    log_plan("cn_force_adjoint", cn::kAdjoint, n, n, guard, p, g, g.njt);
+    e = cn::launch_adjoint(a, p, guard, g.grid, s);
+    return e == cudaSuccess ? CN_OK : fail_cuda(e, "adjoint kernel launch");
+  });
 }
 
 cn_status cn_force_jerk(int64_t n_i, const float* pos_i, const float* vel_i, int64_t n_j, const float* pos_mass_j,
                         const float* vel_j, float eps2, float* acc_out, float* jerk_out, float* pot_out,
                         cn_stream stream) {
   NvtxRange nvtx_range("cn_force_jerk");
-  return jerk_common(n_i, pos_i, vel_i, n_j, pos_mass_j, vel_j, eps2, acc_out, jerk_out, pot_out,
-                     reinterpret_cast<cudaStream_t>(stream));
+  return cn::guard([&]() -> cn_status {
+    return jerk_common(n_i, pos_i, vel_i, n_j, pos_mass_j, vel_j, eps2, acc_out, jerk_out, pot_out,
+                       reinterpret_cast<cudaStream_t>(stream));
+  });
 }
 
 cn_status cn_force_symmetric(int64_t n, const float* pos_mass, float eps2, float* acc_out, float* pot_out,
                              cn_stream stream) {
   NvtxRange nvtx_range("cn_force_symmetric");
-  return symmetric_common(n, pos_mass, eps2, acc_out, pot_out, reinterpret_cast<cudaStream_t>(stream));
+  return cn::guard([&]() -> cn_status {
+    return symmetric_common(n, pos_mass, eps2, acc_out, pot_out, reinterpret_cast<cudaStream_t>(stream));
+  });
 }
 
 cn_status cn_potential_energy(int64_t n, const float* pos_mass, const float* pot, double* w_out, cn_stream stream) {
   NvtxRange nvtx_range("cn_potential_energy");
-  return energy_common(n, pos_mass, pot, nullptr, w_out, reinterpret_cast<cudaStream_t>(stream));
+  return cn::guard([&]() -> cn_status {
+    return energy_common(n, pos_mass, pot, nullptr, w_out, reinterpret_cast<cudaStream_t>(stream));
+  });
 }
 
 cn_status cn_potential_energy_dd(int64_t n, const float* pos_mass, const double* pot, double* w_out,
                                  cn_stream stream) {
   NvtxRange nvtx_range("cn_potential_energy_dd");
-  return energy_common(n, pos_mass, nullptr, pot, w_out, reinterpret_cast<cudaStream_t>(stream));
+  return cn::guard([&]() -> cn_status {
+    return energy_common(n, pos_mass, nullptr, pot, w_out, reinterpret_cast<cudaStream_t>(stream));
+  });
 }
 
 cn_status cn_force_host(int64_t n_i, const float* pos_i_host, int64_t n_j, const float* pos_mass_j_host, float eps2,
                         float* acc_host, float* pot_host, cn_stream stream) {
   NvtxRange nvtx_range("cn_force_host");
-  auto s = reinterpret_cast<cudaStream_t>(stream);
-  if (n_i < 0 || n_j < 0) return fail(CN_ERR_INVALID_ARG, "n_i and n_j must be >= 0");
-  if ((n_i > 0 && (!pos_i_host || !acc_host)) || (n_j > 0 && !pos_mass_j_host))
-    return fail(CN_ERR_INVALID_ARG, "NULL host buffer");
-  cn_status st = check_eps2(eps2);
-  if (st != CN_OK) return st;
-  if (n_i == 0) return CN_OK;
-  int dev = 0;
-  DeviceInfo* d = nullptr;
-  if ((st = current_device(&dev, &d)) != CN_OK) return st;
-  // i = j when the caller passes the same host array for both sets: copy it once
-  const bool same = pos_i_host == pos_mass_j_host && n_i == n_j;
-  const size_t bi = align_up(static_cast<size_t>(n_i) * 16, 256);
-  const size_t bj = same ? 0 : align_up(static_cast<size_t>(n_j) * 16, 256);
-  const size_t ba = align_up(static_cast<size_t>(n_i) * 12, 256);
-  const size_t bp = pot_host ? align_up(static_cast<size_t>(n_i) * 4, 256) : 0;
-  void* buf = nullptr;
-  if ((st = stage_buffer(s, bi + bj + ba + bp, &buf)) != CN_OK) return st;
-  char* base = static_cast<char*>(buf);
-  float* d_pi = reinterpret_cast<float*>(base);
-  float* d_pj = same ? d_pi : reinterpret_cast<float*>(base + bi);
-  float* d_acc = reinterpret_cast<float*>(base + bi + bj);
-  float* d_pot = pot_host ? reinterpret_cast<float*>(base + bi + bj + ba) : nullptr;
-  cudaError_t e = cudaMemcpyAsync(d_pi, pos_i_host, static_cast<size_t>(n_i) * 16, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess && !same && n_j > 0)
-    e = cudaMemcpyAsync(d_pj, pos_mass_j_host, static_cast<size_t>(n_j) * 16, cudaMemcpyHostToDevice, s);
-  if (e != cudaSuccess) return fail_cuda(e, "cudaMemcpyAsync(host to device)");
-  if ((st = cn_force(n_i, d_pi, n_j, d_pj, eps2, d_acc, d_pot, stream)) != CN_OK) return st;
-  e = cudaMemcpyAsync(acc_host, d_acc, static_cast<size_t>(n_i) * 12, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess && pot_host)
-    e = cudaMemcpyAsync(pot_host, d_pot, static_cast<size_t>(n_i) * 4, cudaMemcpyDeviceToHost, s);
-  if (e != cudaSuccess) return fail_cuda(e, "cudaMemcpyAsync(device to host)");
-  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return fail_cuda(e, "cudaStreamSynchronize");
-  return CN_OK;
+  return cn::guard([&]() -> cn_status {
+    auto s = reinterpret_cast<cudaStream_t>(stream);
+    if (n_i < 0 || n_j < 0) return fail(CN_ERR_INVALID_ARG, "n_i and n_j must be >= 0");
+    if ((n_i > 0 && (!pos_i_host || !acc_host)) || (n_j > 0 && !pos_mass_j_host))
+      return fail(CN_ERR_INVALID_ARG, "NULL host buffer");
+    cn_status st = check_eps2(eps2);
+    if (st != CN_OK) return st;
+    if (n_i == 0) return CN_OK;
+    int dev = 0;
+    DeviceInfo* d = nullptr;
+    if ((st = current_device(&dev, &d)) != CN_OK) return st;
+    // i = j when the caller passes the same host array for both sets: copy it once
+    const bool same = pos_i_host == pos_mass_j_host && n_i == n_j;
+    const size_t bi = align_up(static_cast<size_t>(n_i) * 16, 256);
+    const size_t bj = same ? 0 : align_up(static_cast<size_t>(n_j) * 16, 256);
+    const size_t ba = align_up(static_cast<size_t>(n_i) * 12, 256);
+    const size_t bp = pot_host ? align_up(static_cast<size_t>(n_i) * 4, 256) : 0;
+    void* buf = nullptr;
+    if ((st = stage_buffer(s, bi + bj + ba + bp, &buf)) != CN_OK) return st;
+    char* base = static_cast<char*>(buf);
+    float* d_pi = reinterpret_cast<float*>(base);
+    float* d_pj = same ? d_pi : reinterpret_cast<float*>(base + bi);
+    float* d_acc = reinterpret_cast<float*>(base + bi + bj);
+    float* d_pot = pot_host ? reinterpret_cast<float*>(base + bi + bj + ba) : nullptr;
+    cudaError_t e = cudaMemcpyAsync(d_pi, pos_i_host, static_cast<size_t>(n_i) * 16, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && !same && n_j > 0)
+      e = cudaMemcpyAsync(d_pj, pos_mass_j_host, static_cast<size_t>(n_j) * 16, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return fail_cuda(e, "cudaMemcpyAsync(host to device)");
+    if ((st = cn_force(n_i, d_pi, n_j, d_pj, eps2, d_acc, d_pot, stream)) != CN_OK) return st;
+    e = cudaMemcpyAsync(acc_host, d_acc, static_cast<size_t>(n_i) * 12, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && pot_host)
+      e = cudaMemcpyAsync(pot_host, d_pot, static_cast<size_t>(n_i) * 4, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return fail_cuda(e, "cudaMemcpyAsync(device to host)");
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return fail_cuda(e, "cudaStreamSynchronize");
+    return CN_OK;
+  });
 }
 
 cn_status cn_force_host_f64(const double* xj, const double* mj, const double* xi, double eps2, double* a, int ni,
                             int nj) {
   NvtxRange nvtx_range("cn_force_host_f64");
-  if (ni < 0 || nj < 0) return fail(CN_ERR_INVALID_ARG, "ni and nj must be >= 0");
-  if ((ni > 0 && (!xi || !a)) || (nj > 0 && (!xj || !mj))) return fail(CN_ERR_INVALID_ARG, "NULL host array");
-  if (!std::isfinite(eps2) || eps2 < 0.0) return fail(CN_ERR_INVALID_ARG, "eps2 must be finite and >= 0");
-  if (ni == 0) return CN_OK;
-  std::vector<float> pi(static_cast<size_t>(ni) * 4), pj(static_cast<size_t>(nj) * 4), acc(static_cast<size_t>(ni) * 3);
-  for (int i = 0; i < ni; ++i) {
-    for (int c = 0; c < 3; ++c) pi[4 * i + c] = static_cast<float>(xi[3 * i + c]);
-    pi[4 * i + 3] = 0.f;
-  }
-  for (int j = 0; j < nj; ++j) {
-    for (int c = 0; c < 3; ++c) pj[4 * j + c] = static_cast<float>(xj[3 * j + c]);
-    pj[4 * j + 3] = static_cast<float>(mj[j]);
-  }
-  cn_status st = cn_force_host(ni, pi.data(), nj, nj ? pj.data() : nullptr, static_cast<float>(eps2), acc.data(),
-                               nullptr, nullptr);
-  if (st != CN_OK) return st;
-  for (size_t k = 0; k < acc.size(); ++k) a[k] = acc[k];
-  return CN_OK;
+  return cn::guard([&]() -> cn_status {
+    if (ni < 0 || nj < 0) return fail(CN_ERR_INVALID_ARG, "ni and nj must be >= 0");
+    if ((ni > 0 && (!xi || !a)) || (nj > 0 && (!xj || !mj))) return fail(CN_ERR_INVALID_ARG, "NULL host array");
+    if (!std::isfinite(eps2) || eps2 < 0.0) return fail(CN_ERR_INVALID_ARG, "eps2 must be finite and >= 0");
+    if (ni == 0) return CN_OK;
+    std::vector<float> pi(static_cast<size_t>(ni) * 4), pj(static_cast<size_t>(nj) * 4), acc(static_cast<size_t>(ni) * 3);
+    for (int i = 0; i < ni; ++i) {
+      for (int c = 0; c < 3; ++c) pi[4 * i + c] = static_cast<float>(xi[3 * i + c]);
+      pi[4 * i + 3] = 0.f;
+    }
+    for (int j = 0; j < nj; ++j) {
+      for (int c = 0; c < 3; ++c) pj[4 * j + c] = static_cast<float>(xj[3 * j + c]);
+      pj[4 * j + 3] = static_cast<float>(mj[j]);
+    }
+    cn_status st = cn_force_host(ni, pi.data(), nj, nj ? pj.data() : nullptr, static_cast<float>(eps2), acc.data(),
+                                 nullptr, nullptr);
+    if (st != CN_OK) return st;
+    for (size_t k = 0; k < acc.size(); ++k) a[k] = acc[k];
+    return CN_OK;
+  });
 }
 
 cn_status cn_tune_get(int variant, int64_t n_i, int64_t n_j, cn_tune* out) {
-  if (!out || variant < cn::kF32 || variant > cn::kF32EpsIPot || n_i < 0 || n_j < 0)
-    return fail(CN_ERR_INVALID_ARG, "bad variant, size or NULL output");
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return fail_cuda(e, "cudaGetDevice");
-  Plan p;
-  cn_status st = resolve_plan(dev, variant, n_i, n_j, false, nullptr, &p);
-  if (st != CN_OK) return st;
-  out->i_per_thread = p.k;
-  out->threads = p.threads;
-  out->j_tile = p.j_tile;
-  out->stages = p.stages;
-  out->ctas_per_sm = p.ctas_per_sm;
-  out->chunk_units = static_cast<int32_t>(p.chunk_units);
-  out->j_lanes = p.j_lanes;
-  return CN_OK;
+  return cn::guard([&]() -> cn_status {
+    if (!out || variant < cn::kF32 || variant > cn::kF32EpsIPot || n_i < 0 || n_j < 0)
+      return fail(CN_ERR_INVALID_ARG, "bad variant, size or NULL output");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail_cuda(e, "cudaGetDevice");
+    Plan p;
+    cn_status st = resolve_plan(dev, variant, n_i, n_j, false, nullptr, &p);
+    if (st != CN_OK) return st;
+    out->i_per_thread = p.k;
+    out->threads = p.threads;
+    out->j_tile = p.j_tile;
+    out->stages = p.stages;
+    out->ctas_per_sm = p.ctas_per_sm;
+    out->chunk_units = static_cast<int32_t>(p.chunk_units);
+    out->j_lanes = p.j_lanes;
+    return CN_OK;
+  });
 }
 
 cn_status cn_tune_set(int variant, int64_t n_i, int64_t n_j, const cn_tune* tune) {
-  if (variant < cn::kF32 || variant > cn::kF32EpsIPot || n_i < 0 || n_j < 0)
-    return fail(CN_ERR_INVALID_ARG, "bad variant or size");
-  if (tune) {
-    cn_status st = check_tune(variant, *tune);
-    if (st != CN_OK) return st;
-  }
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return fail_cuda(e, "cudaGetDevice");
-  std::lock_guard<std::mutex> lock(g_mu);
-  const auto key = std::make_tuple(dev, variant, bucket(n_i), bucket(n_j));
-  if (tune)
-    g_tune[key] = *tune;
-  else
-    g_tune.erase(key);
-  g_plan_gen.fetch_add(1, std::memory_order_acq_rel);
-  return CN_OK;
+  return cn::guard([&]() -> cn_status {
+    if (variant < cn::kF32 || variant > cn::kF32EpsIPot || n_i < 0 || n_j < 0)
+      return fail(CN_ERR_INVALID_ARG, "bad variant or size");
+    if (tune) {
+      cn_status st = check_tune(variant, *tune);
+      if (st != CN_OK) return st;
+    }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail_cuda(e, "cudaGetDevice");
+    std::lock_guard<std::mutex> lock(g_mu);
+    const auto key = std::make_tuple(dev, variant, bucket(n_i), bucket(n_j));
+    if (tune)
+      g_tune[key] = *tune;
+    else
+      g_tune.erase(key);
+    g_plan_gen.fetch_add(1, std::memory_order_acq_rel);
+    return CN_OK;
+  });
 }
 
 cn_status cn_tune_save(const char* path) {
-  if (!path) return fail(CN_ERR_INVALID_ARG, "path is NULL");
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return fail_cuda(e, "cudaGetDevice");
-  std::string name, arch;
-  int sms = 0;
-  cn_status st = device_identity(dev, &name, &arch, &sms);
-  if (st != CN_OK) return st;
-  std::string out = "{\"format\": \"cunbody-tune-1\", \"device\": \"";
-  for (char c : name) {
-    if (c == '"' || c == '\\') out.push_back('\\');
-    out.push_back(c);
-  }
-  out += "\", \"arch\": \"" + arch + "\", \"sms\": " + std::to_string(sms) + ", \"entries\": [";
-  {
-    std::lock_guard<std::mutex> lock(g_mu);
-    bool first = true;
-    for (const auto& kv : g_tune) {
-      if (std::get<0>(kv.first) != dev) continue;
-      const cn_tune& t = kv.second;
-      char line[512];
-      std::snprintf(line, sizeof(line),
-                    "%s\n  {\"variant\": \"%s\", \"n_i_class\": %d, \"n_j_class\": %d, \"i_per_thread\": %d, "
-                    "\"threads\": %d, \"j_tile\": %d, \"stages\": %d, \"ctas_per_sm\": %d, \"chunk_units\": %d, "
-                    "\"j_lanes\": %d}",
-                    first ? "" : ",", variant_name(std::get<1>(kv.first)), std::get<2>(kv.first), std::get<3>(kv.first),
-                    t.i_per_thread, t.threads, t.j_tile, t.stages, t.ctas_per_sm, t.chunk_units, t.j_lanes);
-      out += line;
-      first = false;
+  return cn::guard([&]() -> cn_status {
+    if (!path) return fail(CN_ERR_INVALID_ARG, "path is NULL");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail_cuda(e, "cudaGetDevice");
+    std::string name, arch;
+    int sms = 0;
+    cn_status st = device_identity(dev, &name, &arch, &sms);
+    if (st != CN_OK) return st;
+    std::string out = "{\"format\": \"cunbody-tune-1\", \"device\": \"";
+    for (char c : name) {
+      if (c == '"' || c == '\\') out.push_back('\\');
+      out.push_back(c);
     }
-  }
-  out += "\n]}\n";
-  FILE* f = std::fopen(path, "w");
-  if (!f) return fail(CN_ERR_INVALID_ARG, std::string("cannot write ") + path);
-  const bool ok = std::fwrite(out.data(), 1, out.size(), f) == out.size();
-  if (std::fclose(f) != 0 || !ok) return fail(CN_ERR_INVALID_ARG, std::string("writing ") + path + " failed");
-  return CN_OK;
+    out += "\", \"arch\": \"" + arch + "\", \"sms\": " + std::to_string(sms) + ", \"entries\": [";
+    {
+      std::lock_guard<std::mutex> lock(g_mu);
+      bool first = true;
+      for (const auto& kv : g_tune) {
+        if (std::get<0>(kv.first) != dev) continue;
+        const cn_tune& t = kv.second;
+        char line[512];
+        std::snprintf(line, sizeof(line),
+                      "%s\n  {\"variant\": \"%s\", \"n_i_class\": %d, \"n_j_class\": %d, \"i_per_thread\": %d, "
+                      "\"threads\": %d, \"j_tile\": %d, \"stages\": %d, \"ctas_per_sm\": %d, \"chunk_units\": %d, "
+                      "\"j_lanes\": %d}",
+                      first ? "" : ",", variant_name(std::get<1>(kv.first)), std::get<2>(kv.first), std::get<3>(kv.first),
+                      t.i_per_thread, t.threads, t.j_tile, t.stages, t.ctas_per_sm, t.chunk_units, t.j_lanes);
+        out += line;
+        first = false;
+      }
+    }
+    out += "\n]}\n";
+    FILE* f = std::fopen(path, "w");
+    if (!f) return fail(CN_ERR_INVALID_ARG, std::string("cannot write ") + path);
+    const bool ok = std::fwrite(out.data(), 1, out.size(), f) == out.size();
+    if (std::fclose(f) != 0 || !ok) return fail(CN_ERR_INVALID_ARG, std::string("writing ") + path + " failed");
+    return CN_OK;
+  });
 }
 
 cn_status cn_tune_load(const char* path, int32_t* n_loaded) {
-  if (n_loaded) *n_loaded = 0;
-  if (!path) return fail(CN_ERR_INVALID_ARG, "path is NULL");
-  FILE* f = std::fopen(path, "r");
-  if (!f) return fail(CN_ERR_INVALID_ARG, std::string("cannot read ") + path);
-  std::string text;
-  char buf[4096];
-  size_t got;
-  while ((got = std::fread(buf, 1, sizeof(buf), f)) > 0 && text.size() < (static_cast<size_t>(1) << 24))
-    text.append(buf, got);
-  std::fclose(f);
-  JsonValue root;
-  JsonReader rd{text};
-  if (!rd.value(&root) || root.kind != JsonValue::kObject) return fail(CN_ERR_INVALID_ARG, "tuning file: not a JSON object");
-  rd.skip();
-  if (rd.pos != text.size()) return fail(CN_ERR_INVALID_ARG, "tuning file: trailing characters");
-  const JsonValue* fmt = root.get("format");
-  const JsonValue* dname = root.get("device");
-  const JsonValue* darch = root.get("arch");
-  const JsonValue* entries = root.get("entries");
-  int64_t file_sms = 0;
-  if (!fmt || fmt->kind != JsonValue::kString || fmt->text != "cunbody-tune-1")
-    return fail(CN_ERR_INVALID_ARG, "tuning file: unknown format");
-  if (!dname || dname->kind != JsonValue::kString || !darch || darch->kind != JsonValue::kString ||
-      !json_int(root, "sms", 1, 1 << 20, &file_sms) || !entries || entries->kind != JsonValue::kArray)
-    return fail(CN_ERR_INVALID_ARG, "tuning file: device, arch, sms or entries missing");
-  struct Entry {
-    int variant, ci, cj;
-    cn_tune t;
-  };
-  std::vector<Entry> parsed;
-  for (const JsonValue& e : entries->items) {
-    if (e.kind != JsonValue::kObject) return fail(CN_ERR_INVALID_ARG, "tuning file: an entry is not an object");
-    const JsonValue* vn = e.get("variant");
-    const int variant = (vn && vn->kind == JsonValue::kString) ? variant_from_name(vn->text) : -1;
-    int64_t ci, cj, k, th, jt, stg, cps, ch, jl;
-    if (variant < 0 || !json_int(e, "n_i_class", 0, 62, &ci) || !json_int(e, "n_j_class", 0, 62, &cj) ||
-        !json_int(e, "i_per_thread", 0, 8, &k) || !json_int(e, "threads", 0, 1024, &th) ||
-        !json_int(e, "j_tile", 0, 4096, &jt) || !json_int(e, "stages", 0, 8, &stg) ||
-        !json_int(e, "ctas_per_sm", 0, 64, &cps) || !json_int(e, "chunk_units", 0, INT32_MAX, &ch) ||
-        !json_int(e, "j_lanes", 0, 32, &jl))
-      return fail(CN_ERR_INVALID_ARG, "tuning file: an entry has a missing or out-of-range field");
-    Entry en{variant, static_cast<int>(ci), static_cast<int>(cj),
-             cn_tune{static_cast<int32_t>(k), static_cast<int32_t>(th), static_cast<int32_t>(jt),
-                     static_cast<int32_t>(stg), static_cast<int32_t>(cps), static_cast<int32_t>(ch),
-                     static_cast<int32_t>(jl)}};
-    const cn_status st = check_tune(variant, en.t);
+  return cn::guard([&]() -> cn_status {
+    if (n_loaded) *n_loaded = 0;
+    if (!path) return fail(CN_ERR_INVALID_ARG, "path is NULL");
+    FILE* f = std::fopen(path, "r");
+    if (!f) return fail(CN_ERR_INVALID_ARG, std::string("cannot read ") + path);
+    std::string text;
+    char buf[4096];
+    size_t got;
+    while ((got = std::fread(buf, 1, sizeof(buf), f)) > 0 && text.size() < (static_cast<size_t>(1) << 24))
+      text.append(buf, got);
+    std::fclose(f);
+    JsonValue root;
+    JsonReader rd{text};
+    if (!rd.value(&root) || root.kind != JsonValue::kObject) return fail(CN_ERR_INVALID_ARG, "tuning file: not a JSON object");
+    rd.skip();
+    if (rd.pos != text.size()) return fail(CN_ERR_INVALID_ARG, "tuning file: trailing characters");
+    const JsonValue* fmt = root.get("format");
+    const JsonValue* dname = root.get("device");
+    const JsonValue* darch = root.get("arch");
+    const JsonValue* entries = root.get("entries");
+    int64_t file_sms = 0;
+    if (!fmt || fmt->kind != JsonValue::kString || fmt->text != "cunbody-tune-1")
+      return fail(CN_ERR_INVALID_ARG, "tuning file: unknown format");
+    if (!dname || dname->kind != JsonValue::kString || !darch || darch->kind != JsonValue::kString ||
+        !json_int(root, "sms", 1, 1 << 20, &file_sms) || !entries || entries->kind != JsonValue::kArray)
+      return fail(CN_ERR_INVALID_ARG, "tuning file: device, arch, sms or entries missing");
+    struct Entry {
+      int variant, ci, cj;
+      cn_tune t;
+    };
+    std::vector<Entry> parsed;
+    for (const JsonValue& e : entries->items) {
+      if (e.kind != JsonValue::kObject) return fail(CN_ERR_INVALID_ARG, "tuning file: an entry is not an object");
+      const JsonValue* vn = e.get("variant");
+      const int variant = (vn && vn->kind == JsonValue::kString) ? variant_from_name(vn->text) : -1;
+      int64_t ci, cj, k, th, jt, stg, cps, ch, jl;
+      if (variant < 0 || !json_int(e, "n_i_class", 0, 62, &ci) || !json_int(e, "n_j_class", 0, 62, &cj) ||
+          !json_int(e, "i_per_thread", 0, 8, &k) || !json_int(e, "threads", 0, 1024, &th) ||
+          !json_int(e, "j_tile", 0, 4096, &jt) || !json_int(e, "stages", 0, 8, &stg) ||
+          !json_int(e, "ctas_per_sm", 0, 64, &cps) || !json_int(e, "chunk_units", 0, INT32_MAX, &ch) ||
+          !json_int(e, "j_lanes", 0, 32, &jl))
+        return fail(CN_ERR_INVALID_ARG, "tuning file: an entry has a missing or out-of-range field");
+      Entry en{variant, static_cast<int>(ci), static_cast<int>(cj),
+               cn_tune{static_cast<int32_t>(k), static_cast<int32_t>(th), static_cast<int32_t>(jt),
+                       static_cast<int32_t>(stg), static_cast<int32_t>(cps), static_cast<int32_t>(ch),
+                       static_cast<int32_t>(jl)}};
+      const cn_status st = check_tune(variant, en.t);
+      if (st != CN_OK) return st;
+      parsed.push_back(en);
+    }
+    int dev = 0;
+    cudaError_t ce = cudaGetDevice(&dev);
+    if (ce != cudaSuccess) return fail_cuda(ce, "cudaGetDevice");
+    std::string name, arch;
+    int sms = 0;
+    cn_status st = device_identity(dev, &name, &arch, &sms);
     if (st != CN_OK) return st;
-    parsed.push_back(en);
-  }
-  int dev = 0;
-  cudaError_t ce = cudaGetDevice(&dev);
-  if (ce != cudaSuccess) return fail_cuda(ce, "cudaGetDevice");
-  std::string name, arch;
-  int sms = 0;
-  cn_status st = device_identity(dev, &name, &arch, &sms);
-  if (st != CN_OK) return st;
-  if (name != dname->text || arch != darch->text || sms != file_sms)
-    return fail(CN_ERR_UNSUPPORTED_DEVICE, "tuning file was written on " + dname->text + " (" + darch->text + ", " +
-                                               std::to_string(file_sms) + " SMs), this device is " + name + " (" +
-                                               arch + ", " + std::to_string(sms) + " SMs)");
-  {
-    std::lock_guard<std::mutex> lock(g_mu);
-    for (const Entry& en : parsed) g_tune[std::make_tuple(dev, en.variant, en.ci, en.cj)] = en.t;
-    g_plan_gen.fetch_add(1, std::memory_order_acq_rel);
-  }
-  if (n_loaded) *n_loaded = static_cast<int32_t>(parsed.size());
-  return CN_OK;
+    if (name != dname->text || arch != darch->text || sms != file_sms)
+      return fail(CN_ERR_UNSUPPORTED_DEVICE, "tuning file was written on " + dname->text + " (" + darch->text + ", " +
+                                                 std::to_string(file_sms) + " SMs), this device is " + name + " (" +
+                                                 arch + ", " + std::to_string(sms) + " SMs)");
+    {
+      std::lock_guard<std::mutex> lock(g_mu);
+      for (const Entry& en : parsed) g_tune[std::make_tuple(dev, en.variant, en.ci, en.cj)] = en.t;
+      g_plan_gen.fetch_add(1, std::memory_order_acq_rel);
+    }
+    if (n_loaded) *n_loaded = static_cast<int32_t>(parsed.size());
+    return CN_OK;
+  });
 }
 
 cn_status cn_autotune(int variant, int64_t n_i, const float* pos_i, int64_t n_j, const float* pos_mass_j, float eps2,
                       void* acc_out, void* pot_out, int reps, cn_stream stream, cn_tune* best_out) {
   NvtxRange nvtx_range("cn_autotune");
-  if (variant < cn::kF32 || variant > cn::kDDPot) return fail(CN_ERR_INVALID_ARG, "cn_autotune covers the F32 and DD variants");
-  if (n_i <= 0 || n_j <= 0) return fail(CN_ERR_INVALID_ARG, "autotuning needs n_i > 0 and n_j > 0");
-  const bool dd = variant == cn::kDD || variant == cn::kDDPot;
-  const bool pot = variant == cn::kF32Pot || variant == cn::kDDPot;
-  if (pot && !pot_out) return fail(CN_ERR_INVALID_ARG, "the potential variants need pot_out");
-  auto s = reinterpret_cast<cudaStream_t>(stream);
-  if (reps < 1) reps = 1;
-  const int ks[] = {1, 2, 4, 8};
-  const int ths[] = {64, 128, 256};
-  const int tiles[] = {128, 256, 512, 1024};
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
-  float best_ms = 1e30f;
-  cn_tune best{};
-  cn_status result = CN_OK;
-  std::vector<cn_tune> cands;
-  {
-    // the default shape of these sizes first (its j-tile fitted to the
-    // schedule, which the grid below does not contain), so that the result
-    // is never slower than the default by more than the timing noise
-    int dev = 0;
-    DeviceInfo* d = nullptr;
-    cn_status st = current_device(&dev, &d);
-    if (st != CN_OK) return st;
-    cands.push_back(default_tune(variant, n_i, n_j, d->sms));
-  }
-  for (int k : ks) {
-    if (!valid_k(variant, k)) continue;
-    for (int th : ths) {
-      if (static_cast<int64_t>(k) * th > 4 * std::max<int64_t>(n_i, 256)) continue;  // tile far larger than the i set
-      for (int jt : tiles) {
-        if (jt > 4 * std::max<int64_t>(n_j, 64)) continue;
-        cands.push_back(cn_tune{k, th, jt, 4, 0, 0, 1});
+  return cn::guard([&]() -> cn_status {
+    if (variant < cn::kF32 || variant > cn::kDDPot) return fail(CN_ERR_INVALID_ARG, "cn_autotune covers the F32 and DD variants");
+    if (n_i <= 0 || n_j <= 0) return fail(CN_ERR_INVALID_ARG, "autotuning needs n_i > 0 and n_j > 0");
+    const bool dd = variant == cn::kDD || variant == cn::kDDPot;
+    const bool pot = variant == cn::kF32Pot || variant == cn::kDDPot;
+    if (pot && !pot_out) return fail(CN_ERR_INVALID_ARG, "the potential variants need pot_out");
+    auto s = reinterpret_cast<cudaStream_t>(stream);
+    if (reps < 1) reps = 1;
+    const int ks[] = {1, 2, 4, 8};
+    const int ths[] = {64, 128, 256};
+    const int tiles[] = {128, 256, 512, 1024};
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best_ms = 1e30f;
+    cn_tune best{};
+    cn_status result = CN_OK;
+    std::vector<cn_tune> cands;
+    {
+      // the default shape of these sizes first (its j-tile fitted to the
+      // schedule, which the grid below does not contain), so that the result
+      // is never slower than the default by more than the timing noise
+      int dev = 0;
+      DeviceInfo* d = nullptr;
+      cn_status st = current_device(&dev, &d);
+      if (st != CN_OK) return st;
+      cands.push_back(default_tune(variant, n_i, n_j, d->sms));
+    }
+    for (int k : ks) {
+      if (!valid_k(variant, k)) continue;
+      for (int th : ths) {
+        if (static_cast<int64_t>(k) * th > 4 * std::max<int64_t>(n_i, 256)) continue;  // tile far larger than the i set
+        for (int jt : tiles) {
+          if (jt > 4 * std::max<int64_t>(n_j, 64)) continue;
+          cands.push_back(cn_tune{k, th, jt, 4, 0, 0, 1});
+        }
       }
     }
-  }
-  if (!dd && n_i <= 16384) {  // split-j shapes for small systems
-    for (int jl : {2, 4, 8, 16, 32}) {
-      if (n_i * jl > 262144) continue;
-      for (int th : {128, 256})
-        for (int64_t jt : {static_cast<int64_t>(512), static_cast<int64_t>(2048), round_up(std::max<int64_t>(n_j, 1), 8 * jl),
-                           static_cast<int64_t>(4096)}) {
-          if (jt % (8 * jl) || jt > 4096 || jt < 8 * jl) continue;
-          for (int k : {1, 2, 4, 8}) {  // i-particles per lane group (packed for K >= 2)
-            if (static_cast<int64_t>(k) * th / jl > 4 * std::max<int64_t>(n_i, 64)) continue;
-            cands.push_back(cn_tune{k, th, static_cast<int32_t>(jt), jt >= n_j ? 1 : 3, 0, 0, jl});
+    if (!dd && n_i <= 16384) {  // split-j shapes for small systems
+      for (int jl : {2, 4, 8, 16, 32}) {
+        if (n_i * jl > 262144) continue;
+        for (int th : {128, 256})
+          for (int64_t jt : {static_cast<int64_t>(512), static_cast<int64_t>(2048), round_up(std::max<int64_t>(n_j, 1), 8 * jl),
+                             static_cast<int64_t>(4096)}) {
+            if (jt % (8 * jl) || jt > 4096 || jt < 8 * jl) continue;
+            for (int k : {1, 2, 4, 8}) {  // i-particles per lane group (packed for K >= 2)
+              if (static_cast<int64_t>(k) * th / jl > 4 * std::max<int64_t>(n_i, 64)) continue;
+              cands.push_back(cn_tune{k, th, static_cast<int32_t>(jt), jt >= n_j ? 1 : 3, 0, 0, jl});
+            }
           }
-        }
+      }
     }
-  }
-  // Candidates are timed as one CUDA graph of `reps` calls, so that the host
-  // cost of a call does not hide the device time of small problems. Capture
-  // needs a non-default stream: the legacy stream gets a private one.
-  cudaStream_t ts = s;
-  const bool own_stream = (s == nullptr);
-  if (own_stream && cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking) != cudaSuccess) {
+    // Candidates are timed as one CUDA graph of `reps` calls, so that the host
+    // cost of a call does not hide the device time of small problems. Capture
+    // needs a non-default stream: the legacy stream gets a private one.
+    cudaStream_t ts = s;
+    const bool own_stream = (s == nullptr);
+    if (own_stream && cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return fail(CN_ERR_CUDA, "autotune: cudaStreamCreate failed");
+    }
+    auto call = [&]() {
+      return force_common(dd, n_i, pos_i, n_j, pos_mass_j, eps2, acc_out, pot ? pot_out : nullptr, nullptr, 0, true,
+                          ts);
+    };
+    for (const cn_tune& t : cands) {
+      if (check_tune(variant, t) != CN_OK) continue;
+      cn_tune_set(variant, n_i, n_j, &t);
+      cn_status st = call();  // warm-up (and workspace growth)
+      if (st == CN_ERR_INVALID_ARG) continue;  // shape does not fit
+      if (st != CN_OK) {
+        result = st;
+        break;
+      }
+      cudaGraph_t graph = nullptr;
+      cudaGraphExec_t exec = nullptr;
+      if (cudaStreamBeginCapture(ts, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        result = fail(CN_ERR_CUDA, "autotune: cudaStreamBeginCapture failed");
+        break;
+      }
+      for (int r = 0; r < reps && st == CN_OK; ++r) st = call();
+      cudaError_t e = cudaStreamEndCapture(ts, &graph);
+      if (st == CN_OK && e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+      if (st == CN_OK && e == cudaSuccess) e = cudaGraphLaunch(exec, ts);  // warm
+      if (st == CN_OK && e == cudaSuccess) e = cudaEventRecord(e0, ts);
+      if (st == CN_OK && e == cudaSuccess) e = cudaGraphLaunch(exec, ts);
+      if (st == CN_OK && e == cudaSuccess) e = cudaEventRecord(e1, ts);
+      if (st == CN_OK && e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (st == CN_OK && e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+      if (exec) cudaGraphExecDestroy(exec);
+      if (graph) cudaGraphDestroy(graph);
+      if (st != CN_OK) {
+        result = st;
+        break;
+      }
+      if (e != cudaSuccess) {
+        result = fail_cuda(e, "autotune: timing a candidate");
+        break;
+      }
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = t;
+      }
+    }
+    if (own_stream) {
+      cudaStreamSynchronize(ts);
+      release_library_workspace(ts);
+      cudaStreamDestroy(ts);
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    return fail(CN_ERR_CUDA, "autotune: cudaStreamCreate failed");
-  }
-  auto call = [&]() {
-    return force_common(dd, n_i, pos_i, n_j, pos_mass_j, eps2, acc_out, pot ? pot_out : nullptr, nullptr, 0, true,
-                        ts);
-  };
-  for (const cn_tune& t : cands) {
-    if (check_tune(variant, t) != CN_OK) continue;
-    cn_tune_set(variant, n_i, n_j, &t);
-    cn_status st = call();  // warm-up (and workspace growth)
-    if (st == CN_ERR_INVALID_ARG) continue;  // shape does not fit
-    if (st != CN_OK) {
-      result = st;
-      break;
+    if (result != CN_OK) {
+      cn_tune_set(variant, n_i, n_j, nullptr);
+      return result;
     }
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    if (cudaStreamBeginCapture(ts, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
-      result = fail(CN_ERR_CUDA, "autotune: cudaStreamBeginCapture failed");
-      break;
+    if (best_ms >= 1e30f) {
+      cn_tune_set(variant, n_i, n_j, nullptr);
+      return fail(CN_ERR_INVALID_ARG, "no candidate launch shape fits");
     }
-    for (int r = 0; r < reps && st == CN_OK; ++r) st = call();
-    cudaError_t e = cudaStreamEndCapture(ts, &graph);
-    if (st == CN_OK && e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
-    if (st == CN_OK && e == cudaSuccess) e = cudaGraphLaunch(exec, ts);  // warm
-    if (st == CN_OK && e == cudaSuccess) e = cudaEventRecord(e0, ts);
-    if (st == CN_OK && e == cudaSuccess) e = cudaGraphLaunch(exec, ts);
-    if (st == CN_OK && e == cudaSuccess) e = cudaEventRecord(e1, ts);
-    if (st == CN_OK && e == cudaSuccess) e = cudaEventSynchronize(e1);
-    float ms = 0.f;
-    if (st == CN_OK && e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
-    if (exec) cudaGraphExecDestroy(exec);
-    if (graph) cudaGraphDestroy(graph);
-    if (st != CN_OK) {
-      result = st;
-      break;
-    }
-    if (e != cudaSuccess) {
-      result = fail_cuda(e, "autotune: timing a candidate");
-      break;
-    }
-    if (ms < best_ms) {
-      best_ms = ms;
-      best = t;
-    }
-  }
-  if (own_stream) {
-    cudaStreamSynchronize(ts);
-    release_library_workspace(ts);
-    cudaStreamDestroy(ts);
-  }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  if (result != CN_OK) {
-    cn_tune_set(variant, n_i, n_j, nullptr);
-    return result;
-  }
-  if (best_ms >= 1e30f) {
-    cn_tune_set(variant, n_i, n_j, nullptr);
-    return fail(CN_ERR_INVALID_ARG, "no candidate launch shape fits");
-  }
-  cn_tune_set(variant, n_i, n_j, &best);
-  if (best_out) *best_out = best;
-  return CN_OK;
+    cn_tune_set(variant, n_i, n_j, &best);
+    if (best_out) *best_out = best;
+    return CN_OK;
+  });
 }
 
 cn_status cn_autotune_batched(int32_t n_clusters, const int64_t* offsets_host, const float* eps2_host,
                               const float* pos_mass, float* acc_out, float* pot_out, int reps, cn_stream stream,
                               cn_tune* best_out) {
   NvtxRange nvtx_range("cn_autotune_batched");
-  if (n_clusters <= 0 || !offsets_host) return fail(CN_ERR_INVALID_ARG, "empty ensemble");
-  auto s = reinterpret_cast<cudaStream_t>(stream);
-  if (reps < 1) reps = 1;
-  const int variant = pot_out ? cn::kBatchedPot : cn::kBatched;
-  const int ks[] = {2, 4, 8};
-  const int ths[] = {64, 128, 256};
-  const int tiles[] = {128, 256, 512};
-  const int chunks[] = {0, 8, 32};
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
-  float best_ms = 1e30f;
-  cn_tune best{};
-  cn_status result = CN_OK;
-  std::vector<cn_tune> cands;
-  for (int k : ks)
-    for (int th : ths)
-      for (int jt : tiles)
-        for (int ch : chunks) cands.push_back(cn_tune{k, th, jt, 4, 0, ch, 1});
-  // split-j shapes: eight i-particles per lane group, small i-tiles
-  for (int jl : {2, 4, 8})
-    for (int jt : {256, 512})
-      for (int ch : {0, 8}) cands.push_back(cn_tune{8, 256, jt, 4, 0, ch, jl});
-  for (const cn_tune& t : cands) {
-    if (result != CN_OK) break;
-    cn_batch_plan* plan = nullptr;
-    cn_status st = build_batch_plan(n_clusters, offsets_host, eps2_host, &t, pot_out != nullptr, &plan);
-    if (st != CN_OK) {
-      if (st == CN_ERR_INVALID_ARG) continue;
-      result = st;
-      break;
-    }
-    st = run_batched(plan, pos_mass, pos_mass, acc_out, pot_out, nullptr, 0, s);
-    if (st == CN_OK) {
-      cudaEventRecord(e0, s);
-      for (int r = 0; r < reps; ++r) run_batched(plan, pos_mass, pos_mass, acc_out, pot_out, nullptr, 0, s);
-      cudaEventRecord(e1, s);
-      if (cudaEventSynchronize(e1) == cudaSuccess) {
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best_ms) {
-          best_ms = ms;
-          best = t;
-        }
-      } else {
-        st = fail(CN_ERR_CUDA, "autotune: event synchronisation failed");
+  return cn::guard([&]() -> cn_status {
+    if (n_clusters <= 0 || !offsets_host) return fail(CN_ERR_INVALID_ARG, "empty ensemble");
+    auto s = reinterpret_cast<cudaStream_t>(stream);
+    if (reps < 1) reps = 1;
+    const int variant = pot_out ? cn::kBatchedPot : cn::kBatched;
+    const int ks[] = {2, 4, 8};
+    const int ths[] = {64, 128, 256};
+    const int tiles[] = {128, 256, 512};
+    const int chunks[] = {0, 8, 32};
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best_ms = 1e30f;
+    cn_tune best{};
+    cn_status result = CN_OK;
+    std::vector<cn_tune> cands;
+    for (int k : ks)
+      for (int th : ths)
+        for (int jt : tiles)
+          for (int ch : chunks) cands.push_back(cn_tune{k, th, jt, 4, 0, ch, 1});
+    // split-j shapes: eight i-particles per lane group, small i-tiles
+    for (int jl : {2, 4, 8})
+      for (int jt : {256, 512})
+        for (int ch : {0, 8}) cands.push_back(cn_tune{8, 256, jt, 4, 0, ch, jl});
+    for (const cn_tune& t : cands) {
+      if (result != CN_OK) break;
+      cn_batch_plan* plan = nullptr;
+      cn_status st = build_batch_plan(n_clusters, offsets_host, eps2_host, &t, pot_out != nullptr, &plan);
+      if (st != CN_OK) {
+        if (st == CN_ERR_INVALID_ARG) continue;
+        result = st;
+        break;
       }
+      st = run_batched(plan, pos_mass, pos_mass, acc_out, pot_out, nullptr, 0, s);
+      if (st == CN_OK) {
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < reps; ++r) run_batched(plan, pos_mass, pos_mass, acc_out, pot_out, nullptr, 0, s);
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) == cudaSuccess) {
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          if (ms < best_ms) {
+            best_ms = ms;
+            best = t;
+          }
+        } else {
+          st = fail(CN_ERR_CUDA, "autotune: event synchronisation failed");
+        }
+      }
+      cn_batch_plan_destroy(plan);
+      if (st != CN_OK) result = st;
     }
-    cn_batch_plan_destroy(plan);
-    if (st != CN_OK) result = st;
-  }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  if (result != CN_OK) return result;
-  if (best_ms >= 1e30f) return fail(CN_ERR_INVALID_ARG, "no candidate launch shape fits");
-  const int64_t n_total = offsets_host[n_clusters];
-  cn_tune_set(variant, n_clusters, n_total, &best);
-  if (best_out) *best_out = best;
-  return CN_OK;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (result != CN_OK) return result;
+    if (best_ms >= 1e30f) return fail(CN_ERR_INVALID_ARG, "no candidate launch shape fits");
+    const int64_t n_total = offsets_host[n_clusters];
+    cn_tune_set(variant, n_clusters, n_total, &best);
+    if (best_out) *best_out = best;
+    return CN_OK;
+  });
 }
 
 cn_status cn_get_device_status(cn_stream stream) {
   NvtxRange nvtx_range("cn_get_device_status");
-  auto s = reinterpret_cast<cudaStream_t>(stream);
-  int dev = 0;
-  DeviceInfo* d = nullptr;
-  cn_status st = current_device(&dev, &d);
-  if (st != CN_OK) return st;
-  cudaError_t e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return fail_cuda(e, "cudaStreamSynchronize");
-  int flag = 0;
-  if ((e = cudaMemcpy(&flag, d->status, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
-    return fail_cuda(e, "reading the device status word");
-  if (flag == 0) return CN_OK;
-  const int zero = 0;
-  cudaMemcpy(d->status, &zero, sizeof(int), cudaMemcpyHostToDevice);
-  {
-    // arrival counters may have been left mid-protocol: clear every library workspace of this device
-    std::lock_guard<std::mutex> lock(g_mu);
-    for (auto& kv : g_ws)
-      if (kv.first.first == dev) {
-        if (kv.second.ctrl) cudaMemset(kv.second.ctrl, 0, kv.second.ctrl_bytes);
-        if (kv.second.aux) cudaMemset(kv.second.aux, 0, (cn::energy_workspace_doubles() + 1) * sizeof(double));
-      }
-  }
-  cudaDeviceSynchronize();
-  return fail(CN_ERR_TIMEOUT, "a kernel wait timed out (device status bits " + std::to_string(flag) + ")");
+  return cn::guard([&]() -> cn_status {
+    auto s = reinterpret_cast<cudaStream_t>(stream);
+    int dev = 0;
+    DeviceInfo* d = nullptr;
+    cn_status st = current_device(&dev, &d);
+    if (st != CN_OK) return st;
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail_cuda(e, "cudaStreamSynchronize");
+    int flag = 0;
+    if ((e = cudaMemcpy(&flag, d->status, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+      return fail_cuda(e, "reading the device status word");
+    if (flag == 0) return CN_OK;
+    const int zero = 0;
+    cudaMemcpy(d->status, &zero, sizeof(int), cudaMemcpyHostToDevice);
+    {
+      // arrival counters may have been left mid-protocol: clear every library workspace of this device
+      std::lock_guard<std::mutex> lock(g_mu);
+      for (auto& kv : g_ws)
+        if (kv.first.first == dev) {
+          if (kv.second.ctrl) cudaMemset(kv.second.ctrl, 0, kv.second.ctrl_bytes);
+          if (kv.second.aux) cudaMemset(kv.second.aux, 0, (cn::energy_workspace_doubles() + 1) * sizeof(double));
+        }
+    }
+    cudaDeviceSynchronize();
+    return fail(CN_ERR_TIMEOUT, "a kernel wait timed out (device status bits " + std::to_string(flag) + ")");
+  });
 }
 
 cn_status cn_set_wait_limit_ns(uint64_t ns) {
-  g_wait_ns.store(ns ? ns : kDefaultWaitNs);
-  return CN_OK;
+  return cn::guard([&]() -> cn_status {
+    g_wait_ns.store(ns ? ns : kDefaultWaitNs);
+    return CN_OK;
+  });
 }
 
 cn_status cn_debug_timeout_probe(cn_stream stream) {
-  int dev = 0;
-  DeviceInfo* d = nullptr;
-  cn_status st = current_device(&dev, &d);
-  if (st != CN_OK) return st;
-  cudaError_t e = cn::launch_timeout_probe(d->status, g_wait_ns.load(), reinterpret_cast<cudaStream_t>(stream));
-  return e == cudaSuccess ? CN_OK : fail_cuda(e, "timeout probe launch");
+  return cn::guard([&]() -> cn_status {
+    int dev = 0;
+    DeviceInfo* d = nullptr;
+    cn_status st = current_device(&dev, &d);
+    if (st != CN_OK) return st;
+    cudaError_t e = cn::launch_timeout_probe(d->status, g_wait_ns.load(), reinterpret_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? CN_OK : fail_cuda(e, "timeout probe launch");
+  });
 }
 
 cn_status cn_probe_peaks(cn_stream stream, double* out5) {
-  if (!out5) return fail(CN_ERR_INVALID_ARG, "out is NULL");
-  int dev = 0;
-  DeviceInfo* d = nullptr;
-  cn_status st = current_device(&dev, &d);
-  if (st != CN_OK) return st;
-  cudaError_t e = cn::run_probes(reinterpret_cast<cudaStream_t>(stream), out5);
-  return e == cudaSuccess ? CN_OK : fail_cuda(e, "issue-rate probes");
+  return cn::guard([&]() -> cn_status {
+    if (!out5) return fail(CN_ERR_INVALID_ARG, "out is NULL");
+    int dev = 0;
+    DeviceInfo* d = nullptr;
+    cn_status st = current_device(&dev, &d);
+    if (st != CN_OK) return st;
+    cudaError_t e = cn::run_probes(reinterpret_cast<cudaStream_t>(stream), out5);
+    return e == cudaSuccess ? CN_OK : fail_cuda(e, "issue-rate probes");
+  });
 }
 
 const char* cn_status_string(cn_status status) {
@@ -2317,6 +2396,7 @@ const char* cn_status_string(cn_status status) {
     case CN_ERR_TIMEOUT: return "CN_ERR_TIMEOUT";
     case CN_ERR_UNSUPPORTED_DEVICE: return "CN_ERR_UNSUPPORTED_DEVICE";
     case CN_ERR_WORKSPACE: return "CN_ERR_WORKSPACE";
+    case CN_ERR_HOST: return "CN_ERR_HOST";
   }
   return "CN_ERR_UNKNOWN";
 }

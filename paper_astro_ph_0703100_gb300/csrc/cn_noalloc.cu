@@ -8,6 +8,7 @@
 // array that is part of the library's device image, so it allocates
 // nothing. The paper has no counterpart.
 #include "cunbody.h"
+#include "cn_guard.h"
 #include "cn_kernels.h"
 
 #include <nvtx3/nvToolsExt.h>
@@ -79,7 +80,8 @@ cn_status noalloc_call(int64_t n_i, const float* pos_i, int64_t n_j, const float
 extern "C" cn_status cn_force_noalloc(int64_t n_i, const float* pos_i, int64_t n_j, const float* pos_mass_j,
                                       float eps2, float* acc_out, float* pot_out, cn_stream stream) {
   nvtxRangePushA("cn_force_noalloc");
-  const cn_status st = noalloc_call(n_i, pos_i, n_j, pos_mass_j, eps2, acc_out, pot_out, stream);
+  const cn_status st =
+      cn::guard([&]() -> cn_status { return noalloc_call(n_i, pos_i, n_j, pos_mass_j, eps2, acc_out, pot_out, stream); });
   nvtxRangePop();
   return st;
 }

@@ -51,7 +51,8 @@ def test_library_exports_every_declared_symbol(lib):
 
 def test_status_strings_and_version(lib):
     for code, name in {0: "CN_OK", 1: "CN_ERR_INVALID_ARG", 2: "CN_ERR_MISALIGNED", 3: "CN_ERR_CUDA",
-                       4: "CN_ERR_TIMEOUT", 5: "CN_ERR_UNSUPPORTED_DEVICE", 6: "CN_ERR_WORKSPACE"}.items():
+                       4: "CN_ERR_TIMEOUT", 5: "CN_ERR_UNSUPPORTED_DEVICE", 6: "CN_ERR_WORKSPACE",
+                       7: "CN_ERR_HOST"}.items():
         assert lib.cn_status_string(code).decode() == name
     assert b"sm_103a" in lib.cn_version()
 
@@ -165,6 +166,29 @@ def test_indexed_list_plan_validation(lib):
     assert lib.cn_list_plan_create_indexed(2, i_off, (ctypes.c_int64 * 2)(0, 3), (ctypes.c_int64 * 2)(3, 3), eps,
                                            idx, 6, 10, None, 0, None) == 1  # NULL plan_out
     assert h.value is None
+
+
+def test_no_exception_leaves_the_library(lib, monkeypatch):
+    """Host memory exhausted while a plan is built (CN_FAULT_INJECT=hostmem
+    throws std::bad_alloc inside the library, after the arguments were
+    checked and before any device work) comes back as CN_ERR_HOST with a
+    message; no plan is returned and the process carries on."""
+    h = ctypes.c_void_p()
+    offs = (ctypes.c_int64 * 3)(0, 10, 20)
+    eps = (ctypes.c_float * 2)(0.1, 0.1)
+    jb, jc = (ctypes.c_int64 * 2)(0, 5), (ctypes.c_int64 * 2)(5, 5)
+    idx = (ctypes.c_int32 * 10)(*range(10))
+    monkeypatch.setenv("CN_FAULT_INJECT", "hostmem")
+    assert lib.cn_batch_plan_create(2, offs, eps, None, 0, ctypes.byref(h)) == 7
+    assert b"host memory" in lib.cn_last_error_message()
+    assert lib.cn_list_plan_create(2, offs, jb, jc, eps, None, 0, ctypes.byref(h)) == 7
+    assert lib.cn_list_plan_create_indexed(2, offs, jb, jc, eps, idx, 10, 10, None, 0, ctypes.byref(h)) == 7
+    assert h.value is None
+    # argument errors are still reported as such, before the injected failure
+    bad = (ctypes.c_int64 * 3)(0, 10, 5)
+    assert lib.cn_batch_plan_create(2, bad, eps, None, 0, ctypes.byref(h)) == 1
+    monkeypatch.delenv("CN_FAULT_INJECT")
+    assert lib.cn_status_string(7) == b"CN_ERR_HOST"
 
 
 def test_host_f64_form_validation(lib):
