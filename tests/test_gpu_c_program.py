@@ -1,7 +1,9 @@
-"""The C ABI from plain C: a C99 program linked against libcunbody.so calls
-the Section 3.1 routine (cn_force_host_f64: FP64 host arrays xj, mj, xi,
-eps2, a) and cn_force_host, with no Python or PyTorch in the process; its
-printed accelerations are compared with the FP64 oracle."""
+"""The C ABI from plain C: C99 programs linked against libcunbody.so, with no
+Python or PyTorch in the process. One calls the Section 3.1 routine
+(cn_force_host_f64: FP64 host arrays xj, mj, xi, eps2, a) and
+cn_force_host; the other builds a gathering interaction-list plan and runs
+it on device buffers it allocated with the CUDA runtime. Their printed
+accelerations are compared with the FP64 oracle."""
 
 import os
 import subprocess
@@ -73,3 +75,94 @@ def test_c_program_calls_the_paper_routine(tmp_path):
     ref, _ = oracle.force(p, p, eps2, potential=False)
     assert e_max(vals[:, :3], ref) <= 1e-5  # FP64 interface, FP32 records and pairs inside
     assert e_max(vals[:, 3:], ref) <= 1e-5
+
+
+LIST_PROGRAM = r"""
+#include <stdio.h>
+#include <stdlib.h>
+#include <stdint.h>
+#include <cuda_runtime.h>
+#include "cunbody.h"
+
+/* groups of particles against index lists into one source array, from C:
+   argv[1] holds n_i n_src n_groups n_entries eps2, the i records, the
+   source records, i_offsets, j_begin, j_count and the entries */
+int main(int argc, char **argv) {
+    FILE *f = fopen(argv[1], "r");
+    long long ni, ns, ng, ne;
+    double eps2;
+    if (!f || fscanf(f, "%lld %lld %lld %lld %lf", &ni, &ns, &ng, &ne, &eps2) != 5) return 2;
+    float *pi = malloc(sizeof(float) * 4 * ni), *ps = malloc(sizeof(float) * 4 * ns);
+    float *acc = malloc(sizeof(float) * 3 * ni), *e2 = malloc(sizeof(float) * ng);
+    int64_t *ioff = malloc(sizeof(int64_t) * (ng + 1)), *jb = malloc(sizeof(int64_t) * ng);
+    int64_t *jc = malloc(sizeof(int64_t) * ng);
+    int32_t *idx = malloc(sizeof(int32_t) * ne);
+    for (long long k = 0; k < 4 * ni; ++k) if (fscanf(f, "%f", &pi[k]) != 1) return 3;
+    for (long long k = 0; k < 4 * ns; ++k) if (fscanf(f, "%f", &ps[k]) != 1) return 3;
+    for (long long g = 0; g <= ng; ++g) { long long v; if (fscanf(f, "%lld", &v) != 1) return 3; ioff[g] = v; }
+    for (long long g = 0; g < ng; ++g) { long long v; if (fscanf(f, "%lld", &v) != 1) return 3; jb[g] = v; }
+    for (long long g = 0; g < ng; ++g) { long long v; if (fscanf(f, "%lld", &v) != 1) return 3; jc[g] = v; }
+    for (long long e = 0; e < ne; ++e) { int v; if (fscanf(f, "%d", &v) != 1) return 3; idx[e] = v; }
+    fclose(f);
+    for (long long g = 0; g < ng; ++g) e2[g] = (float)eps2;
+    cn_batch_plan *plan = NULL;
+    cn_status st = cn_list_plan_create_indexed((int32_t)ng, ioff, jb, jc, e2, idx, ne, ns, NULL, 0, &plan);
+    if (st != CN_OK) { fprintf(stderr, "%s: %s\n", cn_status_string(st), cn_last_error_message()); return 4; }
+    /* an entry outside the source array is refused on the host */
+    int32_t keep = idx[jb[0]];
+    idx[jb[0]] = (int32_t)ns;
+    cn_batch_plan *bad = NULL;
+    if (cn_list_plan_create_indexed((int32_t)ng, ioff, jb, jc, e2, idx, ne, ns, NULL, 0, &bad) != CN_ERR_INVALID_ARG
+        || bad != NULL) return 5;
+    idx[jb[0]] = keep;
+    float *d_pi, *d_ps, *d_acc;
+    if (cudaMalloc((void **)&d_pi, sizeof(float) * 4 * ni) != cudaSuccess ||
+        cudaMalloc((void **)&d_ps, sizeof(float) * 4 * ns) != cudaSuccess ||
+        cudaMalloc((void **)&d_acc, sizeof(float) * 3 * ni) != cudaSuccess) return 6;
+    cudaMemcpy(d_pi, pi, sizeof(float) * 4 * ni, cudaMemcpyHostToDevice);
+    cudaMemcpy(d_ps, ps, sizeof(float) * 4 * ns, cudaMemcpyHostToDevice);
+    st = cn_force_lists(plan, d_pi, d_ps, d_acc, NULL, NULL, 0, NULL);
+    if (st != CN_OK) { fprintf(stderr, "%s: %s\n", cn_status_string(st), cn_last_error_message()); return 7; }
+    if (cudaMemcpy(acc, d_acc, sizeof(float) * 3 * ni, cudaMemcpyDeviceToHost) != cudaSuccess) return 8;
+    if (cn_get_device_status(NULL) != CN_OK) return 9;
+    cn_batch_plan_destroy(plan);
+    cudaFree(d_pi);
+    cudaFree(d_ps);
+    cudaFree(d_acc);
+    for (long long i = 0; i < ni; ++i) printf("%.9g %.9g %.9g\n", acc[3 * i], acc[3 * i + 1], acc[3 * i + 2]);
+    return 0;
+}
+"""
+
+
+def test_c_program_runs_index_lists(tmp_path):
+    """A C99 program builds a gathering list plan, runs it on device buffers
+    it allocated itself, and has an out-of-range entry refused; its
+    accelerations are compared with the FP64 oracle group by group."""
+    torch_cuda()
+    cuda = os.environ.get("CUDA_HOME", "/usr/local/cuda")
+    lib_dir = os.path.join(ROOT, "paper_astro_ph_0703100_gb300")
+    src = tmp_path / "lists.c"
+    src.write_text(LIST_PROGRAM)
+    exe = tmp_path / "lists"
+    lib64 = os.path.join(cuda, "lib64")
+    subprocess.run(["gcc", "-std=c99", "-O2", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), "-I",
+                    os.path.join(cuda, "include"), str(src), "-L", lib_dir, "-lcunbody", f"-Wl,-rpath,{lib_dir}",
+                    "-L", lib64, "-lcudart", f"-Wl,-rpath,{lib64}", "-o", str(exe)], check=True)
+    pos_i, i_off, srcr, j_index, jb, jc = synth.interaction_lists_indexed(1500, 128, 300, seed=12)
+    eps2 = float(np.float32(0.001))
+    data = tmp_path / "in.txt"
+    with open(data, "w") as f:
+        f.write(f"{pos_i.shape[0]} {srcr.shape[0]} {len(jc)} {j_index.size} {eps2!r}\n")
+        for arr in (pos_i.ravel(), srcr.ravel()):
+            f.write(" ".join(repr(float(v)) for v in arr) + "\n")
+        for arr in (i_off, jb, jc, j_index):
+            f.write(" ".join(str(int(v)) for v in arr) + "\n")
+    res = subprocess.run([str(exe), str(data)], capture_output=True, text=True)
+    assert res.returncode == 0, (res.returncode, res.stderr[-2000:])
+    acc = np.array([[float(v) for v in line.split()] for line in res.stdout.splitlines()])
+    assert acc.shape == (pos_i.shape[0], 3)
+    for g in range(len(jc)):
+        lo, hi = i_off[g], i_off[g + 1]
+        ref, _ = oracle.force(pos_i[lo:hi], srcr[j_index[jb[g]:jb[g] + jc[g]]], eps2, potential=False)
+        assert e_max(acc[lo:hi], ref) <= 1e-5, g
