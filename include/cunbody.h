@@ -41,6 +41,10 @@
  *    a CUDA graph (CN_ERR_WORKSPACE): make one call on that stream before
  *    capturing, or use the *_ws forms.
  *  - Thread safety: concurrent calls are safe on different streams.
+ *  - Errors are returned as cn_status codes, with a message from
+ *    cn_last_error_message (per thread). No C++ exception leaves the
+ *    library: host memory exhausted inside it, or any other C++ runtime
+ *    error, is CN_ERR_HOST.
  *  - Kernels are launched with programmatic stream serialization
  *    (programmatic dependent launch): a library kernel may be scheduled
  *    while the previous kernel of the stream is still running, and it waits
